@@ -1,0 +1,221 @@
+/*
+ * sf.h — C ABI of the batched Safety-Filter (SF) solver for B300 (sm_103a).
+ *
+ * The SF projects candidate multi-robot trajectories, given as polynomial
+ * coefficients, onto the constraint set of the paper's projection problem
+ * (Sec. IV-B, eqs. proj_cost..proj_robot): boundary equalities A xi = b,
+ * workspace box G xi <= h, and inter-robot / robot-obstacle separation written
+ * in spherical form (Appendix, eqs. inter_robot_polar, workspace_polar).  It
+ * runs the fixed-point operator T of eq. fixed_point — the alternating
+ * minimisation of the augmented Lagrangian (eq. aug_lag) in the order alpha,
+ * beta, d, s, lambda, xi_bar (eqs. alpha_step..xi_step) — for many independent
+ * instances at once, and differentiates through it.
+ *
+ * Conventions shared by every call
+ *  - Coefficients are axis-major per instance, [n_d][n][n_xi] (Sec. III-A,
+ *    coefficient stacking); the trajectory basis is Bernstein of degree n_xi-1
+ *    sampled at tau_k = k/(H-1), k = 0..H-1, so coefficient 0 is the start and
+ *    coefficient n_xi-1 the goal.
+ *  - Per-instance arrays are packed back to back in instance order; the packing
+ *    offsets are returned by sf_layout().
+ *  - Element type T of every floating-point array argument: double when the
+ *    handle's precision is SF_FP64, float otherwise.
+ *  - Array arguments of sf_solve / sf_solve_backward are DEVICE pointers owned
+ *    by the caller; the library never frees them.  The library owns its factor
+ *    and workspace memory (allocated in sf_create, freed in sf_destroy).
+ *  - All calls return an sf_status; SF_OK is 0.  No call aborts, traps or exits.
+ *  - sf_solve and sf_solve_backward are asynchronous on the given stream
+ *    (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *    Device-side failures (non-finite values, bounded waits that ran out) are
+ *    reported per instance by sf_get_status() after the stream is synchronised.
+ *  - A handle is not thread-safe; calls on one handle must be serialised.
+ */
+#ifndef SF_H
+#define SF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+enum {
+    SF_OK = 0,
+    SF_EINVAL = 1,      /* invalid argument (NULL pointer, size or value out of range)   */
+    SF_ESHAPE = 2,      /* inconsistent shapes (e.g. backward after a solve with other sizes) */
+    SF_ECUDA = 3,       /* a CUDA runtime call failed                                     */
+    SF_ENOMEM = 4,      /* device or host allocation failed                               */
+    SF_ETIMEOUT = 5,    /* a bounded device-side wait ran out (reported per instance)     */
+    SF_ENONFINITE = 6,  /* NaN/Inf met in an iterate (reported per instance)              */
+    SF_ESTATE = 7,      /* call order violated (e.g. backward without checkpoints)        */
+    SF_EUNSUPPORTED = 8 /* option not built into this library                             */
+};
+
+/* ---- precision of the iteration ------------------------------------------ */
+enum {
+    SF_FP64 = 0,       /* everything in FP64 (plain reference path on the GPU)            */
+    SF_FP32 = 1,       /* FP32 elementwise steps, FP32 SIMT projection                    */
+    SF_TF32 = 2,       /* FP32 elementwise, projection on tensor cores in TF32, FP32 acc  */
+    SF_BF16X3 = 3,     /* FP32 elementwise, projection as three BF16 tensor-core products
+                          (hi*hi + hi*lo + lo*hi of a two-term BF16 split), FP32 acc      */
+    SF_BF16 = 4        /* FP32 elementwise, projection in one BF16 tensor-core product    */
+};
+
+/* ---- projection operator (step xi_bar, eq. batch_comp) -------------------- */
+enum {
+    SF_PROJ_DENSE = 0,      /* dense P_eta (N x N per shape), as in eq. batch_comp          */
+    SF_PROJ_STRUCTURED = 1  /* same operator through its Kronecker form (n_xi x n_xi blocks) */
+};
+
+/* ---- per-instance shape ---------------------------------------------------- */
+typedef struct sf_shape {
+    int32_t n;          /* robots, >= 1                                                    */
+    int32_t n_obs;      /* obstacles, >= 0                                                 */
+    int32_t H;          /* timesteps K+1 of the planning period, >= 2                      */
+    int32_t dyn_obs;    /* 0: static centres [n_obs][n_d]; 1: per timestep [n_obs][H][n_d] */
+    double a, b;        /* robot spheroid: M_r = diag(a, a, b) (Sec. III-A); centre
+                           distance >= a between spherical robots of radius a/2             */
+    double p_min[3];    /* workspace box (eq. workspace_con), already inset by the robot   */
+    double p_max[3];
+} sf_shape;
+
+/* ---- solver description --------------------------------------------------- */
+typedef struct sf_desc {
+    int32_t n_d;        /* workspace dimension, 2 or 3                                     */
+    int32_t n_xi;       /* Bernstein coefficients per robot per axis, 4..32                */
+    double rho;         /* augmented-Lagrangian penalty (eq. aug_lag), > 0                 */
+    int32_t precision;  /* SF_FP64 .. SF_BF16                                              */
+    int32_t proj;       /* SF_PROJ_DENSE or SF_PROJ_STRUCTURED                             */
+    int32_t n_refine;   /* extra refinement passes of the reduced-precision projection      */
+    int32_t max_iters;  /* upper bound on `iters` of sf_solve (sizes checkpoint storage)    */
+    int32_t ckpt_every; /* > 0: sf_solve keeps (xi_bar, lambda) every ckpt_every iterations
+                           so sf_solve_backward can run; 0: no backward                    */
+    double tol;         /* residual threshold in metres for iterations-to-tolerance        */
+    int32_t n_inst;     /* number of instances, >= 1                                       */
+    const sf_shape *shapes; /* host array [n_inst], copied by sf_create                    */
+    void *stream;       /* cudaStream_t on which sf_create runs the factorisations         */
+} sf_desc;
+
+typedef struct sf_handle sf_handle;
+
+/* ---- instance data (device pointers, element type T) ---------------------- */
+typedef struct sf_instance_data {
+    const void *bnd;    /* [n_d][n][2] start and goal per axis and robot (eq. boundary_con) */
+    const void *obs_c;  /* obstacle centres, static [n_obs][n_d] or dynamic [n_obs][H][n_d]  */
+    const void *obs_ab; /* [n_obs][2] obstacle axes (a_o, b_o), inflated by the robot size  */
+} sf_instance_data;
+
+/* Layout kinds for sf_layout */
+enum { SF_LAYOUT_XI = 0, SF_LAYOUT_BND = 1, SF_LAYOUT_OBS = 2, SF_LAYOUT_OBS_AB = 3 };
+
+/* Per-instance outputs of sf_solve in resid_out (double, device, [n_inst][SF_NRES]) */
+enum {
+    SF_RES_RP = 0,      /* ||r_p||_2 of the returned xi_bar, FP64 (eq. primal_residual)      */
+    SF_RES_MAX = 1,     /* max constraint residual of the returned xi_bar in metres, FP64:
+                           max over rows of ||r_1 row|| (penetration) and of r_2 entries   */
+    SF_RES_FP = 2,      /* ||z^L - z^(L-1)||_2, last fixed-point step (eq. fixed_point_residual) */
+    SF_RES_ITERS = 3,   /* first l whose iterate met max residual <= tol, or -1            */
+    SF_NRES = 4
+};
+
+/*
+ * sf_create — validate `desc`, build every distinct (n, n_obs, H) shape's basis W
+ * and the xi_bar-step operators, and factor them in FP64 on the GPU (eq. xi_step:
+ * Cholesky of H = I + rho F'F + rho G'G, Schur complement of A; the factorisation
+ * is independent of the candidate and is stored, as the Appendix notes, and only
+ * changes with rho or the horizon).  Runs on desc->stream and synchronises it.
+ * On success *out owns all device memory of the solver.
+ * Errors: SF_EINVAL (bad sizes/values, NULL), SF_ENOMEM, SF_ECUDA, SF_EUNSUPPORTED.
+ */
+int sf_create(const sf_desc *desc, sf_handle **out);
+
+/* sf_destroy — free the handle and its device memory (synchronises its streams). */
+int sf_destroy(sf_handle *h);
+
+/*
+ * sf_layout — packing offsets (in elements of T) of one per-instance array kind:
+ * offsets[i] = start of instance i, offsets[n_inst] = total length.
+ * `offsets` is a host array of n_inst + 1 entries.
+ */
+int sf_layout(const sf_handle *h, int32_t kind, int64_t *offsets);
+
+/*
+ * sf_solve — run `iters` applications of T (eq. fixed_point) on every instance.
+ *  data            instance data (device, T), see sf_instance_data
+ *  xi_cand         candidate coefficients xi (SF_LAYOUT_XI packing)
+ *  xi0, lam0       initial (xi_bar^0, lambda^0); NULL means xi_bar^0 = xi_cand, lambda^0 = 0
+ *  iters           0 <= iters <= desc->max_iters
+ *  xi_out, lam_out (xi_bar^L, lambda^L); lam_out may be NULL
+ *  resid_out       device double [n_inst][SF_NRES] or NULL
+ *  iters_to_tol    device int32 [n_inst] or NULL (same value as resid_out[SF_RES_ITERS])
+ *  stream          cudaStream_t
+ * When desc->ckpt_every > 0 the call also records what sf_solve_backward needs; the
+ * caller must keep data, xi_cand, xi0, lam0 unchanged until that backward call.
+ * Errors: SF_EINVAL, SF_ECUDA.
+ */
+int sf_solve(sf_handle *h, const sf_instance_data *data, const void *xi_cand, const void *xi0,
+             const void *lam0, int32_t iters, void *xi_out, void *lam_out, double *resid_out,
+             int32_t *iters_to_tol, void *stream);
+
+/*
+ * sf_solve_backward — vector-Jacobian product through the iterations of the last
+ * sf_solve on this handle (the unrolled chain of T, Fig. unroll_learning), by a
+ * hand-written adjoint that recomputes each checkpoint segment.
+ *  g_xi_out, g_lam_out  seeds dL/dxi_bar^L, dL/dlambda^L (either may be NULL = 0)
+ *  g_rp2                device double [n_inst] or NULL: dL/d||r_p(xi_bar^L)||^2
+ *  g_xi_cand            out: dL/dxi_cand (through eta in every iteration; when that
+ *                       solve had xi0 = NULL, also through xi_bar^0 = xi_cand)
+ *  g_xi0, g_lam0        out: dL/dxi_bar^0, dL/dlambda^0 (either may be NULL)
+ * Errors: SF_ESTATE (no preceding solve with checkpoints), SF_EINVAL, SF_ECUDA.
+ */
+int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void *g_lam_out,
+                      const double *g_rp2, void *g_xi_cand, void *g_xi0, void *g_lam0,
+                      void *stream);
+
+/*
+ * sf_get_status — copy the per-instance device status words (SF_OK, SF_ENONFINITE,
+ * SF_ETIMEOUT) of the last solve/backward into the host array [n_inst] and
+ * clear them.  Synchronises the handle's last stream.
+ */
+int sf_get_status(sf_handle *h, int32_t *per_instance_status);
+
+/*
+ * sf_shape_operator — diagnostic copy of the FP64 operators of instance `inst`'s shape
+ * to host memory `host_out`:
+ *   which = 0: basis W [H][n_xi]
+ *   which = 1: P_eta [N][N]            (N = n * n_xi)
+ *   which = 2: P_b [N][2n]             (columns robot-major: start, goal)
+ *   which = 3: Kronecker blocks P_dev [n_xi][n_xi], P_mean [n_xi][n_xi],
+ *              B_dev [n_xi][2], B_mean [n_xi][2], back to back
+ * Synchronises the device.  Errors: SF_EINVAL, SF_ECUDA.
+ */
+int sf_shape_operator(const sf_handle *h, int32_t inst, int32_t which, double *host_out);
+
+/* Kernel timing slots of sf_kernel_times */
+enum { SF_KT_FORWARD = 0, SF_KT_RESIDUAL = 1, SF_KT_BACKWARD = 2, SF_NKT = 3 };
+
+/*
+ * sf_profile — enable (1) or disable (0) CUDA-event timing of each kernel that
+ * sf_solve / sf_solve_backward launch on this handle (events are recorded on the
+ * call's stream around the launch).  Off by default.
+ */
+int sf_profile(sf_handle *h, int32_t enable);
+
+/*
+ * sf_kernel_times — durations in milliseconds of the kernels of the most recent
+ * profiled calls, into host ms_out[SF_NKT] (0 for a kernel that did not run).
+ * Synchronises on the recorded events.  Errors: SF_EINVAL, SF_ESTATE (profiling off).
+ */
+int sf_kernel_times(sf_handle *h, float *ms_out);
+
+/* sf_strerror — static description of a status code. */
+const char *sf_strerror(int32_t code);
+
+/* sf_version — library version as an integer (major * 10000 + minor * 100 + patch). */
+int32_t sf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SF_H */

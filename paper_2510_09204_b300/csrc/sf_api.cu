@@ -1,0 +1,535 @@
+// C ABI of the SF solver: handle, validation, shape registry, factorisation and
+// launches.  See include/sf.h for the contract of every call.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "sf_internal.cuh"
+
+using namespace sf;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t alloc(size_t b)
+    {
+        bytes = b;
+        if (b == 0) return cudaSuccess;
+        return cudaMalloc(&p, b);
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+struct SolveRecord {
+    bool valid = false;
+    const void *bnd = nullptr, *obs = nullptr, *oab = nullptr;
+    const void *xc = nullptr, *x0 = nullptr, *l0 = nullptr;
+    int iters = 0;
+};
+
+}  // namespace
+
+struct sf_handle {
+    sf_desc d{};
+    std::vector<sf_shape> shp;
+    int esz = 8;                       // sizeof(T)
+    int n_shapes = 0;
+    std::vector<int> inst_shape;
+    std::vector<Shape> shapes_h;
+    std::vector<int64_t> off[4];       // SF_LAYOUT_* offsets, n_inst + 1 each
+    std::vector<int> order;
+    std::vector<int> hc;
+    // device memory
+    DevBuf inst_dev, shapes_dev, order_dev, status_dev;
+    DevBuf W64, P64, Pb64, S64;        // FP64 factors
+    DevBuf Wt, Pt, Pbt, St;            // in T (aliases of the FP64 pools when T = double)
+    DevBuf ck_x, ck_l;
+    int n_slots = 0;
+    int64_t xi_total = 0;
+    // launch configuration
+    int threads = 256;
+    size_t smem_fwd = 0, smem_res = 0;
+    int p_smem = 0;
+    int smem_optin = 0;
+    int num_sms = 0;
+    SolveRecord last;
+    cudaStream_t last_stream = nullptr;
+    bool profile = false;
+    cudaEvent_t ev[2 * SF_NKT] = {};
+    bool ev_used[SF_NKT] = {};
+};
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SF_OK : (e == cudaErrorMemoryAllocation ? SF_ENOMEM : SF_ECUDA); }
+
+#define SF_TRY(expr)                                  \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Shared memory of the forward kernel for one instance (mirrors the carve in k_forward).
+static size_t fwd_bytes(const sf_handle *h, const sf_shape &s, int hc, bool with_p)
+{
+    const int nd = h->d.n_d, nxi = h->d.n_xi, N = s.n * nxi;
+    size_t t = (size_t)s.H * nxi + 5 * (size_t)nd * N + (size_t)nd * s.n * hc + (size_t)s.n_obs * (nd + 4) +
+               (size_t)nd * s.n * 2;
+    if (h->d.proj == SF_PROJ_STRUCTURED) t += 2 * (size_t)nxi * nxi + 4 * (size_t)nxi + (size_t)nd * nxi * 2;
+    size_t b = align16(t * h->esz) + kRedDoubles * sizeof(double);
+    if (with_p) b += (size_t)N * N * h->esz;
+    return b;
+}
+
+static size_t res_bytes(const sf_handle *h, const sf_shape &s, int hc)
+{
+    const int nd = h->d.n_d, nxi = h->d.n_xi, N = s.n * nxi;
+    size_t t = (size_t)s.H * nxi + (size_t)nd * N + (size_t)nd * s.n * hc + (size_t)s.n_obs * (nd + 4) + kRedDoubles;
+    return t * sizeof(double);
+}
+
+static int validate(const sf_desc *d)
+{
+    if (!d || !d->shapes) return SF_EINVAL;
+    if (d->n_d < 2 || d->n_d > 3 || d->n_xi < 4 || d->n_xi > 32) return SF_EINVAL;
+    if (!(d->rho > 0.0) || !isfinite(d->rho) || d->n_inst < 1) return SF_EINVAL;
+    if (d->precision < SF_FP64 || d->precision > SF_BF16) return SF_EINVAL;
+    if (d->proj != SF_PROJ_DENSE && d->proj != SF_PROJ_STRUCTURED) return SF_EINVAL;
+    if (d->max_iters < 0 || d->ckpt_every < 0 || d->n_refine < 0 || !(d->tol >= 0.0)) return SF_EINVAL;
+    for (int i = 0; i < d->n_inst; ++i) {
+        const sf_shape &s = d->shapes[i];
+        if (s.n < 1 || s.n > 256 || s.n_obs < 0 || s.n_obs > 4096 || s.H < 2 || s.H > 4096) return SF_EINVAL;
+        if (!(s.a > 0.0) || !(s.b > 0.0) || !isfinite(s.a) || !isfinite(s.b)) return SF_EINVAL;
+        if (s.dyn_obs != 0 && s.dyn_obs != 1) return SF_EINVAL;
+        for (int ax = 0; ax < d->n_d; ++ax)
+            if (!isfinite(s.p_min[ax]) || !isfinite(s.p_max[ax]) || !(s.p_min[ax] <= s.p_max[ax])) return SF_EINVAL;
+    }
+    return SF_OK;
+}
+
+template <typename T>
+static int upload_instances(sf_handle *h)
+{
+    const int nd = h->d.n_d;
+    std::vector<Inst<T>> I(h->d.n_inst);
+    for (int i = 0; i < h->d.n_inst; ++i) {
+        const sf_shape &s = h->shp[i];
+        Inst<T> &x = I[i];
+        memset(&x, 0, sizeof(x));
+        x.n = s.n;
+        x.n_obs = s.n_obs;
+        x.H = s.H;
+        x.dyn = s.dyn_obs;
+        x.N = s.n * h->d.n_xi;
+        x.shape = h->inst_shape[i];
+        x.hc = h->hc[i];
+        x.a = (T)s.a;
+        x.b = (T)s.b;
+        x.ia2 = (T)(1.0 / (s.a * s.a));
+        x.ib2 = (T)(1.0 / (s.b * s.b));
+        for (int ax = 0; ax < 3; ++ax) {
+            x.pmin[ax] = (T)(ax < nd ? s.p_min[ax] : 0.0);
+            x.pmax[ax] = (T)(ax < nd ? s.p_max[ax] : 0.0);
+        }
+        x.off_xi = h->off[SF_LAYOUT_XI][i];
+        x.off_bnd = h->off[SF_LAYOUT_BND][i];
+        x.off_obs = h->off[SF_LAYOUT_OBS][i];
+        x.off_oab = h->off[SF_LAYOUT_OBS_AB][i];
+    }
+    SF_TRY(h->inst_dev.alloc(sizeof(Inst<T>) * I.size()));
+    SF_TRY(cudaMemcpy(h->inst_dev.p, I.data(), sizeof(Inst<T>) * I.size(), cudaMemcpyHostToDevice));
+    return SF_OK;
+}
+
+static void destroy_all(sf_handle *h)
+{
+    for (int k = 0; k < 2 * SF_NKT; ++k)
+        if (h->ev[k]) {
+            cudaEventDestroy(h->ev[k]);
+            h->ev[k] = nullptr;
+        }
+    DevBuf *bufs[] = {&h->inst_dev, &h->shapes_dev, &h->order_dev, &h->status_dev, &h->W64, &h->P64,
+                      &h->Pb64, &h->S64, &h->ck_x, &h->ck_l};
+    if (h->esz == 4) {
+        h->Wt.release();
+        h->Pt.release();
+        h->Pbt.release();
+        h->St.release();
+    }
+    for (DevBuf *b : bufs) b->release();
+}
+
+extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
+{
+    if (!out) return SF_EINVAL;
+    *out = nullptr;
+    int rc = validate(desc);
+    if (rc) return rc;
+    sf_handle *h = new (std::nothrow) sf_handle();
+    if (!h) return SF_ENOMEM;
+    h->d = *desc;
+    h->shp.assign(desc->shapes, desc->shapes + desc->n_inst);
+    h->d.shapes = nullptr;
+    h->esz = desc->precision == SF_FP64 ? 8 : 4;
+    const int nd = desc->n_d, nxi = desc->n_xi, B = desc->n_inst;
+    cudaStream_t st = (cudaStream_t)desc->stream;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { delete h; return SF_ECUDA; }
+    cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+
+    // layouts
+    for (int k = 0; k < 4; ++k) h->off[k].assign(B + 1, 0);
+    for (int i = 0; i < B; ++i) {
+        const sf_shape &s = h->shp[i];
+        h->off[SF_LAYOUT_XI][i + 1] = h->off[SF_LAYOUT_XI][i] + (int64_t)nd * s.n * nxi;
+        h->off[SF_LAYOUT_BND][i + 1] = h->off[SF_LAYOUT_BND][i] + (int64_t)nd * s.n * 2;
+        h->off[SF_LAYOUT_OBS][i + 1] = h->off[SF_LAYOUT_OBS][i] + (int64_t)s.n_obs * (s.dyn_obs ? s.H : 1) * nd;
+        h->off[SF_LAYOUT_OBS_AB][i + 1] = h->off[SF_LAYOUT_OBS_AB][i] + (int64_t)s.n_obs * 2;
+    }
+    h->xi_total = h->off[SF_LAYOUT_XI][B];
+
+    // distinct shapes
+    std::map<std::tuple<int, int, int>, int> key;
+    h->inst_shape.resize(B);
+    int64_t oW = 0, oP = 0, oPb = 0, oS = 0;
+    for (int i = 0; i < B; ++i) {
+        const sf_shape &s = h->shp[i];
+        auto k = std::make_tuple(s.n, s.n_obs, s.H);
+        auto it = key.find(k);
+        if (it == key.end()) {
+            Shape S;
+            S.n = s.n;
+            S.n_obs = s.n_obs;
+            S.H = s.H;
+            S.N = s.n * nxi;
+            S.off_W = oW;
+            S.off_P = oP;
+            S.off_Pb = oPb;
+            S.off_S = oS;
+            oW += (int64_t)s.H * nxi;
+            oP += (int64_t)S.N * S.N;
+            oPb += (int64_t)S.N * 2 * s.n;
+            oS += 2 * (int64_t)nxi * nxi + 4 * (int64_t)nxi;
+            it = key.emplace(k, (int)h->shapes_h.size()).first;
+            h->shapes_h.push_back(S);
+        }
+        h->inst_shape[i] = it->second;
+    }
+    h->n_shapes = (int)h->shapes_h.size();
+
+    // launch geometry: chunk of timesteps per instance, shared memory
+    h->threads = kMaxThreads;
+    h->hc.resize(B);
+    const size_t budget = (size_t)h->smem_optin;
+    size_t need = 0, need_p = 0, need_r = 0;
+    for (int i = 0; i < B; ++i) {
+        const sf_shape &s = h->shp[i];
+        int hc = std::min(s.H, kIPT * h->threads / s.n);
+        if (hc < 1) hc = 1;
+        while (hc > 1 && fwd_bytes(h, s, hc, false) > budget) --hc;
+        if (fwd_bytes(h, s, hc, false) > budget) { destroy_all(h); delete h; return SF_EUNSUPPORTED; }
+        h->hc[i] = hc;
+        need = std::max(need, fwd_bytes(h, s, hc, false));
+        need_p = std::max(need_p, fwd_bytes(h, s, hc, true));
+        need_r = std::max(need_r, res_bytes(h, s, 1));
+    }
+    h->p_smem = (desc->proj == SF_PROJ_DENSE && need_p <= budget) ? 1 : 0;
+    h->smem_fwd = h->p_smem ? need_p : need;
+    h->smem_res = std::min(budget, std::max(need_r, (size_t)96 * 1024));
+    if (need_r > budget) { destroy_all(h); delete h; return SF_EUNSUPPORTED; }
+
+    // instance order: largest work first
+    h->order.resize(B);
+    for (int i = 0; i < B; ++i) h->order[i] = i;
+    std::stable_sort(h->order.begin(), h->order.end(), [&](int x, int y) {
+        auto cost = [&](int i) {
+            const sf_shape &s = h->shp[i];
+            return (double)s.H * ((double)s.n * (s.n - 1) + (double)s.n * s.n_obs);
+        };
+        return cost(x) > cost(y);
+    });
+
+    // device allocations
+    int r;
+    if ((r = cuda_status(h->shapes_dev.alloc(sizeof(Shape) * h->n_shapes))) ||
+        (r = cuda_status(h->order_dev.alloc(sizeof(int) * B))) ||
+        (r = cuda_status(h->status_dev.alloc(sizeof(int32_t) * B))) ||
+        (r = cuda_status(h->W64.alloc(sizeof(double) * oW))) ||
+        (r = cuda_status(h->P64.alloc(sizeof(double) * oP))) ||
+        (r = cuda_status(h->Pb64.alloc(sizeof(double) * oPb))) ||
+        (r = cuda_status(h->S64.alloc(sizeof(double) * oS)))) {
+        destroy_all(h);
+        delete h;
+        return r;
+    }
+    if ((r = cuda_status(cudaMemcpy(h->shapes_dev.p, h->shapes_h.data(), sizeof(Shape) * h->n_shapes, cudaMemcpyHostToDevice))) ||
+        (r = cuda_status(cudaMemcpy(h->order_dev.p, h->order.data(), sizeof(int) * B, cudaMemcpyHostToDevice))) ||
+        (r = cuda_status(cudaMemset(h->status_dev.p, 0, sizeof(int32_t) * B)))) {
+        destroy_all(h);
+        delete h;
+        return r;
+    }
+    r = h->esz == 8 ? upload_instances<double>(h) : upload_instances<float>(h);
+    if (r) { destroy_all(h); delete h; return r; }
+
+    // FP64 factorisation on the GPU
+    {
+        DevBuf scratch, info;
+        if ((r = cuda_status(scratch.alloc(sizeof(double) * 3 * std::max<int64_t>(oP, 1)))) ||
+            (r = cuda_status(info.alloc(sizeof(int) * h->n_shapes)))) {
+            scratch.release();
+            info.release();
+            destroy_all(h);
+            delete h;
+            return r;
+        }
+        cudaMemsetAsync(info.p, 0, sizeof(int) * h->n_shapes, st);
+        cudaError_t e = factor_shapes((const Shape *)h->shapes_dev.p, h->n_shapes, h->shapes_h.data(), nxi,
+                                      desc->rho, (double *)h->W64.p, (double *)h->P64.p, (double *)h->Pb64.p,
+                                      (double *)h->S64.p, (double *)scratch.p, 3 * oP, (int *)info.p, st);
+        std::vector<int> inf(h->n_shapes, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaMemcpy(inf.data(), info.p, sizeof(int) * h->n_shapes, cudaMemcpyDeviceToHost);
+        scratch.release();
+        info.release();
+        if (e != cudaSuccess) { destroy_all(h); delete h; return cuda_status(e); }
+        for (int v : inf)
+            if (v) { destroy_all(h); delete h; return SF_EINVAL; }
+    }
+    if (h->esz == 8) {
+        h->Wt = h->W64;
+        h->Pt = h->P64;
+        h->Pbt = h->Pb64;
+        h->St = h->S64;
+    } else {
+        if ((r = cuda_status(h->Wt.alloc(sizeof(float) * oW))) || (r = cuda_status(h->Pt.alloc(sizeof(float) * oP))) ||
+            (r = cuda_status(h->Pbt.alloc(sizeof(float) * oPb))) || (r = cuda_status(h->St.alloc(sizeof(float) * oS)))) {
+            destroy_all(h);
+            delete h;
+            return r;
+        }
+        convert_pool((double *)h->W64.p, (float *)h->Wt.p, oW, st);
+        convert_pool((double *)h->P64.p, (float *)h->Pt.p, oP, st);
+        convert_pool((double *)h->Pb64.p, (float *)h->Pbt.p, oPb, st);
+        convert_pool((double *)h->S64.p, (float *)h->St.p, oS, st);
+        if ((r = cuda_status(cudaStreamSynchronize(st)))) { destroy_all(h); delete h; return r; }
+    }
+    // checkpoints
+    if (desc->ckpt_every > 0) {
+        h->n_slots = desc->max_iters / desc->ckpt_every + 1;
+        size_t b = (size_t)h->n_slots * h->xi_total * h->esz;
+        if ((r = cuda_status(h->ck_x.alloc(b))) || (r = cuda_status(h->ck_l.alloc(b)))) {
+            destroy_all(h);
+            delete h;
+            return r;
+        }
+    }
+    *out = h;
+    return SF_OK;
+}
+
+extern "C" int sf_destroy(sf_handle *h)
+{
+    if (!h) return SF_EINVAL;
+    cudaDeviceSynchronize();
+    destroy_all(h);
+    delete h;
+    return SF_OK;
+}
+
+extern "C" int sf_layout(const sf_handle *h, int32_t kind, int64_t *offsets)
+{
+    if (!h || !offsets || kind < 0 || kind > 3) return SF_EINVAL;
+    memcpy(offsets, h->off[kind].data(), sizeof(int64_t) * (h->d.n_inst + 1));
+    return SF_OK;
+}
+
+template <typename T>
+static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, const void *x0, const void *l0,
+                   int iters, void *xo, void *lo, double *resid, int32_t *its, cudaStream_t st)
+{
+    FwdArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.nd = h->d.n_d;
+    a.nxi = h->d.n_xi;
+    a.iters = iters;
+    a.n_inst = h->d.n_inst;
+    a.p_smem = h->p_smem;
+    a.proj = h->d.proj;
+    a.rho = (T)h->d.rho;
+    a.tol = h->d.tol;
+    a.inst = (const Inst<T> *)h->inst_dev.p;
+    a.order = (const int *)h->order_dev.p;
+    a.shapes = (const Shape *)h->shapes_dev.p;
+    a.W = (const T *)h->Wt.p;
+    a.P = (const T *)h->Pt.p;
+    a.Pb = (const T *)h->Pbt.p;
+    a.Sx = (const T *)h->St.p;
+    a.xc = (const T *)xc;
+    a.x0 = (const T *)x0;
+    a.l0 = (const T *)l0;
+    a.bnd = (const T *)data->bnd;
+    a.obs = (const T *)data->obs_c;
+    a.oab = (const T *)data->obs_ab;
+    a.xo = (T *)xo;
+    a.lo = (T *)lo;
+    a.resid = resid;
+    a.its = its;
+    a.status = (int32_t *)h->status_dev.p;
+    if (h->d.ckpt_every > 0) {
+        a.ck_x = (T *)h->ck_x.p;
+        a.ck_l = (T *)h->ck_l.p;
+        a.ck_every = h->d.ckpt_every;
+        a.ck_slot = h->xi_total;
+    }
+    int grid = h->d.n_inst;
+    for (int k = 0; k < SF_NKT; ++k) h->ev_used[k] = false;
+    if (h->profile) SF_TRY(cudaEventRecord(h->ev[0], st));
+    SF_TRY(launch_forward(a, grid, h->threads, h->smem_fwd, st));
+    if (h->profile) {
+        SF_TRY(cudaEventRecord(h->ev[1], st));
+        h->ev_used[SF_KT_FORWARD] = true;
+    }
+    if (resid) {
+        ResArgs<T> r;
+        memset(&r, 0, sizeof(r));
+        r.nd = a.nd;
+        r.nxi = a.nxi;
+        r.n_inst = a.n_inst;
+        r.tol = a.tol;
+        r.inst = a.inst;
+        r.shapes = a.shapes;
+        r.W = a.W;
+        r.x = (const T *)xo;
+        r.obs = a.obs;
+        r.oab = a.oab;
+        r.resid = resid;
+        r.its = its;
+        r.iters = iters;
+        r.status = a.status;
+        r.smem_doubles = (int64_t)(h->smem_res / sizeof(double));
+        if (h->profile) SF_TRY(cudaEventRecord(h->ev[2], st));
+        SF_TRY(launch_residual(r, h->threads, h->smem_res, st));
+        if (h->profile) {
+            SF_TRY(cudaEventRecord(h->ev[3], st));
+            h->ev_used[SF_KT_RESIDUAL] = true;
+        }
+    }
+    return SF_OK;
+}
+
+extern "C" int sf_solve(sf_handle *h, const sf_instance_data *data, const void *xi_cand, const void *xi0,
+                        const void *lam0, int32_t iters, void *xi_out, void *lam_out, double *resid_out,
+                        int32_t *iters_to_tol, void *stream)
+{
+    if (!h || !data || !xi_cand || !xi_out || !data->bnd) return SF_EINVAL;
+    if (iters < 0 || iters > h->d.max_iters) return SF_EINVAL;
+    bool any_obs = h->off[SF_LAYOUT_OBS][h->d.n_inst] > 0;
+    if (any_obs && (!data->obs_c || !data->obs_ab)) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = h->esz == 8 ? solve_t<double>(h, data, xi_cand, xi0, lam0, iters, xi_out, lam_out, resid_out, iters_to_tol, st)
+                         : solve_t<float>(h, data, xi_cand, xi0, lam0, iters, xi_out, lam_out, resid_out, iters_to_tol, st);
+    if (rc) return rc;
+    h->last_stream = st;
+    h->last.valid = h->d.ckpt_every > 0;
+    h->last.bnd = data->bnd;
+    h->last.obs = data->obs_c;
+    h->last.oab = data->obs_ab;
+    h->last.xc = xi_cand;
+    h->last.x0 = xi0;
+    h->last.l0 = lam0;
+    h->last.iters = iters;
+    return SF_OK;
+}
+
+extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void *g_lam_out, const double *g_rp2,
+                                 void *g_xi_cand, void *g_xi0, void *g_lam0, void *stream)
+{
+    (void)g_xi_out; (void)g_lam_out; (void)g_rp2; (void)g_xi_cand; (void)g_xi0; (void)g_lam0; (void)stream;
+    if (!h) return SF_EINVAL;
+    if (!h->last.valid) return SF_ESTATE;
+    return SF_EUNSUPPORTED;
+}
+
+extern "C" int sf_profile(sf_handle *h, int32_t enable)
+{
+    if (!h) return SF_EINVAL;
+    if (enable && !h->ev[0])
+        for (int k = 0; k < 2 * SF_NKT; ++k) SF_TRY(cudaEventCreate(&h->ev[k]));
+    h->profile = enable != 0;
+    return SF_OK;
+}
+
+extern "C" int sf_kernel_times(sf_handle *h, float *ms_out)
+{
+    if (!h || !ms_out) return SF_EINVAL;
+    if (!h->ev[0]) return SF_ESTATE;
+    for (int k = 0; k < SF_NKT; ++k) {
+        ms_out[k] = 0.0f;
+        if (h->ev_used[k]) {
+            SF_TRY(cudaEventSynchronize(h->ev[2 * k + 1]));
+            SF_TRY(cudaEventElapsedTime(&ms_out[k], h->ev[2 * k], h->ev[2 * k + 1]));
+        }
+    }
+    return SF_OK;
+}
+
+extern "C" int sf_get_status(sf_handle *h, int32_t *per_instance_status)
+{
+    if (!h || !per_instance_status) return SF_EINVAL;
+    SF_TRY(cudaDeviceSynchronize());
+    SF_TRY(cudaMemcpy(per_instance_status, h->status_dev.p, sizeof(int32_t) * h->d.n_inst, cudaMemcpyDeviceToHost));
+    SF_TRY(cudaMemset(h->status_dev.p, 0, sizeof(int32_t) * h->d.n_inst));
+    return SF_OK;
+}
+
+extern "C" int sf_shape_operator(const sf_handle *h, int32_t inst, int32_t which, double *host_out)
+{
+    if (!h || !host_out || inst < 0 || inst >= h->d.n_inst || which < 0 || which > 3) return SF_EINVAL;
+    const Shape &S = h->shapes_h[h->inst_shape[inst]];
+    const int nxi = h->d.n_xi;
+    const double *src;
+    size_t cnt;
+    switch (which) {
+    case 0: src = (const double *)h->W64.p + S.off_W; cnt = (size_t)S.H * nxi; break;
+    case 1: src = (const double *)h->P64.p + S.off_P; cnt = (size_t)S.N * S.N; break;
+    case 2: src = (const double *)h->Pb64.p + S.off_Pb; cnt = (size_t)S.N * 2 * S.n; break;
+    default: src = (const double *)h->S64.p + S.off_S; cnt = 2 * (size_t)nxi * nxi + 4 * (size_t)nxi; break;
+    }
+    SF_TRY(cudaDeviceSynchronize());
+    SF_TRY(cudaMemcpy(host_out, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+    return SF_OK;
+}
+
+extern "C" const char *sf_strerror(int32_t code)
+{
+    switch (code) {
+    case SF_OK: return "ok";
+    case SF_EINVAL: return "invalid argument";
+    case SF_ESHAPE: return "inconsistent shapes";
+    case SF_ECUDA: return "CUDA runtime error";
+    case SF_ENOMEM: return "out of memory";
+    case SF_ETIMEOUT: return "bounded device wait ran out";
+    case SF_ENONFINITE: return "non-finite value in an iterate";
+    case SF_ESTATE: return "call order violated";
+    case SF_EUNSUPPORTED: return "option not supported";
+    default: return "unknown status";
+    }
+}
+
+extern "C" int32_t sf_version(void) { return 100; }

@@ -1,0 +1,281 @@
+// FP64 factorisation of the xi_bar-step operator, once per (n, n_obs, H) shape.
+//
+// The xi_bar step (Appendix, eq. xi_step) is the equality-constrained QP
+//   argmin_x 1/2 x'Hx - eta'x  s.t.  A x = b,   H = I + rho F'F + rho G'G,
+// whose matrix does not depend on the candidate, so it is factored once and
+// stored (the Appendix's remark on refactorisation: only rho or the horizon
+// change it).  With F_r = D (x) W (pair incidence), F_o = I (x) stack(W) and
+// the two-sided box G = [I (x) W; -I (x) W], the Hessian is
+//   H = I_N + rho ((n + n_obs + 2) I_n - 1 1') (x) W'W,
+// assembled here from that identity and then factored densely:
+//   H = L L' (Cholesky), Hinv = L^-T L^-1, Y = Hinv A', S = A Y (Schur
+//   complement), P_b = Y S^-1, P_eta = Hinv - P_b Y'.
+// so that argmin = P_eta eta + P_b b.  Every step runs in FP64 on the GPU.
+#include <math.h>
+
+#include "sf_internal.cuh"
+
+namespace sf {
+
+// Bernstein basis W[k][c] = C(deg, c) tau^c (1 - tau)^(deg - c), tau = k / (H - 1)
+__global__ void k_basis(const Shape *sh, int nxi, double *W)
+{
+    const Shape S = sh[blockIdx.x];
+    double *Ws = W + S.off_W;
+    const int deg = nxi - 1;
+    for (int e = threadIdx.x; e < S.H * nxi; e += blockDim.x) {
+        const int k = e / nxi, c = e % nxi;
+        const double tau = (double)k / (double)(S.H - 1);
+        double bin = 1.0;
+        for (int q = 1; q <= c; ++q) bin = bin * (double)(deg - c + q) / (double)q;
+        Ws[e] = bin * pow(tau, (double)c) * pow(1.0 - tau, (double)(deg - c));
+    }
+}
+
+__global__ void k_build_H(const Shape *sh, int nxi, double rho, const double *W, double *Hs)
+{
+    const Shape S = sh[blockIdx.y];
+    const int N = S.N;
+    double *Hm = Hs + S.off_P;
+    const double *Ws = W + S.off_W;
+    const double cdiag = (double)(S.n + S.n_obs + 2);
+    const int64_t tot = (int64_t)N * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / N), c = (int)(e % N);
+        const int i = r / nxi, u = r % nxi, j = c / nxi, v = c % nxi;
+        double wtw = 0.0;
+        for (int k = 0; k < S.H; ++k) wtw += Ws[k * nxi + u] * Ws[k * nxi + v];
+        const double lap = (i == j ? cdiag : 0.0) - 1.0;
+        Hm[e] = (r == c ? 1.0 : 0.0) + rho * lap * wtw;
+    }
+}
+
+// Right-looking Cholesky, one CTA per shape, in place (lower triangle).  info = 0 or pivot + 1.
+__global__ void k_cholesky(const Shape *sh, double *Hs, int *info)
+{
+    const Shape S = sh[blockIdx.x];
+    const int N = S.N, tid = threadIdx.x, nt = blockDim.x;
+    double *A = Hs + S.off_P;
+    __shared__ double piv;
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
+    for (int j = 0; j < N; ++j) {
+        __syncthreads();
+        if (tid == 0) {
+            double d = A[(int64_t)j * N + j];
+            if (!(d > 0.0)) {
+                if (!bad) bad = j + 1;
+                d = 1.0;
+            }
+            piv = sqrt(d);
+            A[(int64_t)j * N + j] = piv;
+        }
+        __syncthreads();
+        const double p = piv;
+        for (int i = j + 1 + tid; i < N; i += nt) A[(int64_t)i * N + j] /= p;
+        __syncthreads();
+        const int m = N - j - 1;
+        const int64_t tot = (int64_t)m * m;
+        for (int64_t t = tid; t < tot; t += nt) {
+            const int ii = (int)(t / m), kk = (int)(t % m);
+            if (kk <= ii) {
+                const int i = j + 1 + ii, k = j + 1 + kk;
+                A[(int64_t)i * N + k] -= A[(int64_t)i * N + j] * A[(int64_t)k * N + j];
+            }
+        }
+    }
+    __syncthreads();
+    for (int64_t t = tid; t < (int64_t)N * N; t += nt) {
+        const int i = (int)(t / N), k = (int)(t % N);
+        if (k > i) A[t] = 0.0;
+    }
+    if (tid == 0) info[blockIdx.x] = bad;
+}
+
+// Hinv = (L L')^-1, one thread per column: forward then backward substitution.
+__global__ void k_chol_inverse(const Shape *sh, const double *Ls_pool, double *X_pool)
+{
+    const Shape S = sh[blockIdx.y];
+    const int N = S.N;
+    if (blockIdx.x * blockDim.x >= N) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    const double *L = Ls_pool + S.off_P;
+    double *X = X_pool + S.off_P;
+    for (int i = 0; i < N; ++i) {
+        double s = (i == q) ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) s -= L[(int64_t)i * N + k] * X[(int64_t)k * N + q];
+        X[(int64_t)i * N + q] = s / L[(int64_t)i * N + i];
+    }
+    for (int i = N - 1; i >= 0; --i) {
+        double s = X[(int64_t)i * N + q];
+        for (int k = i + 1; k < N; ++k) s -= L[(int64_t)k * N + i] * X[(int64_t)k * N + q];
+        X[(int64_t)i * N + q] = s / L[(int64_t)i * N + i];
+    }
+}
+
+// A selects, per robot i, the basis rows k = 0 (start) and k = H-1 (goal): row q = 2i + s.
+__device__ __forceinline__ double arow(const double *Ws, int nxi, int H, int s, int c)
+{
+    return Ws[(s ? H - 1 : 0) * nxi + c];
+}
+
+// Per shape (one CTA): Y = Hinv A', S = A Y, Cholesky of S, Sinv, P_b = Y Sinv.
+// Y goes to Ypool (N x 2n), S / Sinv to Spool ((2n)^2 each, within the N^2 slot).
+__global__ void k_schur(const Shape *sh, int nxi, const double *W, const double *Hinv, double *Ypool,
+                        double *Spool, double *Pb, int *info)
+{
+    const Shape S = sh[blockIdx.x];
+    const int N = S.N, n = S.n, m = 2 * n, tid = threadIdx.x, nt = blockDim.x;
+    const double *Ws = W + S.off_W;
+    const double *Hi = Hinv + S.off_P;
+    double *Y = Ypool + S.off_P;
+    double *Sm = Spool + S.off_P;
+    double *Si = Sm + (int64_t)m * m;
+    double *B = Pb + S.off_Pb;
+    for (int64_t e = tid; e < (int64_t)N * m; e += nt) {
+        const int r = (int)(e / m), q = (int)(e % m), i = q / 2, s = q % 2;
+        double acc = 0.0;
+        for (int c = 0; c < nxi; ++c) acc += Hi[(int64_t)r * N + i * nxi + c] * arow(Ws, nxi, S.H, s, c);
+        Y[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) {
+        const int q = e / m, q2 = e % m, i = q / 2, s = q % 2;
+        double acc = 0.0;
+        for (int c = 0; c < nxi; ++c) acc += arow(Ws, nxi, S.H, s, c) * Y[(int64_t)(i * nxi + c) * m + q2];
+        Sm[e] = acc;
+    }
+    // Cholesky of S (m <= 2 * 64 * ... small), then Sinv column by column
+    __shared__ double piv;
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
+    for (int j = 0; j < m; ++j) {
+        __syncthreads();
+        if (tid == 0) {
+            double d = Sm[j * m + j];
+            if (!(d > 0.0)) {
+                if (!bad) bad = N + j + 1;
+                d = 1.0;
+            }
+            piv = sqrt(d);
+            Sm[j * m + j] = piv;
+        }
+        __syncthreads();
+        for (int i = j + 1 + tid; i < m; i += nt) Sm[i * m + j] /= piv;
+        __syncthreads();
+        const int mm = m - j - 1;
+        for (int t = tid; t < mm * mm; t += nt) {
+            const int ii = t / mm, kk = t % mm;
+            if (kk <= ii) Sm[(j + 1 + ii) * m + j + 1 + kk] -= Sm[(j + 1 + ii) * m + j] * Sm[(j + 1 + kk) * m + j];
+        }
+    }
+    __syncthreads();
+    for (int q = tid; q < m; q += nt) {
+        for (int i = 0; i < m; ++i) {
+            double s = (i == q) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= Sm[i * m + k] * Si[k * m + q];
+            Si[i * m + q] = s / Sm[i * m + i];
+        }
+        for (int i = m - 1; i >= 0; --i) {
+            double s = Si[i * m + q];
+            for (int k = i + 1; k < m; ++k) s -= Sm[k * m + i] * Si[k * m + q];
+            Si[i * m + q] = s / Sm[i * m + i];
+        }
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < (int64_t)N * m; e += nt) {
+        const int r = (int)(e / m), q = (int)(e % m);
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc += Y[(int64_t)r * m + k] * Si[k * m + q];
+        B[e] = acc;
+    }
+    if (tid == 0 && bad && !info[blockIdx.x]) info[blockIdx.x] = bad;
+}
+
+// P_eta = Hinv - P_b Y'   (in place over Hinv)
+__global__ void k_peta(const Shape *sh, const double *Ypool, const double *Pb, double *P)
+{
+    const Shape S = sh[blockIdx.y];
+    const int N = S.N, m = 2 * S.n;
+    const double *Y = Ypool + S.off_P;
+    const double *B = Pb + S.off_Pb;
+    double *Pe = P + S.off_P;
+    const int64_t tot = (int64_t)N * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / N), c = (int)(e % N);
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc += B[(int64_t)r * m + k] * Y[(int64_t)c * m + k];
+        Pe[e] -= acc;
+    }
+}
+
+// Kronecker blocks of the dense operators: P_eta = (I - Q) (x) P_dev + Q (x) P_mean with
+// Q = 11'/n, read off robot blocks (0,0) and (0,1); the same for P_b with B_dev, B_mean.
+// Layout per shape at off_S: P_dev [nxi][nxi], P_mean [nxi][nxi], B_dev [nxi][2], B_mean [nxi][2].
+__global__ void k_structured(const Shape *sh, int nxi, const double *P, const double *Pb, double *Sx)
+{
+    const Shape S = sh[blockIdx.x];
+    const int N = S.N, n = S.n, m = 2 * n;
+    const double *Pe = P + S.off_P;
+    const double *B = Pb + S.off_Pb;
+    double *o = Sx + S.off_S;
+    for (int e = threadIdx.x; e < nxi * nxi; e += blockDim.x) {
+        const int u = e / nxi, v = e % nxi;
+        const double d0 = Pe[(int64_t)u * N + v];
+        const double d1 = n > 1 ? Pe[(int64_t)u * N + nxi + v] : 0.0;
+        o[e] = n > 1 ? d0 - d1 : d0;
+        o[nxi * nxi + e] = d0 + (n - 1) * d1;
+    }
+    for (int e = threadIdx.x; e < nxi * 2; e += blockDim.x) {
+        const int u = e / 2, s = e % 2;
+        const double d0 = B[(int64_t)u * m + s];
+        const double d1 = n > 1 ? B[(int64_t)u * m + 2 + s] : 0.0;
+        o[2 * nxi * nxi + e] = n > 1 ? d0 - d1 : d0;
+        o[2 * nxi * nxi + 2 * nxi + e] = d0 + (n - 1) * d1;
+    }
+}
+
+__global__ void k_convert(const double *src, float *dst, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (float)src[e];
+}
+
+cudaError_t convert_pool(const double *src, float *dst, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    k_convert<<<grid, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t factor_shapes(const Shape *shapes_dev, int n_shapes, const Shape *shapes_host, int nxi,
+                          double rho, double *W64, double *P64, double *Pb64, double *S64,
+                          double *scratch, int64_t scratch_elems, int *info, cudaStream_t s)
+{
+    // scratch holds three pools laid out like P64: L (Cholesky), Y, S
+    (void)scratch_elems;
+    int maxN = 0;
+    int64_t poolP = 0;
+    for (int i = 0; i < n_shapes; ++i) {
+        if (shapes_host[i].N > maxN) maxN = shapes_host[i].N;
+        int64_t end = shapes_host[i].off_P + (int64_t)shapes_host[i].N * shapes_host[i].N;
+        if (end > poolP) poolP = end;
+    }
+    double *Lp = scratch, *Yp = scratch + poolP, *Sp = scratch + 2 * poolP;
+    k_basis<<<n_shapes, 256, 0, s>>>(shapes_dev, nxi, W64);
+    const int64_t hblocks = ((int64_t)maxN * maxN + 255) / 256;
+    dim3 gH((unsigned)(hblocks > 1024 ? 1024 : hblocks), n_shapes);
+    k_build_H<<<gH, 256, 0, s>>>(shapes_dev, nxi, rho, W64, Lp);
+    k_cholesky<<<n_shapes, 1024, 0, s>>>(shapes_dev, Lp, info);
+    dim3 gI((maxN + 31) / 32, n_shapes);
+    k_chol_inverse<<<gI, 32, 0, s>>>(shapes_dev, Lp, P64);
+    k_schur<<<n_shapes, 256, 0, s>>>(shapes_dev, nxi, W64, P64, Yp, Sp, Pb64, info);
+    k_peta<<<gH, 256, 0, s>>>(shapes_dev, Yp, Pb64, P64);
+    k_structured<<<n_shapes, 128, 0, s>>>(shapes_dev, nxi, P64, Pb64, S64);
+    return cudaGetLastError();
+}
+
+}  // namespace sf
