@@ -49,7 +49,8 @@ enum {
     SF_ETIMEOUT = 5,    /* a bounded device-side wait ran out (reported per instance)     */
     SF_ENONFINITE = 6,  /* NaN/Inf met in an iterate (reported per instance)              */
     SF_ESTATE = 7,      /* call order violated (e.g. backward without checkpoints)        */
-    SF_EUNSUPPORTED = 8 /* option not built into this library                             */
+    SF_EUNSUPPORTED = 8, /* option not built into this library                            */
+    SF_ETOOBIG = 9       /* sizes beyond the fixed limits of sf_solve_noalloc                  */
 };
 
 /* ---- precision of the iteration ------------------------------------------ */
@@ -208,6 +209,48 @@ int sf_profile(sf_handle *h, int32_t enable);
  * Synchronises on the recorded events.  Errors: SF_EINVAL, SF_ESTATE (profiling off).
  */
 int sf_kernel_times(sf_handle *h, float *ms_out);
+
+/*
+ * sf_solve_noalloc — the same SF solve as sf_create + sf_solve with SF_FP32 and
+ * SF_PROJ_STRUCTURED, for a batch whose instances all share one shape, in one call
+ * that allocates no memory at all.  The paper has no counterpart to this call.
+ *
+ * Who needs it: code that must not allocate device memory once it is running — a
+ * robot's control loop with a fixed memory budget set at start-up, or a plug-in
+ * running inside a host framework that owns every device allocation and forbids its
+ * plug-ins to call cudaMalloc — cannot use sf_create, which allocates the factor and
+ * workspace memory of a handle.  This call instead keeps its working memory (instance
+ * table, basis, the projection's Kronecker blocks, status words) in one fixed array
+ * of about 450 KB compiled into the library, which every GPU that loads the library
+ * holds until the process exits.
+ *
+ *  n_d, n_xi, rho  as in sf_desc (2 or 3, 4..32, > 0)
+ *  shape           host pointer to the one sf_shape every instance has
+ *  n_inst          1 .. SF_NOALLOC_MAX_INST instances
+ *  bnd, obs_c, obs_ab, xi_cand   device float arrays packed as sf_layout would pack
+ *                  n_inst copies of `shape` (instance k's coefficients start at
+ *                  k * n_d * n * n_xi, and so on)
+ *  iters           >= 0
+ *  xi_out, lam_out device float [n_inst * n_d * n * n_xi]; lam_out may be NULL
+ *  resid_out       device double [n_inst][SF_NRES] or NULL (iterations-to-tolerance
+ *                  uses tol = 1e-3 m)
+ *  stream          cudaStream_t
+ * Limits: n_inst <= SF_NOALLOC_MAX_INST, H <= SF_NOALLOC_MAX_H, n_xi <= 32; larger
+ * sizes return SF_ETOOBIG before anything is launched.  Other bad arguments return
+ * SF_EINVAL; CUDA failures SF_ECUDA.
+ * Set-up: the first call on each device looks up the device address of the fixed
+ * array (with that device current); make that first call before any stream capture.
+ * Sharing: every call, on every stream, uses the same array, which keeps the last
+ * call's contents (each call rewrites what it reads and clears its status words),
+ * so calls whose work overlaps on the GPU race with each other: serialise them.
+ * Per-instance status words are not reported; a non-finite iterate shows as a
+ * non-finite entry of resid_out.
+ */
+#define SF_NOALLOC_MAX_INST 256
+#define SF_NOALLOC_MAX_H 1024
+int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_shape *shape, int32_t n_inst,
+                     const float *bnd, const float *obs_c, const float *obs_ab, const float *xi_cand,
+                     int32_t iters, float *xi_out, float *lam_out, double *resid_out, void *stream);
 
 /* sf_strerror — static description of a status code. */
 const char *sf_strerror(int32_t code);

@@ -528,6 +528,7 @@ extern "C" const char *sf_strerror(int32_t code)
     case SF_ENONFINITE: return "non-finite value in an iterate";
     case SF_ESTATE: return "call order violated";
     case SF_EUNSUPPORTED: return "option not supported";
+    case SF_ETOOBIG: return "size beyond the fixed limits of sf_solve_noalloc";
     default: return "unknown status";
     }
 }

@@ -14,7 +14,9 @@ import torch
 
 from . import build as _build
 
-SF_OK, SF_EINVAL, SF_ESHAPE, SF_ECUDA, SF_ENOMEM, SF_ETIMEOUT, SF_ENONFINITE, SF_ESTATE, SF_EUNSUPPORTED = range(9)
+(SF_OK, SF_EINVAL, SF_ESHAPE, SF_ECUDA, SF_ENOMEM, SF_ETIMEOUT, SF_ENONFINITE, SF_ESTATE, SF_EUNSUPPORTED,
+ SF_ETOOBIG) = range(10)
+SF_NOALLOC_MAX_INST, SF_NOALLOC_MAX_H = 256, 1024
 SF_FP64, SF_FP32, SF_TF32, SF_BF16X3, SF_BF16 = range(5)
 SF_PROJ_DENSE, SF_PROJ_STRUCTURED = 0, 1
 SF_LAYOUT_XI, SF_LAYOUT_BND, SF_LAYOUT_OBS, SF_LAYOUT_OBS_AB = range(4)
@@ -25,7 +27,8 @@ PROJECTIONS = {"dense": SF_PROJ_DENSE, "structured": SF_PROJ_STRUCTURED}
 
 # every symbol declared in include/sf.h
 EXPORTS = ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
-           "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_strerror", "sf_version")
+           "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_strerror",
+           "sf_version")
 SF_KT_FORWARD, SF_KT_RESIDUAL, SF_KT_BACKWARD, SF_NKT = range(4)
 
 
@@ -72,11 +75,13 @@ def lib(path: str | None = None):
         L.sf_shape_operator.argtypes = [vp, i32, i32, ct.POINTER(ct.c_double)]
         L.sf_profile.argtypes = [vp, i32]
         L.sf_kernel_times.argtypes = [vp, ct.POINTER(ct.c_float)]
+        L.sf_solve_noalloc.argtypes = [i32, i32, ct.c_double, ct.POINTER(sf_shape), i32, vp, vp, vp, vp, i32, vp,
+                                       vp, vp, vp]
         L.sf_strerror.argtypes = [i32]
         L.sf_strerror.restype = ct.c_char_p
         L.sf_version.restype = i32
         for f in ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
-                  "sf_shape_operator", "sf_profile", "sf_kernel_times"):
+                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
