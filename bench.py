@@ -309,6 +309,7 @@ def main():
             "config": {"workload": cfg.name, "instances": len(insts), "robots": cfg.n[0], "obstacles": cfg.n_obs[0],
                        "horizon": cfg.H[0], "iterations": iters, "n_d": nd, "n_xi": 11, "rho": RHO,
                        "precision": a.precision, "projection": a.proj, "l2": "flushed between steps (256 MB write)",
+                       "cluster_ctas_per_instance": solver.launch()[0], "threads_per_cta": solver.launch()[1],
                        "parallelism": "instances sharded by rank" if world > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
                          "traffic": None, "kernel": "k_forward", "kernel_ms": fwd_avg,

@@ -193,6 +193,20 @@ int sf_get_status(sf_handle *h, int32_t *per_instance_status);
  */
 int sf_shape_operator(const sf_handle *h, int32_t inst, int32_t which, double *host_out);
 
+/*
+ * sf_set_launch — override the launch geometry of this handle's kernels:
+ *  cluster   CTAs that share one instance (a thread-block cluster, each CTA taking a
+ *            contiguous share of the timesteps), 1..8, or 0 for the automatic choice
+ *            (enough clusters to cover the SMs)
+ *  threads   threads per CTA, a multiple of 32 in 64..512, or 0 for 512
+ * Results do not depend on the geometry beyond rounding order.  Errors: SF_EINVAL,
+ * SF_EUNSUPPORTED (an instance does not fit in shared memory with this geometry).
+ */
+int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads);
+
+/* sf_get_launch — the geometry in use: cluster, threads, staged projection rows. */
+int sf_get_launch(const sf_handle *h, int32_t *cluster, int32_t *threads, int32_t *p_rows);
+
 /* Kernel timing slots of sf_kernel_times */
 enum { SF_KT_FORWARD = 0, SF_KT_RESIDUAL = 1, SF_KT_BACKWARD = 2, SF_NKT = 3 };
 

@@ -60,9 +60,7 @@ struct sf_handle {
     int n_slots = 0;
     int64_t xi_total = 0;
     // launch configuration
-    int threads = 256;
-    size_t smem_fwd = 0, smem_res = 0;
-    int p_smem = 0;
+    Plan plan;
     int smem_optin = 0;
     int num_sms = 0;
     SolveRecord last;
@@ -82,23 +80,46 @@ static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SF_OK : (e == 
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Shared memory of the forward kernel for one instance (mirrors the carve in k_forward).
-static size_t fwd_bytes(const sf_handle *h, const sf_shape &s, int hc, bool with_p)
+int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
+                     int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out)
 {
-    const int nd = h->d.n_d, nxi = h->d.n_xi, N = s.n * nxi;
-    size_t t = (size_t)s.H * nxi + 5 * (size_t)nd * N + (size_t)nd * s.n * hc + (size_t)s.n_obs * (nd + 4) +
-               (size_t)nd * s.n * 2;
-    if (h->d.proj == SF_PROJ_STRUCTURED) t += 2 * (size_t)nxi * nxi + 4 * (size_t)nxi + (size_t)nd * nxi * 2;
-    size_t b = align16(t * h->esz) + kRedDoubles * sizeof(double);
-    if (with_p) b += (size_t)N * N * h->esz;
-    return b;
-}
-
-static size_t res_bytes(const sf_handle *h, const sf_shape &s, int hc)
-{
-    const int nd = h->d.n_d, nxi = h->d.n_xi, N = s.n * nxi;
-    size_t t = (size_t)s.H * nxi + (size_t)nd * N + (size_t)nd * s.n * hc + (size_t)s.n_obs * (nd + 4) + kRedDoubles;
-    return t * sizeof(double);
+    Plan p;
+    p.threads = threads;
+    int minH = H[0];
+    for (int i = 1; i < n_inst; ++i) minH = std::min(minH, H[i]);
+    int C = csize_req > 0 ? csize_req : std::max(1, num_sms / std::max(1, n_inst));
+    C = std::max(1, std::min(std::min(C, kMaxCluster), minH));
+    p.csize = C;
+    size_t need = 0, need_r = 0;
+    int maxL = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const int own = (H[i] + C - 1) / C;
+        int hc = own;
+        auto bytes = [&](int h, int rows) {
+            return (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz).total * esz;
+        };
+        while (hc > 1 && bytes(hc, 0) > (size_t)optin) --hc;
+        if (bytes(hc, 0) > (size_t)optin) return SF_EUNSUPPORTED;
+        hc_out[i] = hc;
+        need = std::max(need, bytes(hc, 0));
+        maxL = std::max(maxL, (n[i] * nxi + C - 1) / C);
+        const size_t r1 = (size_t)residual_doubles(nd, nxi, H[i], n[i], nobs[i], 1) * sizeof(double);
+        if (r1 > (size_t)optin) return SF_EUNSUPPORTED;
+        need_r = std::max(need_r, (size_t)residual_doubles(nd, nxi, H[i], n[i], nobs[i], own) * sizeof(double));
+    }
+    if (proj == SF_PROJ_DENSE) {
+        size_t with_p = 0;
+        for (int i = 0; i < n_inst; ++i)
+            with_p = std::max(with_p, (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], maxL, esz).total * esz);
+        if (with_p <= (size_t)optin) {
+            p.p_rows = maxL;
+            need = with_p;
+        }
+    }
+    p.smem_fwd = need;
+    p.smem_res = std::min((size_t)optin, need_r);
+    *out = p;
+    return SF_OK;
 }
 
 static int validate(const sf_desc *d)
@@ -149,7 +170,7 @@ static int upload_instances(sf_handle *h)
         x.off_obs = h->off[SF_LAYOUT_OBS][i];
         x.off_oab = h->off[SF_LAYOUT_OBS_AB][i];
     }
-    SF_TRY(h->inst_dev.alloc(sizeof(Inst<T>) * I.size()));
+    if (!h->inst_dev.p) SF_TRY(h->inst_dev.alloc(sizeof(Inst<T>) * I.size()));
     SF_TRY(cudaMemcpy(h->inst_dev.p, I.data(), sizeof(Inst<T>) * I.size(), cudaMemcpyHostToDevice));
     return SF_OK;
 }
@@ -232,26 +253,19 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
     }
     h->n_shapes = (int)h->shapes_h.size();
 
-    // launch geometry: chunk of timesteps per instance, shared memory
-    h->threads = kMaxThreads;
-    h->hc.resize(B);
-    const size_t budget = (size_t)h->smem_optin;
-    size_t need = 0, need_p = 0, need_r = 0;
-    for (int i = 0; i < B; ++i) {
-        const sf_shape &s = h->shp[i];
-        int hc = std::min(s.H, kIPT * h->threads / s.n);
-        if (hc < 1) hc = 1;
-        while (hc > 1 && fwd_bytes(h, s, hc, false) > budget) --hc;
-        if (fwd_bytes(h, s, hc, false) > budget) { destroy_all(h); delete h; return SF_EUNSUPPORTED; }
-        h->hc[i] = hc;
-        need = std::max(need, fwd_bytes(h, s, hc, false));
-        need_p = std::max(need_p, fwd_bytes(h, s, hc, true));
-        need_r = std::max(need_r, res_bytes(h, s, 1));
+    // launch geometry: cluster size, chunk of timesteps per instance, shared memory
+    {
+        std::vector<int> vn(B), vo(B), vH(B);
+        for (int i = 0; i < B; ++i) {
+            vn[i] = h->shp[i].n;
+            vo[i] = h->shp[i].n_obs;
+            vH[i] = h->shp[i].H;
+        }
+        h->hc.resize(B);
+        int prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
+                               h->smem_optin, 0, kMaxThreads, &h->plan, h->hc.data());
+        if (prc) { destroy_all(h); delete h; return prc; }
     }
-    h->p_smem = (desc->proj == SF_PROJ_DENSE && need_p <= budget) ? 1 : 0;
-    h->smem_fwd = h->p_smem ? need_p : need;
-    h->smem_res = std::min(budget, std::max(need_r, (size_t)96 * 1024));
-    if (need_r > budget) { destroy_all(h); delete h; return SF_EUNSUPPORTED; }
 
     // instance order: largest work first
     h->order.resize(B);
@@ -369,7 +383,8 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
     a.nxi = h->d.n_xi;
     a.iters = iters;
     a.n_inst = h->d.n_inst;
-    a.p_smem = h->p_smem;
+    a.csize = h->plan.csize;
+    a.p_rows = h->plan.p_rows;
     a.proj = h->d.proj;
     a.rho = (T)h->d.rho;
     a.tol = h->d.tol;
@@ -397,10 +412,9 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
         a.ck_every = h->d.ckpt_every;
         a.ck_slot = h->xi_total;
     }
-    int grid = h->d.n_inst;
     for (int k = 0; k < SF_NKT; ++k) h->ev_used[k] = false;
     if (h->profile) SF_TRY(cudaEventRecord(h->ev[0], st));
-    SF_TRY(launch_forward(a, grid, h->threads, h->smem_fwd, st));
+    SF_TRY(launch_forward(a, h->plan.threads, h->plan.smem_fwd, st));
     if (h->profile) {
         SF_TRY(cudaEventRecord(h->ev[1], st));
         h->ev_used[SF_KT_FORWARD] = true;
@@ -422,9 +436,10 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
         r.its = its;
         r.iters = iters;
         r.status = a.status;
-        r.smem_doubles = (int64_t)(h->smem_res / sizeof(double));
+        r.smem_doubles = (int64_t)(h->plan.smem_res / sizeof(double));
+        r.csize = h->plan.csize;
         if (h->profile) SF_TRY(cudaEventRecord(h->ev[2], st));
-        SF_TRY(launch_residual(r, h->threads, h->smem_res, st));
+        SF_TRY(launch_residual(r, h->plan.threads, h->plan.smem_res, st));
         if (h->profile) {
             SF_TRY(cudaEventRecord(h->ev[3], st));
             h->ev_used[SF_KT_RESIDUAL] = true;
@@ -464,6 +479,37 @@ extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void 
     if (!h) return SF_EINVAL;
     if (!h->last.valid) return SF_ESTATE;
     return SF_EUNSUPPORTED;
+}
+
+extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
+{
+    if (!h || cluster < 0 || cluster > kMaxCluster || threads < 0 || threads > kMaxThreads || threads % 32 ||
+        (threads > 0 && threads < 64))
+        return SF_EINVAL;
+    const int B = h->d.n_inst;
+    std::vector<int> vn(B), vo(B), vH(B), hc(B);
+    for (int i = 0; i < B; ++i) {
+        vn[i] = h->shp[i].n;
+        vo[i] = h->shp[i].n_obs;
+        vH[i] = h->shp[i].H;
+    }
+    Plan p;
+    int rc = plan_forward(h->d.n_d, h->d.n_xi, h->esz, h->d.proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
+                          h->smem_optin, cluster, threads ? threads : kMaxThreads, &p, hc.data());
+    if (rc) return rc;
+    SF_TRY(cudaDeviceSynchronize());
+    h->plan = p;
+    h->hc = hc;
+    return h->esz == 8 ? upload_instances<double>(h) : upload_instances<float>(h);
+}
+
+extern "C" int sf_get_launch(const sf_handle *h, int32_t *cluster, int32_t *threads, int32_t *p_rows)
+{
+    if (!h) return SF_EINVAL;
+    if (cluster) *cluster = h->plan.csize;
+    if (threads) *threads = h->plan.threads;
+    if (p_rows) *p_rows = h->plan.p_rows;
+    return SF_OK;
 }
 
 extern "C" int sf_profile(sf_handle *h, int32_t enable)

@@ -1,29 +1,34 @@
-// Persistent SF forward kernel: every iteration of T (eq. fixed_point) for one
-// instance runs inside one CTA, with the iterate, multipliers, candidate, basis,
-// positions and (when it fits) the projection operator resident in shared
-// memory.  Instances are taken from a largest-first order.
+// Persistent SF forward kernel.  Each instance is owned by one thread-block
+// cluster of C CTAs that runs every iteration of T (eq. fixed_point) with the
+// iterate, multipliers, candidate, basis and positions in shared memory.  CTA r
+// of the cluster owns a contiguous share of the horizon's timesteps; the only
+// exchange per iteration is the all-reduce of g = F'r_1 + G'r_2 through
+// distributed shared memory (and, for the dense projection, the gather of the
+// projected rows).  Every CTA then holds the same xi_bar and lambda.
 //
-// Per iteration, from the current iterate (xi_bar, lambda):
-//   positions   p = W xi_bar                               (eq. poly)
-//   rows        per (robot i, timestep k): for every partner j and obstacle m the
-//               alpha/beta/d closed forms give e; the row residual r_1 = Delta - e is
-//               accumulated with the sign of the incidence row (F'), plus the box
-//               residual r_2 = max(0, p - p_max) - max(0, p_min - p) (G')
-//                                                          (eqs. alpha_step..s_step)
-//   g           = W' R = F'r_1 + G'r_2                      (Appendix, structure of F, G)
-//   lambda'     = lambda - rho g                            (eq. lambda_step)
+// Per iteration, from (xi_bar, lambda):
+//   positions   p = W xi_bar for this CTA's timesteps          (eq. poly)
+//   rows        per (robot i, timestep k): every partner j and obstacle m gives a
+//               line of sight Delta; the alpha/beta/d closed forms give e and the
+//               row residual r_1 = Delta - e, summed with the sign of the incidence
+//               row (F'); the box adds r_2 = max(0, p - p_max) - max(0, p_min - p) (G')
+//                                                              (eqs. alpha_step..s_step)
+//   g           = W' R over the cluster                       (structure of F, G)
+//   lambda'     = lambda - rho g                                (eq. lambda_step)
 //   xi_bar'     = xi_bar + P_eta (xi - xi_bar + lambda' - rho g) [+ P_b (b - A xi_bar)]
-//                                                          (eq. xi_step, see below)
-// The xi_bar step is applied in correction form: with eta the paper's right-hand
-// side and H = I + rho F'F + rho G'G, eta - H xi_bar = xi - xi_bar + lambda' - rho g,
-// and P_eta H + P_b A = I, so P_eta eta + P_b b equals the line above exactly.
-// The alpha/beta/d steps use the algebraic form of the closed forms: for a row
-// with line of sight Delta and q = ||M^-1 Delta||, e = Delta when q >= 1 and
-// e = Delta / q otherwise (the scaled radial point on the spheroid); Delta = 0
-// maps to e = (a, 0) in 2D and (0, 0, b) in 3D (atan2(0, 0) = 0).
+//                                                              (eq. xi_step)
+// The xi_bar step is applied in correction form: with eta the paper's right-hand side
+// and H = I + rho F'F + rho G'G, eta - H xi_bar = xi - xi_bar + lambda' - rho g and
+// P_eta H + P_b A = I, so this equals P_eta eta + P_b b.
+// The alpha/beta/d steps in algebraic form: with q = ||M^-1 Delta||, e = Delta when
+// q >= 1 and e = Delta / q otherwise; Delta = 0 gives e = (a, 0) in 2D and (0, 0, b)
+// in 3D for the row's own orientation (atan2(0, 0) = 0).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "sf_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sf {
 
@@ -31,38 +36,136 @@ template <typename T> __device__ __forceinline__ T rsq(T x);
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return 1.0 / sqrt(x); }
 
-// One constraint row: adds sg * r_1 to R, the squared norm to rp2 (if count) and the
-// norm to the running max.
+template <typename T, int K>
+struct alignas(K * sizeof(T) >= 16 ? 16 : K * sizeof(T)) Vec {
+    T v[K];
+};
+
+template <int ND> struct NDP { static constexpr int v = ND == 2 ? 2 : 4; };
+
+// An active row (q <= a^2): r_1 = Delta (1 - 1/||M^-1 Delta||), or the tie value tie
+// when Delta = 0.  Adds r_1 to R, its squared norm to rp2 (if count) and to the max.
 template <typename T, int ND>
-__device__ __forceinline__ void add_row(const T (&d)[ND], T ia2, T ib2, T ra, T rb, T sg, T (&R)[ND],
-                                        T &rp2, T &mx, bool count)
+__device__ __forceinline__ void row_active(const T (&d)[ND], T q, T ia2, const T (&tie)[ND], T (&R)[ND], T &rp2,
+                                           T &mx2, bool count)
 {
-    T q2 = (d[0] * d[0] + d[1] * d[1]) * ia2;
-    if (ND == 3) q2 += d[ND - 1] * d[ND - 1] * ib2;
-    if (q2 <= T(1)) {
-        T r1[ND];
-        if (q2 > T(0)) {
-            const T f = T(1) - rsq(q2);
+    T r1[ND];
+    if (q > T(0)) {
+        const T f = T(1) - rsq(q * ia2);
 #pragma unroll
-            for (int ax = 0; ax < ND; ++ax) r1[ax] = d[ax] * f;
-        } else {
+        for (int ax = 0; ax < ND; ++ax) r1[ax] = d[ax] * f;
+    } else {
 #pragma unroll
-            for (int ax = 0; ax < ND; ++ax) r1[ax] = T(0);
-            if (ND == 2) r1[0] = -ra; else r1[ND - 1] = -rb;
+        for (int ax = 0; ax < ND; ++ax) r1[ax] = tie[ax];
+    }
+    T nn = T(0);
+#pragma unroll
+    for (int ax = 0; ax < ND; ++ax) {
+        R[ax] += r1[ax];
+        nn += r1[ax] * r1[ax];
+    }
+    if (count) rp2 += nn;
+    mx2 = fmax(mx2, nn);
+}
+
+// squared scaled distance: dx^2 + dy^2 + kz dz^2 with kz = a^2 / b^2
+template <typename T, int ND>
+__device__ __forceinline__ T qdist(const T (&d)[ND], T kz)
+{
+    T q = d[0] * d[0] + d[1] * d[1];
+    if (ND == 3) q += kz * d[ND - 1] * d[ND - 1];
+    return q;
+}
+
+// Rows of the items (i, k) of one chunk: positions P[i][kl] (vectors), obstacle records
+// ob[m] = (c_x, c_y, [c_z,] a_o^2, ...), result R written to Rb[ax][i][kl].
+template <typename T, int ND>
+__device__ __forceinline__ void rows_chunk(const Inst<T> &I, const Vec<T, NDP<ND>::v> *P, const T *ob,
+                                           const T *obs_g, T *Rb, int k0, int hcc, T &rp2, T &mx2)
+{
+    using VP = Vec<T, NDP<ND>::v>;
+    const int n = I.n, nobs = I.n_obs;
+    const T a2 = I.a * I.a, ia2 = I.ia2, kz = (I.a * I.a) * I.ib2;
+    T tie_f[ND], tie_b[ND];   // r_1 of a coincident pair seen from the row's first / second robot
+#pragma unroll
+    for (int ax = 0; ax < ND; ++ax) tie_f[ax] = tie_b[ax] = T(0);
+    if (ND == 2) { tie_f[0] = -I.a; tie_b[0] = I.a; }
+    else { tie_f[ND - 1] = -I.b; tie_b[ND - 1] = I.b; }
+    for (int e = threadIdx.x; e < n * hcc; e += blockDim.x) {
+        const int i = e / hcc, kl = e - i * hcc, k = k0 + kl;
+        const VP pi = P[i * hcc + kl];
+        T R[ND];
+#pragma unroll
+        for (int ax = 0; ax < ND; ++ax) R[ax] = T(0);
+        // pairs (j, i), j < i: the row's first robot is j
+#pragma unroll 4
+        for (int j = 0; j < i; ++j) {
+            const VP pj = P[j * hcc + kl];
+            T d[ND];
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - pj.v[ax];
+            const T q = qdist<T, ND>(d, kz);
+            if (q <= a2) row_active<T, ND>(d, q, ia2, tie_b, R, rp2, mx2, false);
         }
-        T nn = T(0);
+        // pairs (i, j), j > i: the row's first robot is i
+#pragma unroll 4
+        for (int j = i + 1; j < n; ++j) {
+            const VP pj = P[j * hcc + kl];
+            T d[ND];
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - pj.v[ax];
+            const T q = qdist<T, ND>(d, kz);
+            if (q <= a2) row_active<T, ND>(d, q, ia2, tie_f, R, rp2, mx2, true);
+        }
+        // obstacles: record (c_x, c_y, [c_z], a_o^2 | kz_o, 1/a_o^2, a_o, b_o)
+#pragma unroll 2
+        for (int m = 0; m < nobs; ++m) {
+            const Vec<T, 4> r0 = reinterpret_cast<const Vec<T, 4> *>(ob)[2 * m];
+            T d[ND];
+            if (I.dyn) {
+                const T *c = obs_g + ((int64_t)m * I.H + k) * ND;
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - c[ax];
+            } else {
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - r0.v[ax];
+            }
+            const T a2o = r0.v[3];
+            T q = d[0] * d[0] + d[1] * d[1];
+            if (ND == 3) q += ob[8 * m + 4] * d[ND - 1] * d[ND - 1];
+            if (q <= a2o) {
+                T tie[ND];
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax) tie[ax] = T(0);
+                if (ND == 2) tie[0] = -ob[8 * m + 6]; else tie[ND - 1] = -ob[8 * m + 7];
+                row_active<T, ND>(d, q, ob[8 * m + 5], tie, R, rp2, mx2, true);
+            }
+        }
+        // workspace box (G rows: upper side p <= p_max, lower side -p <= -p_min)
 #pragma unroll
         for (int ax = 0; ax < ND; ++ax) {
-            R[ax] += sg * r1[ax];
-            nn += r1[ax] * r1[ax];
+            const T u = pi.v[ax] - I.pmax[ax];
+            const T l = I.pmin[ax] - pi.v[ax];
+            if (u > T(0)) {
+                R[ax] += u;
+                rp2 += u * u;
+                mx2 = fmax(mx2, u * u);
+            }
+            if (l > T(0)) {
+                R[ax] -= l;
+                rp2 += l * l;
+                mx2 = fmax(mx2, l * l);
+            }
         }
-        if (count) rp2 += nn;
-        mx = fmax(mx, sqrt(nn));
+#pragma unroll
+        for (int ax = 0; ax < ND; ++ax) Rb[(ax * n + i) * hcc + kl] = R[ax];
     }
 }
 
-// (sum, max, sum) block reduction in double; every thread receives the result.
-__device__ __forceinline__ void block_reduce3(double &a, double &b, double &c, double *red)
+// Warp then block reduction of (sum, max, sum) into red[0..2] (all threads participate;
+// the result is valid after the caller's next barrier).
+template <typename T>
+__device__ __forceinline__ void block_reduce3_to(T a, T b, T c, T *red)
 {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -78,7 +181,7 @@ __device__ __forceinline__ void block_reduce3(double &a, double &b, double &c, d
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double x = 0.0, y = 0.0, z = 0.0;
+        T x = T(0), y = T(0), z = T(0);
         for (int q = 0; q < nw; ++q) {
             x += red[q];
             y = fmax(y, red[32 + q]);
@@ -88,274 +191,279 @@ __device__ __forceinline__ void block_reduce3(double &a, double &b, double &c, d
         red[97] = y;
         red[98] = z;
     }
-    __syncthreads();
-    a = red[96];
-    b = red[97];
-    c = red[98];
-}
-
-// Residual stats and R for the items of one timestep chunk [k0, k0 + hcc).
-// pb holds positions [ND][n][hcc]; on return R (registers) has been written over pb.
-template <typename T, int ND>
-__device__ __forceinline__ void rows_chunk(const Inst<T> &I, const T *pb_in, T *pb,
-                                           const T *__restrict__ ob, const T *__restrict__ obs_g, int k0,
-                                           int hcc, T &rp2, T &mx)
-{
-    const int n = I.n, nobs = I.n_obs, tid = threadIdx.x, nt = blockDim.x;
-    T R[kIPT][ND];
-#pragma unroll
-    for (int q = 0; q < kIPT; ++q) {
-#pragma unroll
-        for (int ax = 0; ax < ND; ++ax) R[q][ax] = T(0);
-        const int item = tid + q * nt;
-        if (item < n * hcc) {
-            const int i = item / hcc, kl = item - (item / hcc) * hcc, k = k0 + kl;
-            T pi[ND];
-#pragma unroll
-            for (int ax = 0; ax < ND; ++ax) pi[ax] = pb_in[(ax * n + i) * hcc + kl];
-            // robot pairs (F_r rows): orientation of row (min(i,j), max(i,j))
-            for (int j = 0; j < n; ++j) {
-                if (j == i) continue;
-                const T sg = j > i ? T(1) : T(-1);
-                T d[ND];
-#pragma unroll
-                for (int ax = 0; ax < ND; ++ax) d[ax] = sg * (pi[ax] - pb_in[(ax * n + j) * hcc + kl]);
-                add_row<T, ND>(d, I.ia2, I.ib2, I.a, I.b, sg, R[q], rp2, mx, j > i);
-            }
-            // obstacles (F_o rows)
-            for (int m = 0; m < nobs; ++m) {
-                const T *o = ob + m * (ND + 4);
-                T d[ND];
-                if (I.dyn) {
-                    const T *c = obs_g + ((int64_t)m * I.H + k) * ND;
-#pragma unroll
-                    for (int ax = 0; ax < ND; ++ax) d[ax] = pi[ax] - c[ax];
-                } else {
-#pragma unroll
-                    for (int ax = 0; ax < ND; ++ax) d[ax] = pi[ax] - o[ax];
-                }
-                add_row<T, ND>(d, o[ND], o[ND + 1], o[ND + 2], o[ND + 3], T(1), R[q], rp2, mx, true);
-            }
-            // workspace box (G rows, upper then lower side)
-#pragma unroll
-            for (int ax = 0; ax < ND; ++ax) {
-                const T u = pi[ax] - I.pmax[ax];
-                const T l = I.pmin[ax] - pi[ax];
-                if (u > T(0)) {
-                    R[q][ax] += u;
-                    rp2 += u * u;
-                    mx = fmax(mx, u);
-                }
-                if (l > T(0)) {
-                    R[q][ax] -= l;
-                    rp2 += l * l;
-                    mx = fmax(mx, l);
-                }
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kIPT; ++q) {
-        const int item = tid + q * nt;
-        if (item < n * hcc) {
-            const int i = item / hcc, kl = item - (item / hcc) * hcc;
-#pragma unroll
-            for (int ax = 0; ax < ND; ++ax) pb[(ax * n + i) * hcc + kl] = R[q][ax];
-        }
-    }
 }
 
 template <typename T, int ND>
 __global__ void __launch_bounds__(kMaxThreads) k_forward(FwdArgs<T> A)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
+    cg::cluster_group cl = cg::this_cluster();
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int C = A.csize, cr = (int)cl.block_rank();
     const int nxi = A.nxi;
-    for (int w = blockIdx.x; w < A.n_inst; w += gridDim.x) {
-        const int ii = A.order ? A.order[w] : w;
-        const Inst<T> I = A.inst[ii];
-        const Shape S = A.shapes[I.shape];
-        const int n = I.n, H = I.H, N = I.N, nobs = I.n_obs, hc = I.hc;
-        const int NN = ND * N;
-        const T rho = A.rho;
-        // ---- shared-memory carve (sizes mirror forward_smem_bytes on the host)
-        T *W = sm;
-        T *xb = W + H * nxi;
-        T *lam = xb + NN;
-        T *xc = lam + NN;
-        T *g = xc + NN;
-        T *v = g + NN;
-        T *pb = v + NN;
-        T *ob = pb + ND * n * hc;
-        T *bd = ob + nobs * (ND + 4);
-        T *sx = bd + ND * n * 2;
-        T *endT = sx + (A.proj == SF_PROJ_STRUCTURED ? 2 * nxi * nxi + 4 * nxi + ND * nxi * 2 : 0);
-        size_t off = (size_t)((unsigned char *)endT - smem_raw);
-        off = (off + 15) & ~(size_t)15;
-        double *red = reinterpret_cast<double *>(smem_raw + off);
-        T *Ps = reinterpret_cast<T *>(red + kRedDoubles);
-        // ---- load
-        const T *Wg = A.W + S.off_W;
-        for (int e = tid; e < H * nxi; e += nt) W[e] = Wg[e];
-        const T *xcg = A.xc + I.off_xi;
-        const T *x0g = A.x0 ? A.x0 + I.off_xi : xcg;
-        for (int e = tid; e < NN; e += nt) {
-            xc[e] = xcg[e];
-            xb[e] = x0g[e];
-            lam[e] = A.l0 ? A.l0[I.off_xi + e] : T(0);
+    const int w = blockIdx.x / C;
+    const int ii = A.order ? A.order[w] : w;
+    const Inst<T> I = A.inst[ii];
+    const Shape S = A.shapes[I.shape];
+    const int n = I.n, H = I.H, N = I.N, nobs = I.n_obs, hc = I.hc;
+    const int NN = ND * N;
+    const T rho = A.rho;
+    const bool dense = A.proj == SF_PROJ_DENSE;
+    const T invn = T(1) / T(n);
+    // this CTA's timesteps and projection rows
+    const int k_lo = (int)((int64_t)cr * H / C), k_hi = (int)((int64_t)(cr + 1) * H / C);
+    const int L = (N + C - 1) / C, r_lo = min(N, cr * L), r_hi = min(N, r_lo + L);
+    const FwdCarve cv = forward_carve(ND, nxi, H, n, nobs, hc, A.p_rows, (int)sizeof(T));
+    T *W = sm + cv.W, *xb = sm + cv.xb, *lam = sm + cv.lam, *xc = sm + cv.xc, *v = sm + cv.v;
+    T *gp = sm + cv.gp, *dl = sm + cv.dl, *Rb = sm + cv.Rb, *ob = sm + cv.ob, *bd = sm + cv.bd;
+    T *db = sm + cv.db, *sx = sm + cv.sx, *red = sm + cv.red, *Ps = sm + cv.Ps;
+    Vec<T, NDP<ND>::v> *P = reinterpret_cast<Vec<T, NDP<ND>::v> *>(sm + cv.pb);
+    const int64_t gstride = carve_round(NN + 4, (int)sizeof(T));
+    // ---- load
+    const T *Wg = A.W + S.off_W;
+    for (int e = tid; e < H * nxi; e += nt) W[e] = Wg[e];
+    const T *xcg = A.xc + I.off_xi;
+    const T *x0g = A.x0 ? A.x0 + I.off_xi : xcg;
+    for (int e = tid; e < NN; e += nt) {
+        xc[e] = xcg[e];
+        xb[e] = x0g[e];
+        lam[e] = A.l0 ? A.l0[I.off_xi + e] : T(0);
+    }
+    for (int e = tid; e < ND * n * 2; e += nt) bd[e] = A.bnd[I.off_bnd + e];
+    for (int m = tid; m < nobs; m += nt) {
+        const T ao = A.oab[I.off_oab + 2 * m], bo = A.oab[I.off_oab + 2 * m + 1];
+        T *o = ob + 8 * m;
+        for (int ax = 0; ax < 3; ++ax) o[ax] = (!I.dyn && ax < ND) ? A.obs[I.off_obs + (int64_t)m * ND + ax] : T(0);
+        o[3] = ao * ao;                 // compare d_x^2 + d_y^2 + kz_o d_z^2 with a_o^2
+        o[4] = (ao * ao) / (bo * bo);   // kz_o
+        o[5] = T(1) / (ao * ao);
+        o[6] = ao;
+        o[7] = bo;
+    }
+    const T *Pg = A.P + S.off_P;
+    const T *Pbg = A.Pb + S.off_Pb;
+    if (dense && A.p_rows > 0)
+        for (int e = tid; e < (r_hi - r_lo) * N; e += nt) Ps[e] = Pg[(int64_t)r_lo * N + e];
+    const T *Prow = (dense && A.p_rows > 0) ? Ps - (int64_t)r_lo * N : Pg;   // Prow[r * N + c], r in [r_lo, r_hi)
+    // structured blocks: P_dev, P_mean - P_dev, B_dev, B_mean - B_dev, then mv, pm, mb
+    T *Pdev = sx, *Pdif = sx + nxi * nxi, *Bdev = sx + 2 * nxi * nxi, *Bdif = Bdev + 2 * nxi;
+    T *mv = Bdif + 2 * nxi, *pm = mv + ND * nxi, *mb = pm + ND * nxi;
+    if (!dense) {
+        const T *Sg = A.Sx + S.off_S;
+        for (int e = tid; e < nxi * nxi; e += nt) {
+            Pdev[e] = Sg[e];
+            Pdif[e] = Sg[nxi * nxi + e] - Sg[e];
         }
-        for (int e = tid; e < ND * n * 2; e += nt) bd[e] = A.bnd[I.off_bnd + e];
-        for (int m = tid; m < nobs; m += nt) {
-            const T ao = A.oab[I.off_oab + 2 * m], bo = A.oab[I.off_oab + 2 * m + 1];
-            T *o = ob + m * (ND + 4);
-            if (!I.dyn)
-                for (int ax = 0; ax < ND; ++ax) o[ax] = A.obs[I.off_obs + (int64_t)m * ND + ax];
-            o[ND] = T(1) / (ao * ao);
-            o[ND + 1] = T(1) / (bo * bo);
-            o[ND + 2] = ao;
-            o[ND + 3] = bo;
+        for (int e = tid; e < 2 * nxi; e += nt) {
+            Bdev[e] = Sg[2 * nxi * nxi + e];
+            Bdif[e] = Sg[2 * nxi * nxi + 2 * nxi + e] - Sg[2 * nxi * nxi + e];
         }
-        const T *Pg = A.P + S.off_P;
-        const T *Pbg = A.Pb + S.off_Pb;
-        if (A.p_smem && A.proj == SF_PROJ_DENSE)
-            for (int e = tid; e < N * N; e += nt) Ps[e] = Pg[e];
-        if (A.proj == SF_PROJ_STRUCTURED)
-            for (int e = tid; e < 2 * nxi * nxi + 4 * nxi; e += nt) sx[e] = A.Sx[S.off_S + e];
-        const T *Pm = (A.p_smem && A.proj == SF_PROJ_DENSE) ? Ps : Pg;
-        __syncthreads();
-        // boundary mismatch of the initial iterate: P_b (b - A xi_bar^0) joins the first step
-        int need_b = 0;
-        for (int e = tid; e < ND * n * 2; e += nt) {
-            const int r = e >> 1, s = e & 1;
-            if (xb[r * nxi + (s ? nxi - 1 : 0)] != bd[e]) need_b = 1;
+    }
+    __syncthreads();
+    // b - A xi_bar^0: nonzero only when the initial iterate misses the boundary values
+    int need_b = 0;
+    for (int e = tid; e < ND * n * 2; e += nt) {
+        const int r = e >> 1, s = e & 1;
+        db[e] = bd[e] - xb[r * nxi + (s ? nxi - 1 : 0)];
+        if (db[e] != T(0)) need_b = 1;
+    }
+    need_b = __syncthreads_or(need_b);
+    if (need_b && !dense)
+        for (int e = tid; e < ND * 2; e += nt) {
+            const int ax = e >> 1, s = e & 1;
+            T acc = T(0);
+            for (int i = 0; i < n; ++i) acc += db[(ax * n + i) * 2 + s];
+            mb[e] = acc * invn;
         }
-        need_b = __syncthreads_or(need_b);
 
-        int its_tol = -1;
-        double fp_last = 0.0;
-        int bad = 0;
-        for (int it = 0; it < A.iters; ++it) {
-            if (A.ck_every > 0 && it % A.ck_every == 0) {
+    int its_tol = -1;
+    T fp = T(0), fp_prev = T(0);
+    T gstat[3] = {T(0), T(0), T(0)};
+    bool bad = false;
+    for (int it = 0; it <= A.iters; ++it) {
+        const bool last = it == A.iters;   // the final pass only reduces the last fixed-point step
+        T *gme = gp + (it & 1) * gstride;
+        T rp2 = T(0), mx2 = T(0);
+        if (!last) {
+            if (cr == 0 && A.ck_every > 0 && it % A.ck_every == 0) {
                 const int64_t base = (int64_t)(it / A.ck_every) * A.ck_slot + I.off_xi;
                 for (int e = tid; e < NN; e += nt) {
                     A.ck_x[base + e] = xb[e];
                     A.ck_l[base + e] = lam[e];
                 }
             }
-            for (int e = tid; e < NN; e += nt) g[e] = T(0);
-            T rp2 = T(0), mx = T(0);
-            for (int k0 = 0; k0 < H; k0 += hc) {
-                const int hcc = min(hc, H - k0);
+            for (int e = tid; e < NN; e += nt) gme[e] = T(0);
+            for (int k0 = k_lo; k0 < k_hi; k0 += hc) {
+                const int hcc = min(hc, k_hi - k0);
                 __syncthreads();
-                for (int e = tid; e < ND * n * hcc; e += nt) {
-                    const int r = e / hcc, kl = e - r * hcc;
+                for (int e = tid; e < n * hcc; e += nt) {
+                    const int i = e / hcc, kl = e - i * hcc;
                     const T *wr = W + (k0 + kl) * nxi;
-                    const T *xr = xb + r * nxi;
-                    T s = T(0);
-                    for (int c = 0; c < nxi; ++c) s += wr[c] * xr[c];
-                    pb[r * hcc + kl] = s;
+                    Vec<T, NDP<ND>::v> p;
+#pragma unroll
+                    for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = T(0);
+#pragma unroll
+                    for (int ax = 0; ax < ND; ++ax) {
+                        const T *xr = xb + (ax * n + i) * nxi;
+                        T s0 = T(0), s1 = T(0);
+                        int c = 0;
+                        for (; c + 1 < nxi; c += 2) {
+                            s0 += wr[c] * xr[c];
+                            s1 += wr[c + 1] * xr[c + 1];
+                        }
+                        if (c < nxi) s0 += wr[c] * xr[c];
+                        p.v[ax] = s0 + s1;
+                    }
+                    P[i * hcc + kl] = p;
                 }
                 __syncthreads();
-                rows_chunk<T, ND>(I, pb, pb, ob, A.obs + I.off_obs, k0, hcc, rp2, mx);
+                rows_chunk<T, ND>(I, P, ob, A.obs + I.off_obs, Rb, k0, hcc, rp2, mx2);
                 __syncthreads();
                 for (int e = tid; e < NN; e += nt) {
                     const int r = e / nxi, c = e - r * nxi;
-                    const T *rr = pb + r * hcc;
-                    T s = T(0);
-                    for (int kl = 0; kl < hcc; ++kl) s += W[(k0 + kl) * nxi + c] * rr[kl];
-                    g[e] += s;
+                    const T *rr = Rb + r * hcc;
+                    const T *wc = W + k0 * nxi + c;
+                    T s0 = T(0), s1 = T(0);
+                    int kl = 0;
+                    for (; kl + 1 < hcc; kl += 2) {
+                        s0 += wc[kl * nxi] * rr[kl];
+                        s1 += wc[(kl + 1) * nxi] * rr[kl + 1];
+                    }
+                    if (kl < hcc) s0 += wc[kl * nxi] * rr[kl];
+                    gme[e] += s0 + s1;
                 }
             }
-            __syncthreads();
-            T fp = T(0);
-            for (int e = tid; e < NN; e += nt) {
-                const T gg = g[e];
-                const T ln = lam[e] - rho * gg;
-                const T dl = ln - lam[e];
-                fp += dl * dl;
-                v[e] = xc[e] - xb[e] + ln - rho * gg;
-                lam[e] = ln;
+        }
+        // per-CTA stats (this iteration's rows, the previous iteration's step) -> gme[NN..]
+        block_reduce3_to<T>(rp2, mx2, fp, red);
+        __syncthreads();
+        if (tid == 0) {
+            gme[NN] = red[96];
+            gme[NN + 1] = red[97];
+            gme[NN + 2] = red[98];
+        }
+        cl.sync();
+        if (tid == 0) {
+            T s_rp2 = T(0), s_mx2 = T(0);
+            for (int q = 0; q < C; ++q) {
+                const T *rg = cl.map_shared_rank(gme, q);
+                s_rp2 += rg[NN];
+                s_mx2 = fmax(s_mx2, rg[NN + 1]);
             }
-            __syncthreads();
-            // ---- projection: delta = P_eta v (+ P_b (b - A xi_bar) on the first step) -> g
-            const bool corr_b = need_b && it == 0;
-            if (A.proj == SF_PROJ_DENSE) {
-                for (int r = tid; r < N; r += nt) {
-                    T acc[ND];
+            gstat[0] = s_rp2;
+            gstat[1] = s_mx2;
+            gstat[2] = gme[NN + 2];
+            if (it > 0) {
+                fp_prev = gme[NN + 2];
+                if (!isfinite(fp_prev)) bad = true;
+            }
+            if (!last) {
+                if (!isfinite(s_rp2)) bad = true;
+                const T mxr = sqrt(s_mx2);
+                if (its_tol < 0 && (double)mxr <= A.tol) its_tol = it;
+                if (A.hist && cr == 0) A.hist[(int64_t)ii * A.iters + it] = (float)mxr;
+            }
+        }
+        if (last) break;
+        // g over the cluster (fixed order: the same bits in every CTA), lambda step, correction
+        fp = T(0);
+        for (int e = tid; e < NN; e += nt) {
+            T gg = T(0);
+            for (int q = 0; q < C; ++q) gg += cl.map_shared_rank(gme, q)[e];
+            const T ln = lam[e] - rho * gg;
+            const T dlam = ln - lam[e];
+            fp += dlam * dlam;
+            v[e] = xc[e] - xb[e] + ln - rho * gg;
+            lam[e] = ln;
+        }
+        __syncthreads();
+        const bool corr_b = need_b && it == 0;
+        if (dense) {
+            // rows [r_lo, r_hi) of P_eta v: 8 lanes per row, interleaved columns
+            const int seg = 8, rows = r_hi - r_lo;
+            // the trip count is the same for every thread, so whole warps take part in the shuffles
+            for (int t0 = 0; t0 < rows * seg; t0 += nt) {
+                const int t = t0 + tid;
+                const bool act = t < rows * seg;
+                const int r = r_lo + t / seg, s = t % seg;
+                T acc[ND];
 #pragma unroll
-                    for (int ax = 0; ax < ND; ++ax) acc[ax] = T(0);
-                    for (int c = 0; c < N; ++c) {
-                        const T pv = Pm[(int64_t)c * N + r];
+                for (int ax = 0; ax < ND; ++ax) acc[ax] = T(0);
+                if (act) {
+                    const T *pr = Prow + (int64_t)r * N;
+                    for (int c = s; c < N; c += seg) {
+                        const T pv = pr[c];
 #pragma unroll
                         for (int ax = 0; ax < ND; ++ax) acc[ax] += pv * v[ax * N + c];
                     }
-                    if (corr_b) {
-                        for (int q = 0; q < 2 * n; ++q) {
+                    if (corr_b)
+                        for (int q = s; q < 2 * n; q += seg) {
                             const T pbq = Pbg[(int64_t)r * 2 * n + q];
-                            const int i = q >> 1, s = q & 1;
 #pragma unroll
-                            for (int ax = 0; ax < ND; ++ax)
-                                acc[ax] += pbq * (bd[(ax * n + i) * 2 + s] - xb[(ax * n + i) * nxi + (s ? nxi - 1 : 0)]);
+                            for (int ax = 0; ax < ND; ++ax) acc[ax] += pbq * db[(ax * n + (q >> 1)) * 2 + (q & 1)];
                         }
-                    }
+                }
 #pragma unroll
-                    for (int ax = 0; ax < ND; ++ax) g[ax * N + r] = acc[ax];
-                }
-            } else {
-                // Kronecker form: per axis, with mean m over robots,
-                //   delta_i = P_dev (v_i - m) + P_mean m   (+ the same with B for b - A xi_bar)
-                T *mv = sx + 2 * nxi * nxi + 4 * nxi;   // [ND][nxi] robot means of v
-                T *mb = mv + ND * nxi;                    // [ND][2] robot means of b - A xi_bar
-                for (int e = tid; e < ND * nxi; e += nt) {
-                    const int ax = e / nxi, c = e - ax * nxi;
-                    T s = T(0);
-                    for (int i = 0; i < n; ++i) s += v[(ax * n + i) * nxi + c];
-                    mv[e] = s / T(n);
-                }
-                if (corr_b)
-                    for (int e = tid; e < ND * 2; e += nt) {
-                        const int ax = e >> 1, s = e & 1;
-                        T acc = T(0);
-                        for (int i = 0; i < n; ++i)
-                            acc += bd[(ax * n + i) * 2 + s] - xb[(ax * n + i) * nxi + (s ? nxi - 1 : 0)];
-                        mb[e] = acc / T(n);
-                    }
-                __syncthreads();
-                const T *Pdev = sx, *Pmean = sx + nxi * nxi, *Bdev = sx + 2 * nxi * nxi, *Bmean = Bdev + 2 * nxi;
-                for (int e = tid; e < NN; e += nt) {
-                    const int r = e / nxi, u = e - r * nxi, ax = r / n;
-                    const T *vr = v + r * nxi;
-                    const T *m = mv + ax * nxi;
-                    T acc = T(0);
-                    for (int c = 0; c < nxi; ++c) acc += Pdev[u * nxi + c] * (vr[c] - m[c]) + Pmean[u * nxi + c] * m[c];
-                    if (corr_b) {
-                        for (int s = 0; s < 2; ++s) {
-                            const T db = bd[r * 2 + s] - xb[r * nxi + (s ? nxi - 1 : 0)];
-                            acc += Bdev[u * 2 + s] * (db - mb[ax * 2 + s]) + Bmean[u * 2 + s] * mb[ax * 2 + s];
-                        }
-                    }
-                    g[e] = acc;
+                for (int ax = 0; ax < ND; ++ax) {
+                    T a = acc[ax];
+                    a += __shfl_xor_sync(0xffffffffu, a, 4);
+                    a += __shfl_xor_sync(0xffffffffu, a, 2);
+                    a += __shfl_xor_sync(0xffffffffu, a, 1);
+                    if (act && s == 0) dl[ax * N + r] = a;
                 }
             }
-            __syncthreads();
+            cl.sync();
             for (int e = tid; e < NN; e += nt) {
-                const int r = e / nxi, c = e - r * nxi;
-                T xn = xb[e] + g[e];
-                if (c == 0) xn = bd[r * 2];                 // A xi_bar = b holds exactly
+                const int r = e / nxi, c = e - r * nxi, row = e - (e / N) * N;
+                const T *src = cl.map_shared_rank(dl, row / L);
+                T xn = xb[e] + src[e];
+                if (c == 0) xn = bd[r * 2];                  // A xi_bar = b holds exactly
                 else if (c == nxi - 1) xn = bd[r * 2 + 1];
                 const T dx = xn - xb[e];
                 fp += dx * dx;
                 xb[e] = xn;
             }
-            double s_rp2 = (double)rp2, s_mx = (double)mx, s_fp = (double)fp;
-            block_reduce3(s_rp2, s_mx, s_fp, red);
-            if (!isfinite(s_fp) || !isfinite(s_rp2)) bad = 1;
-            if (its_tol < 0 && s_mx <= A.tol) its_tol = it;
-            fp_last = s_fp;
-            if (A.hist && tid == 0) A.hist[(int64_t)ii * A.iters + it] = (float)s_mx;
+        } else {
+            // Kronecker form, per axis with robot mean m of v:
+            //   delta_i = P_dev v_i + (P_mean - P_dev) m   (+ the same with B for b - A xi_bar)
+            for (int e = tid; e < ND * nxi; e += nt) {
+                const int ax = e / nxi, c = e - ax * nxi;
+                T s = T(0);
+                for (int i = 0; i < n; ++i) s += v[(ax * n + i) * nxi + c];
+                mv[e] = s * invn;
+            }
+            __syncthreads();
+            for (int e = tid; e < ND * nxi; e += nt) {
+                const int ax = e / nxi, u = e - ax * nxi;
+                T s = T(0);
+                for (int c = 0; c < nxi; ++c) s += Pdif[u * nxi + c] * mv[ax * nxi + c];
+                if (corr_b) s += Bdif[u * 2] * mb[ax * 2] + Bdif[u * 2 + 1] * mb[ax * 2 + 1];
+                pm[e] = s;
+            }
+            __syncthreads();
+            for (int e = tid; e < NN; e += nt) {
+                const int r = e / nxi, u = e - r * nxi, ax = r / n;
+                const T *vr = v + r * nxi;
+                const T *pu = Pdev + u * nxi;
+                T s0 = pm[ax * nxi + u], s1 = T(0);
+                int c = 0;
+                for (; c + 1 < nxi; c += 2) {
+                    s0 += pu[c] * vr[c];
+                    s1 += pu[c + 1] * vr[c + 1];
+                }
+                if (c < nxi) s0 += pu[c] * vr[c];
+                if (corr_b) s1 += Bdev[u * 2] * db[r * 2] + Bdev[u * 2 + 1] * db[r * 2 + 1];
+                T xn = xb[e] + (s0 + s1);
+                if (u == 0) xn = bd[r * 2];
+                else if (u == nxi - 1) xn = bd[r * 2 + 1];
+                const T dx = xn - xb[e];
+                fp += dx * dx;
+                xb[e] = xn;
+            }
         }
+    }
+    if (cr == 0) {
         for (int e = tid; e < NN; e += nt) {
             A.xo[I.off_xi + e] = xb[e];
             if (A.lo) A.lo[I.off_xi + e] = lam[e];
@@ -369,144 +477,183 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(FwdArgs<T> A)
         }
         if (tid == 0) {
             if (A.resid) {
-                A.resid[(int64_t)ii * SF_NRES + SF_RES_FP] = sqrt(fp_last);
+                A.resid[(int64_t)ii * SF_NRES + SF_RES_FP] = sqrt((double)fp_prev);
                 A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS] = (double)its_tol;
             }
             if (A.its) A.its[ii] = its_tol;
             if (bad) A.status[ii] = SF_ENONFINITE;
         }
-        __syncthreads();
     }
+    cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------
 // FP64 residual of packed coefficients x (reading of eq. primal_residual):
-// ||r_p||_2 and the max row residual in metres.  One CTA per instance; the same
-// row algebra as the forward kernel, in double whatever the solve precision.
+// ||r_p||_2 and the max row residual in metres, whatever the solve precision.
+// One cluster per instance, CTA r evaluating its share of the timesteps.
 template <typename T, int ND>
 __global__ void __launch_bounds__(kMaxThreads) k_residual(ResArgs<T> A)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     double *sm = reinterpret_cast<double *>(smem_raw);
+    cg::cluster_group cl = cg::this_cluster();
     const int tid = threadIdx.x, nt = blockDim.x, nxi = A.nxi;
-    const int ii = blockIdx.x;
+    const int C = A.csize, cr = (int)cl.block_rank();
+    const int ii = blockIdx.x / C;
     const Inst<T> I = A.inst[ii];
     const Shape S = A.shapes[I.shape];
-    const int n = I.n, H = I.H, nobs = I.n_obs;
-    const int64_t fixed = (int64_t)H * nxi + (int64_t)ND * I.N + (int64_t)nobs * (ND + 4) + kRedDoubles;
-    int hc = (int)((A.smem_doubles - fixed) / (ND * n));
-    hc = hc < 1 ? 1 : (hc > H ? H : hc);
-    double *W = sm;
-    double *xb = W + H * nxi;
-    double *pb = xb + ND * I.N;
-    double *ob = pb + ND * n * hc;
-    double *red = ob + nobs * (ND + 4);
+    const int n = I.n, H = I.H, nobs = I.n_obs, NN = ND * I.N;
+    const int k_lo = (int)((int64_t)cr * H / C), k_hi = (int)((int64_t)(cr + 1) * H / C);
+    const int64_t fixed = residual_doubles(ND, nxi, H, n, nobs, 0);
+    int hc = (int)((A.smem_doubles - fixed) / ((int64_t)n * NDP<ND>::v));
+    // the same hc in every CTA of the cluster, so every CTA's carve (and the partial sums
+    // that peers read through distributed shared memory) sits at the same offsets
+    hc = max(1, min(hc, H));
+    while (hc > 1 && residual_doubles(ND, nxi, H, n, nobs, hc) > A.smem_doubles) --hc;
+    // carve in doubles, every region on a 32-byte boundary (mirrors residual_doubles)
+    double *W = sm, *xb = W + carve_round((int64_t)H * nxi, 8);
+    Vec<double, NDP<ND>::v> *P = reinterpret_cast<Vec<double, NDP<ND>::v> *>(xb + carve_round(NN, 8));
+    double *ob = reinterpret_cast<double *>(P) + carve_round((int64_t)n * hc * NDP<ND>::v, 8);
+    double *red = ob + carve_round((int64_t)nobs * 8, 8);
     Inst<double> Id;
     Id.n = n; Id.n_obs = nobs; Id.H = H; Id.dyn = I.dyn; Id.N = I.N; Id.hc = hc;
-    Id.ia2 = (double)I.ia2; Id.ib2 = (double)I.ib2; Id.a = (double)I.a; Id.b = (double)I.b;
+    Id.a = (double)I.a; Id.b = (double)I.b;
+    Id.ia2 = 1.0 / (Id.a * Id.a); Id.ib2 = 1.0 / (Id.b * Id.b);
     for (int ax = 0; ax < 3; ++ax) { Id.pmin[ax] = (double)I.pmin[ax]; Id.pmax[ax] = (double)I.pmax[ax]; }
     for (int e = tid; e < H * nxi; e += nt) W[e] = (double)A.W[S.off_W + e];
-    for (int e = tid; e < ND * I.N; e += nt) xb[e] = (double)A.x[I.off_xi + e];
+    for (int e = tid; e < NN; e += nt) xb[e] = (double)A.x[I.off_xi + e];
     for (int m = tid; m < nobs; m += nt) {
         const double ao = (double)A.oab[I.off_oab + 2 * m], bo = (double)A.oab[I.off_oab + 2 * m + 1];
-        double *o = ob + m * (ND + 4);
-        if (!I.dyn)
-            for (int ax = 0; ax < ND; ++ax) o[ax] = (double)A.obs[I.off_obs + (int64_t)m * ND + ax];
-        o[ND] = 1.0 / (ao * ao);
-        o[ND + 1] = 1.0 / (bo * bo);
-        o[ND + 2] = ao;
-        o[ND + 3] = bo;
+        double *o = ob + 8 * m;
+        for (int ax = 0; ax < 3; ++ax) o[ax] = (!I.dyn && ax < ND) ? (double)A.obs[I.off_obs + (int64_t)m * ND + ax] : 0.0;
+        o[3] = ao * ao;
+        o[4] = (ao * ao) / (bo * bo);
+        o[5] = 1.0 / (ao * ao);
+        o[6] = ao;
+        o[7] = bo;
     }
-    __syncthreads();
-    double rp2 = 0.0, mx = 0.0;
-    for (int k0 = 0; k0 < H; k0 += hc) {
-        const int hcc = min(hc, H - k0);
+    // dynamic obstacle centres are read from global memory in the row loop; convert on the fly
+    double rp2 = 0.0, mx2 = 0.0;
+    const double a2 = Id.a * Id.a, kz = a2 * Id.ib2;
+    for (int k0 = k_lo; k0 < k_hi; k0 += hc) {
+        const int hcc = min(hc, k_hi - k0);
         __syncthreads();
-        for (int e = tid; e < ND * n * hcc; e += nt) {
-            const int r = e / hcc, kl = e - r * hcc;
-            double s = 0.0;
-            for (int c = 0; c < nxi; ++c) s += W[(k0 + kl) * nxi + c] * xb[r * nxi + c];
-            pb[r * hcc + kl] = s;
+        for (int e = tid; e < n * hcc; e += nt) {
+            const int i = e / hcc, kl = e - i * hcc;
+            Vec<double, NDP<ND>::v> p;
+            for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = 0.0;
+            for (int ax = 0; ax < ND; ++ax) {
+                double s = 0.0;
+                for (int c = 0; c < nxi; ++c) s += W[(k0 + kl) * nxi + c] * xb[(ax * n + i) * nxi + c];
+                p.v[ax] = s;
+            }
+            P[i * hcc + kl] = p;
         }
         __syncthreads();
-        // rows_chunk writes R over its position buffer; evaluate into registers only here
-        const int items = n * hcc;
-        for (int item = tid; item < items; item += nt) {
-            const int i = item / hcc, kl = item - i * hcc, k = k0 + kl;
-            double pi[ND];
-            for (int ax = 0; ax < ND; ++ax) pi[ax] = pb[(ax * n + i) * hcc + kl];
-            double R[ND];
-            for (int ax = 0; ax < ND; ++ax) R[ax] = 0.0;
+        for (int e = tid; e < n * hcc; e += nt) {
+            const int i = e / hcc, kl = e - i * hcc, k = k0 + kl;
+            const Vec<double, NDP<ND>::v> pi = P[i * hcc + kl];
+            double R[ND], tie[ND];
+            for (int ax = 0; ax < ND; ++ax) { R[ax] = 0.0; tie[ax] = 0.0; }
+            if (ND == 2) tie[0] = -Id.a; else tie[ND - 1] = -Id.b;
             for (int j = i + 1; j < n; ++j) {
+                const Vec<double, NDP<ND>::v> pj = P[j * hcc + kl];
                 double d[ND];
-                for (int ax = 0; ax < ND; ++ax) d[ax] = pi[ax] - pb[(ax * n + j) * hcc + kl];
-                add_row<double, ND>(d, Id.ia2, Id.ib2, Id.a, Id.b, 1.0, R, rp2, mx, true);
+                for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - pj.v[ax];
+                const double q = qdist<double, ND>(d, kz);
+                if (q <= a2) row_active<double, ND>(d, q, Id.ia2, tie, R, rp2, mx2, true);
             }
             for (int m = 0; m < nobs; ++m) {
-                const double *o = ob + m * (ND + 4);
+                const double *o = ob + 8 * m;
                 double d[ND];
                 if (I.dyn) {
                     const T *c = A.obs + I.off_obs + ((int64_t)m * H + k) * ND;
-                    for (int ax = 0; ax < ND; ++ax) d[ax] = pi[ax] - (double)c[ax];
+                    for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - (double)c[ax];
                 } else {
-                    for (int ax = 0; ax < ND; ++ax) d[ax] = pi[ax] - o[ax];
+                    for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - o[ax];
                 }
-                add_row<double, ND>(d, o[ND], o[ND + 1], o[ND + 2], o[ND + 3], 1.0, R, rp2, mx, true);
+                double q = d[0] * d[0] + d[1] * d[1];
+                if (ND == 3) q += o[4] * d[ND - 1] * d[ND - 1];
+                if (q <= o[3]) {
+                    double t2[ND];
+                    for (int ax = 0; ax < ND; ++ax) t2[ax] = 0.0;
+                    if (ND == 2) t2[0] = -o[6]; else t2[ND - 1] = -o[7];
+                    row_active<double, ND>(d, q, o[5], t2, R, rp2, mx2, true);
+                }
             }
             for (int ax = 0; ax < ND; ++ax) {
-                const double u = pi[ax] - Id.pmax[ax], l = Id.pmin[ax] - pi[ax];
-                if (u > 0.0) { rp2 += u * u; mx = fmax(mx, u); }
-                if (l > 0.0) { rp2 += l * l; mx = fmax(mx, l); }
+                const double u = pi.v[ax] - Id.pmax[ax], l = Id.pmin[ax] - pi.v[ax];
+                if (u > 0.0) { rp2 += u * u; mx2 = fmax(mx2, u * u); }
+                if (l > 0.0) { rp2 += l * l; mx2 = fmax(mx2, l * l); }
             }
         }
     }
-    double dummy = 0.0;
-    block_reduce3(rp2, mx, dummy, red);
-    if (tid == 0) {
-        A.resid[(int64_t)ii * SF_NRES + SF_RES_RP] = sqrt(rp2);
+    block_reduce3_to<double>(rp2, mx2, 0.0, red);
+    cl.sync();
+    if (cr == 0 && tid == 0) {
+        double s_rp2 = 0.0, s_mx2 = 0.0;
+        for (int q = 0; q < C; ++q) {
+            const double *rr = cl.map_shared_rank(red, q);
+            s_rp2 += rr[96];
+            s_mx2 = fmax(s_mx2, rr[97]);
+        }
+        const double mx = sqrt(s_mx2);
+        A.resid[(int64_t)ii * SF_NRES + SF_RES_RP] = sqrt(s_rp2);
         A.resid[(int64_t)ii * SF_NRES + SF_RES_MAX] = mx;
-        double it = A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS];
-        if (it < 0.0 && mx <= A.tol) {
+        const double itv = A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS];
+        if (itv < 0.0 && mx <= A.tol) {
             A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS] = (double)A.iters;
             if (A.its) A.its[ii] = A.iters;
         }
-        if (!isfinite(rp2)) A.status[ii] = SF_ENONFINITE;
+        if (!isfinite(s_rp2)) A.status[ii] = SF_ENONFINITE;
     }
+    cl.sync();
+}
+
+template <typename K, typename Arg>
+static cudaError_t launch_cluster(K kernel, const Arg &a, int n_inst, int csize, int threads, size_t smem,
+                                  cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_inst * csize), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
 template <typename T>
-static cudaError_t launch_forward_t(const FwdArgs<T> &a, int grid, int threads, size_t smem, cudaStream_t s)
+static cudaError_t launch_forward_t(const FwdArgs<T> &a, int threads, size_t smem, cudaStream_t s)
 {
-    if (a.nd == 2) {
-        cudaFuncSetAttribute(k_forward<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_forward<T, 2><<<grid, threads, smem, s>>>(a);
-    } else {
-        cudaFuncSetAttribute(k_forward<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_forward<T, 3><<<grid, threads, smem, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (a.n_inst < 1 || a.csize < 1 || a.csize > kMaxCluster) return cudaErrorInvalidValue;
+    if (a.nd == 2) return launch_cluster(k_forward<T, 2>, a, a.n_inst, a.csize, threads, smem, s);
+    return launch_cluster(k_forward<T, 3>, a, a.n_inst, a.csize, threads, smem, s);
 }
 
-cudaError_t launch_forward(const FwdArgs<double> &a, int grid, int threads, size_t smem, cudaStream_t s)
+cudaError_t launch_forward(const FwdArgs<double> &a, int threads, size_t smem, cudaStream_t s)
 {
-    return launch_forward_t(a, grid, threads, smem, s);
+    return launch_forward_t(a, threads, smem, s);
 }
-cudaError_t launch_forward(const FwdArgs<float> &a, int grid, int threads, size_t smem, cudaStream_t s)
+cudaError_t launch_forward(const FwdArgs<float> &a, int threads, size_t smem, cudaStream_t s)
 {
-    return launch_forward_t(a, grid, threads, smem, s);
+    return launch_forward_t(a, threads, smem, s);
 }
 
 template <typename T>
 static cudaError_t launch_residual_t(const ResArgs<T> &a, int threads, size_t smem, cudaStream_t s)
 {
-    if (a.nd == 2) {
-        cudaFuncSetAttribute(k_residual<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_residual<T, 2><<<a.n_inst, threads, smem, s>>>(a);
-    } else {
-        cudaFuncSetAttribute(k_residual<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_residual<T, 3><<<a.n_inst, threads, smem, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (a.n_inst < 1 || a.csize < 1 || a.csize > kMaxCluster) return cudaErrorInvalidValue;
+    if (a.nd == 2) return launch_cluster(k_residual<T, 2>, a, a.n_inst, a.csize, threads, smem, s);
+    return launch_cluster(k_residual<T, 3>, a, a.n_inst, a.csize, threads, smem, s);
 }
 
 cudaError_t launch_residual(const ResArgs<double> &a, int threads, size_t smem, cudaStream_t s)

@@ -8,8 +8,8 @@
 namespace sf {
 
 constexpr int kMaxThreads = 512;
-constexpr int kIPT = 8;            // (robot, timestep) items a thread keeps in registers per chunk
-constexpr int kRedDoubles = 100;   // block-reduction scratch (3 x 32 warps + 3 results)
+constexpr int kMaxCluster = 8;     // CTAs per instance (portable cluster size)
+constexpr int kRedDoubles = 100;   // block-reduction scratch of the residual kernel
 
 // One instance as the kernels see it.  Offsets are in elements of T.
 template <typename T>
@@ -17,7 +17,7 @@ struct Inst {
     int n, n_obs, H, dyn;
     int N;        // n * n_xi coefficients per axis
     int shape;    // index into the shape table
-    int hc;       // timesteps per chunk in the forward kernel
+    int hc;       // timesteps per chunk of one CTA's share of the horizon (forward kernel)
     int pad_;
     T ia2, ib2;   // diagonal of M_r^-2: 1/a^2 (x, y), 1/b^2 (z)
     T a, b;
@@ -34,10 +34,49 @@ struct Shape {
     int64_t off_S;    // structured form: P_dev, P_mean, B_dev, B_mean (n_xi x n_xi, n_xi x 2 each)
 };
 
+// Shared-memory carve of the forward kernel, in elements of T.  Every region starts on a
+// 32-byte boundary.  Host and kernel both call forward_carve, so they cannot disagree.
+struct FwdCarve {
+    int64_t W, xb, lam, xc, v, gp, dl, pb, Rb, ob, bd, db, sx, red, Ps, total;
+};
+
+__host__ __device__ inline int64_t carve_round(int64_t cnt, int esz)
+{
+    const int64_t q = 32 / esz;
+    return (cnt + q - 1) / q * q;
+}
+
+// nd, nxi: dimension and coefficients; H, n, nobs: instance sizes; hc: timesteps per chunk;
+// p_rows: rows of P_eta staged in shared memory (0: read from global memory).
+__host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz)
+{
+    const int64_t N = (int64_t)n * nxi, NN = nd * N, ndp = nd == 2 ? 2 : 4;
+    FwdCarve c;
+    int64_t o = 0;
+    c.W = o;   o += carve_round((int64_t)H * nxi, esz);
+    c.xb = o;  o += carve_round(NN, esz);
+    c.lam = o; o += carve_round(NN, esz);
+    c.xc = o;  o += carve_round(NN, esz);
+    c.v = o;   o += carve_round(NN, esz);
+    c.gp = o;  o += 2 * carve_round(NN + 4, esz);                 // partial g + stats, two buffers
+    c.dl = o;  o += carve_round(NN, esz);                         // projection rows of this CTA
+    c.pb = o;  o += carve_round((int64_t)n * hc * ndp, esz);      // positions [i][k] as vectors
+    c.Rb = o;  o += carve_round((int64_t)nd * n * hc, esz);       // row sums R [ax][i][k]
+    c.ob = o;  o += carve_round((int64_t)nobs * 8, esz);          // obstacle records
+    c.bd = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b
+    c.db = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b - A xi_bar^0
+    c.sx = o;  o += carve_round(2 * (int64_t)nxi * nxi + 4 * nxi + 2 * (int64_t)nd * nxi + 2 * nd, esz);
+    c.red = o; o += carve_round(4 * 32, esz);
+    c.Ps = o;  o += carve_round((int64_t)p_rows * N, esz);
+    c.total = o;
+    return c;
+}
+
 template <typename T>
 struct FwdArgs {
     int nd, nxi, iters, n_inst;
-    int p_smem;       // 1: P_eta of each instance staged in shared memory
+    int csize;        // CTAs per instance (thread-block cluster), 1..kMaxCluster
+    int p_rows;       // rows of P_eta per CTA staged in shared memory (dense; 0 = global)
     int proj;         // SF_PROJ_DENSE / SF_PROJ_STRUCTURED
     T rho;
     double tol;
@@ -71,14 +110,38 @@ struct ResArgs {
     int iters;                  // iteration count of the solve (its fix-up)
     int32_t *status;
     int64_t smem_doubles;       // dynamic shared memory of the launch, in doubles
+    int csize;                  // CTAs per instance (thread-block cluster)
 };
 
 // ---- launchers (defined in the .cu files) ---------------------------------
-cudaError_t launch_forward(const FwdArgs<double> &a, int grid, int threads, size_t smem, cudaStream_t s);
-cudaError_t launch_forward(const FwdArgs<float> &a, int grid, int threads, size_t smem, cudaStream_t s);
+// Launch geometry shared by every entry point that runs the forward kernel.
+struct Plan {
+    int csize = 1;        // CTAs per instance
+    int threads = kMaxThreads;
+    int p_rows = 0;       // rows of P_eta staged per CTA (dense projection), 0 = read from global
+    size_t smem_fwd = 0;  // dynamic shared memory of the forward launch
+    size_t smem_res = 0;  // and of the residual launch
+};
+
+// Chooses the cluster size (csize_req > 0 forces it), each instance's timestep chunk
+// hc_out[i] and the shared-memory sizes.  Returns SF_OK or SF_EUNSUPPORTED when an
+// instance cannot fit in `optin` bytes of shared memory.
+int plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
+                 int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out);
+
+// Both launch n_inst clusters of a.csize CTAs (one cluster per instance).
+cudaError_t launch_forward(const FwdArgs<double> &a, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_forward(const FwdArgs<float> &a, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_residual(const ResArgs<double> &a, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_residual(const ResArgs<float> &a, int threads, size_t smem, cudaStream_t s);
-cudaError_t forward_smem_limit(size_t bytes);
+
+// Shared memory (doubles) the residual kernel needs for one instance at a chunk of hc timesteps.
+__host__ __device__ inline int64_t residual_doubles(int nd, int nxi, int H, int n, int nobs, int hc)
+{
+    const int64_t N = (int64_t)n * nxi;
+    return carve_round((int64_t)H * nxi, 8) + carve_round(nd * N, 8) + carve_round((int64_t)n * hc * (nd == 2 ? 2 : 4), 8) +
+           carve_round((int64_t)nobs * 8, 8) + kRedDoubles;
+}
 
 // FP64 factorisation of every shape (sf_factor.cu).  W64/P64/Pb64/S64 are pools laid out by
 // Shape offsets; info[s] receives 0 or a failing pivot index + 1.

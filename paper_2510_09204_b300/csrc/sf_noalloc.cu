@@ -127,8 +127,6 @@ __global__ void k_na_operators(NaScratch *S, int nxi, int H, int n, int n_obs, d
     for (int e = tid; e < 2 * nxi * nxi + 4 * nxi; e += nt) S->S32[e] = (float)S->S64[e];
 }
 
-size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-
 }  // namespace
 
 extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_shape *shape, int32_t n_inst,
@@ -158,20 +156,20 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return SF_ECUDA;
 
-    // shared memory of the forward kernel (the carve of k_forward, structured projection, FP32)
-    const int threads = kMaxThreads, nd = n_d, nxi = n_xi, N = s.n * nxi;
-    auto fwd_bytes = [&](int hc) {
-        size_t t = (size_t)s.H * nxi + 5 * (size_t)nd * N + (size_t)nd * s.n * hc + (size_t)s.n_obs * (nd + 4) +
-                   (size_t)nd * s.n * 2 + 2 * (size_t)nxi * nxi + 4 * (size_t)nxi + (size_t)nd * nxi * 2;
-        return align16(t * sizeof(float)) + kRedDoubles * sizeof(double);
-    };
-    int hc = std::max(1, std::min(s.H, kIPT * threads / s.n));
-    while (hc > 1 && fwd_bytes(hc) > (size_t)optin) --hc;
-    if (fwd_bytes(hc) > (size_t)optin) return SF_ETOOBIG;
-    const size_t res_need = ((size_t)s.H * nxi + (size_t)nd * N + (size_t)nd * s.n + (size_t)s.n_obs * (nd + 4) +
-                             kRedDoubles) * sizeof(double);
-    if (res_need > (size_t)optin) return SF_ETOOBIG;
-    const size_t smem_res = std::min((size_t)optin, std::max(res_need, (size_t)96 * 1024));
+    // launch geometry of the forward kernel (structured projection, FP32)
+    int num_sms = 0;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SF_ECUDA;
+    const int nd = n_d, nxi = n_xi, N = s.n * nxi;
+    Plan plan;
+    int hc = 1;
+    {
+        int vn = s.n, vo = s.n_obs, vH = s.H;
+        // every instance has the same shape: plan one and reuse it
+        if (plan_forward(nd, nxi, (int)sizeof(float), SF_PROJ_STRUCTURED, 1, &vn, &vo, &vH,
+                         std::max(1, num_sms / n_inst), optin, 0, kMaxThreads, &plan, &hc) != SF_OK)
+            return SF_ETOOBIG;
+    }
+    const int threads = plan.threads;
 
     // instance table and shape record, written into the fixed array
     const int64_t per_xi = (int64_t)nd * s.n * nxi, per_bnd = (int64_t)nd * s.n * 2;
@@ -218,7 +216,8 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
     a.nxi = nxi;
     a.iters = iters;
     a.n_inst = n_inst;
-    a.p_smem = 0;
+    a.csize = plan.csize;
+    a.p_rows = 0;
     a.proj = SF_PROJ_STRUCTURED;
     a.rho = (float)rho;
     a.tol = 1e-3;
@@ -235,7 +234,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
     a.lo = lam_out;
     a.resid = resid_out;
     a.status = S->status;
-    if (launch_forward(a, n_inst, threads, fwd_bytes(hc), st) != cudaSuccess) return SF_ECUDA;
+    if (launch_forward(a, threads, plan.smem_fwd, st) != cudaSuccess) return SF_ECUDA;
     if (resid_out) {
         ResArgs<float> r;
         memset(&r, 0, sizeof(r));
@@ -252,8 +251,9 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
         r.resid = resid_out;
         r.iters = iters;
         r.status = S->status;
-        r.smem_doubles = (int64_t)(smem_res / sizeof(double));
-        if (launch_residual(r, threads, smem_res, st) != cudaSuccess) return SF_ECUDA;
+        r.smem_doubles = (int64_t)(plan.smem_res / sizeof(double));
+        r.csize = plan.csize;
+        if (launch_residual(r, threads, plan.smem_res, st) != cudaSuccess) return SF_ECUDA;
     }
     return SF_OK;
 }

@@ -27,8 +27,8 @@ PROJECTIONS = {"dense": SF_PROJ_DENSE, "structured": SF_PROJ_STRUCTURED}
 
 # every symbol declared in include/sf.h
 EXPORTS = ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
-           "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_strerror",
-           "sf_version")
+           "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch",
+           "sf_get_launch", "sf_strerror", "sf_version")
 SF_KT_FORWARD, SF_KT_RESIDUAL, SF_KT_BACKWARD, SF_NKT = range(4)
 
 
@@ -77,11 +77,13 @@ def lib(path: str | None = None):
         L.sf_kernel_times.argtypes = [vp, ct.POINTER(ct.c_float)]
         L.sf_solve_noalloc.argtypes = [i32, i32, ct.c_double, ct.POINTER(sf_shape), i32, vp, vp, vp, vp, i32, vp,
                                        vp, vp, vp]
+        L.sf_set_launch.argtypes = [vp, i32, i32]
+        L.sf_get_launch.argtypes = [vp, ct.POINTER(i32), ct.POINTER(i32), ct.POINTER(i32)]
         L.sf_strerror.argtypes = [i32]
         L.sf_strerror.restype = ct.c_char_p
         L.sf_version.restype = i32
         for f in ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
-                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc"):
+                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -197,6 +199,16 @@ class SFSolver:
         _check(lib().sf_solve_backward(self.h, _ptr(g_xi_out), _ptr(g_lam_out), _ptr(g_rp2), _ptr(g_xc),
                                        _ptr(g_x0), _ptr(g_l0), _stream(stream)), "sf_solve_backward")
         return g_xc, g_x0, g_l0
+
+    def set_launch(self, cluster=0, threads=0):
+        """sf_set_launch: CTAs per instance (0 = automatic) and threads per CTA (0 = 512)."""
+        _check(lib().sf_set_launch(self.h, int(cluster), int(threads)), "sf_set_launch")
+
+    def launch(self):
+        """(cluster, threads, staged projection rows) in use."""
+        c, t, p = ct.c_int32(), ct.c_int32(), ct.c_int32()
+        _check(lib().sf_get_launch(self.h, ct.byref(c), ct.byref(t), ct.byref(p)), "sf_get_launch")
+        return c.value, t.value, p.value
 
     def profile(self, enable=True):
         _check(lib().sf_profile(self.h, int(bool(enable))), "sf_profile")

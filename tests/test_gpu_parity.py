@@ -172,3 +172,31 @@ def test_fp32_full_config2_batch_sampled():
         ref = oracle.solve(insts[k], 200, rho=RHO)
         assert max_pos_err(insts[k], out["xi"][k], ref["xi"], W) <= 1e-4
         assert np.all(out["xi"][k][:, :, 0] == np.float32(insts[k]["bnd"][:, :, 0]))
+
+
+@pytest.mark.parametrize("proj", ["dense", "structured"])
+@pytest.mark.parametrize("cluster,threads", [(1, 512), (2, 256), (3, 128), (5, 96), (8, 64)])
+def test_fp64_every_cluster_geometry_matches_oracle(cluster, threads, proj):
+    """The instance split over 1..8 CTAs of a cluster (shares of 100 timesteps that are
+    not multiples of each other) gives the oracle's iterates whatever the geometry."""
+    insts = sfgen.make_batch(2, B=2)
+    out = gpu_solve(insts, 30, proj=proj, cluster=cluster, threads=threads)
+    assert out["solver"].launch()[0] == cluster
+    assert (out["status"] == 0).all()
+    for k, inst in enumerate(insts):
+        ref = oracle.solve(inst, 30, rho=RHO)
+        z = np.concatenate([out["xi"][k].ravel(), out["lam"][k].ravel()])
+        zr = np.concatenate([ref["xi"].ravel(), ref["lam"].ravel()])
+        assert rel(z, zr) <= 1e-10, (cluster, threads, rel(z, zr))
+        r = oracle.residual(inst, out["xi"][k])
+        np.testing.assert_allclose(out["resid"][k, :2], r[:2], rtol=1e-9, atol=1e-12)
+
+
+def test_set_launch_rejects_bad_geometry():
+    from paper_2510_09204_b300 import SFError
+    insts = sfgen.make_batch(1)
+    out = gpu_solve(insts, 1)
+    s = out["solver"]
+    for bad in [(9, 0), (-1, 0), (1, 48), (1, 100), (1, 1024)]:
+        with pytest.raises(SFError):
+            s.set_launch(*bad)
