@@ -37,7 +37,7 @@ FP32_LANES_PER_SM = 128
 def args_():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", type=int, default=2)
@@ -46,6 +46,7 @@ def args_():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--compare-fp64", action="store_true", help="also time the plain FP64 GPU solve")
+    p.add_argument("--no-autotune", action="store_true")
     return p.parse_args()
 
 
@@ -77,45 +78,67 @@ def algorithmic_flops(insts, iters, proj):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons, timestamped, sampled every 20 ms from before
+    the warm-up until after the timed region; only samples inside the timed window count."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.idx = gpu_index  # index, or GPU-<uuid> as nvidia-smi -i accepts
+    def __init__(self, gpu_sel):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_sel), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        self.t0 = self.t1 = None
+
+    def wait_first(self, timeout=5.0):
+        end = time.time() + timeout
+        while self.p is not None and time.time() < end:
+            if os.path.getsize(self.f.name) > 0:
+                return
+            time.sleep(0.02)
+
+    def window(self, t0, t1):
+        self.t0, self.t1 = t0, t1
 
     def stop(self):
+        import datetime
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)
         self.p.terminate()
         self.p.wait()
         self.f.flush()
-        self.f.seek(0)
-        sm, smax, reasons = [], [], set()
+        with open(self.f.name) as fh:
+            lines = fh.read().splitlines()
+        os.unlink(self.f.name)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().splitlines():
+        rows = []
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), float(parts[3]),
+                             [nm for nm, val in zip(names, parts[5:9]) if val.lower().startswith("active")]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        os.unlink(self.f.name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [r for r in rows if self.t0 is not None and self.t0 - 0.01 <= r[0] <= self.t1 + 0.01]
+        how = "samples inside the timed region"
+        if not inside and rows and self.t0 is not None:
+            mid = 0.5 * (self.t0 + self.t1)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+            how = "nearest sample (timed region shorter than the 20 ms sampling interval)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        reasons = sorted({x for r in inside for x in r[4]})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "power_w_max": max(r[3] for r in inside), "reasons": reasons, "samples": len(inside),
+                "sampling": how}
 
 
 def measured_peaks():
@@ -209,11 +232,23 @@ def main():
     res = torch.empty((len(insts), 4), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+    tune = None
+    if not a.no_autotune:
+        t0 = time.perf_counter()
+        c, t, ms = solver.autotune(data, data["xi"], iters, reps=2)
+        tune = {"cluster": c, "threads": t, "best_ms": ms, "tuning_s": time.perf_counter() - t0}
     solver.profile(True)
 
     def step():
         solver.solve(data, data["xi"], iters, xi_out=xo, lam_out=lo, resid=res, stream=stream)
 
+    try:
+        gsel = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        gsel = vis.split(",")[local] if vis else str(local)
+    clocks = ClockSampler(gsel)
+    clocks.wait_first()
     for _ in range(max(a.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -224,13 +259,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    try:
-        gsel = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-        gsel = vis.split(",")[local] if vis else str(local)
-    clocks = ClockSampler(gsel)
     barrier()
+    t_start = time.time()
     times, fwd_ms = [], []
     for _ in range(a.steps):
         flush.zero_()  # L2 flush between timed steps (outside the events)
@@ -243,6 +273,7 @@ def main():
         times.append(e0.elapsed_time(e1))
         fwd_ms.append(solver.kernel_times()[0])
     barrier()
+    clocks.window(t_start, time.time())
     clk = clocks.stop()
     tot_ms = sum(times)
     if world > 1:
@@ -280,6 +311,8 @@ def main():
     if a.compare_fp64 and rank == 0:
         s64 = SFSolver(insts, nd, 11, rho=RHO, precision="fp64", proj="dense", max_iters=iters)
         d64 = s64.pack(insts, device=dev)
+        if not a.no_autotune:
+            s64.autotune(d64, d64["xi"], iters, reps=1)
         s64.solve(d64, d64["xi"], iters)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -290,7 +323,7 @@ def main():
         ms64 = e0.elapsed_time(e1)
         r32 = res.cpu().numpy()
         r64 = r64.cpu().numpy()
-        fp64 = {"ms_per_batch": ms64, "value": pairs * iters / (ms64 * 1e-3),
+        fp64 = {"ms_per_batch": ms64, "value": pairs * iters / (ms64 * 1e-3), "launch": s64.launch(),
                 "max_abs_final_residual_diff_m": float(np.abs(r32[:, 1] - r64[:, 1]).max()),
                 "frac_instances_resid_le_1e-3": float(np.mean(r64[:, 1] <= 1e-3))}
 
@@ -310,6 +343,7 @@ def main():
                        "horizon": cfg.H[0], "iterations": iters, "n_d": nd, "n_xi": 11, "rho": RHO,
                        "precision": a.precision, "projection": a.proj, "l2": "flushed between steps (256 MB write)",
                        "cluster_ctas_per_instance": solver.launch()[0], "threads_per_cta": solver.launch()[1],
+                       "autotune": tune,
                        "parallelism": "instances sharded by rank" if world > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
                          "traffic": None, "kernel": "k_forward", "kernel_ms": fwd_avg,

@@ -204,6 +204,20 @@ int sf_shape_operator(const sf_handle *h, int32_t inst, int32_t which, double *h
  */
 int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads);
 
+/*
+ * sf_autotune — time each candidate launch geometry (cluster 1, 2, 4, 8 x threads
+ * 128, 256, 512 that fit) on this handle's own batch with `iters` iterations of
+ * sf_solve (CUDA events on `stream`, best of `reps` runs), keep the fastest and
+ * return it.  Allocates and frees temporary output buffers; results of later solves
+ * do not depend on the choice beyond rounding order.  The choice is also remembered
+ * for the batch's shape signature, and sf_create of a later handle with the same
+ * signature starts from it.
+ *  best_cluster, best_threads, best_ms  host outputs (any may be NULL)
+ * Errors: SF_EINVAL, SF_ENOMEM, SF_ECUDA.
+ */
+int sf_autotune(sf_handle *h, const sf_instance_data *data, const void *xi_cand, int32_t iters, int32_t reps,
+                void *stream, int32_t *best_cluster, int32_t *best_threads, float *best_ms);
+
 /* sf_get_launch — the geometry in use: cluster, threads, staged projection rows. */
 int sf_get_launch(const sf_handle *h, int32_t *cluster, int32_t *threads, int32_t *p_rows);
 

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <new>
 #include <tuple>
 #include <vector>
@@ -69,6 +70,22 @@ struct sf_handle {
     cudaEvent_t ev[2 * SF_NKT] = {};
     bool ev_used[SF_NKT] = {};
 };
+
+// Geometry chosen by sf_autotune, keyed by the batch's shape signature.
+static std::mutex g_tune_mu;
+static std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;
+
+static std::vector<int64_t> tune_key(const sf_desc &d, const std::vector<sf_shape> &shp)
+{
+    std::vector<int64_t> k = {d.n_d, d.n_xi, d.precision, d.proj, d.n_inst};
+    for (const sf_shape &s : shp) {
+        k.push_back(s.n);
+        k.push_back(s.n_obs);
+        k.push_back(s.H);
+        k.push_back(s.dyn_obs);
+    }
+    return k;
+}
 
 static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SF_OK : (e == cudaErrorMemoryAllocation ? SF_ENOMEM : SF_ECUDA); }
 
@@ -262,8 +279,19 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
             vH[i] = h->shp[i].H;
         }
         h->hc.resize(B);
+        int c0 = 0, t0 = kMaxThreads;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(tune_key(h->d, h->shp));
+            if (it != g_tune_cache.end()) {
+                c0 = it->second.first;
+                t0 = it->second.second;
+            }
+        }
         int prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                               h->smem_optin, 0, kMaxThreads, &h->plan, h->hc.data());
+                               h->smem_optin, c0, t0, &h->plan, h->hc.data());
+        if (prc && c0) prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
+                                          h->smem_optin, 0, kMaxThreads, &h->plan, h->hc.data());
         if (prc) { destroy_all(h); delete h; return prc; }
     }
 
@@ -501,6 +529,73 @@ extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
     h->plan = p;
     h->hc = hc;
     return h->esz == 8 ? upload_instances<double>(h) : upload_instances<float>(h);
+}
+
+extern "C" int sf_autotune(sf_handle *h, const sf_instance_data *data, const void *xi_cand, int32_t iters,
+                           int32_t reps, void *stream, int32_t *best_cluster, int32_t *best_threads, float *best_ms)
+{
+    if (!h || !data || !xi_cand || iters < 1 || iters > h->d.max_iters || reps < 1) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)h->xi_total * h->esz;
+    DevBuf xo, lo;
+    int r;
+    if ((r = cuda_status(xo.alloc(bytes))) || (r = cuda_status(lo.alloc(bytes)))) {
+        xo.release();
+        lo.release();
+        return r;
+    }
+    const Plan keep = h->plan;
+    const std::vector<int> keep_hc = h->hc;
+    const bool keep_prof = h->profile;
+    h->profile = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const SolveRecord keep_last = h->last;
+    int bc = keep.csize, bt = keep.threads;
+    float bms = 1e30f;
+    const int clusters[] = {1, 2, 4, 8}, threads[] = {128, 256, 512};
+    for (int c : clusters)
+        for (int t : threads) {
+            if (sf_set_launch(h, c, t) != SF_OK) continue;
+            float best = 1e30f;
+            bool ok = true;
+            for (int q = 0; q <= reps && ok; ++q) {   // the first run warms up
+                cudaEventRecord(e0, st);
+                ok = sf_solve(h, data, xi_cand, nullptr, nullptr, iters, xo.p, lo.p, nullptr, nullptr, st) == SF_OK;
+                cudaEventRecord(e1, st);
+                if (ok && cudaEventSynchronize(e1) == cudaSuccess && q > 0) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    best = std::min(best, ms);
+                }
+            }
+            if (ok && best < bms) {
+                bms = best;
+                bc = c;
+                bt = t;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    xo.release();
+    lo.release();
+    h->profile = keep_prof;
+    h->last = keep_last;
+    r = sf_set_launch(h, bc, bt);
+    if (r) {
+        h->plan = keep;
+        h->hc = keep_hc;
+        return r;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[tune_key(h->d, h->shp)] = std::make_pair(bc, bt);
+    }
+    if (best_cluster) *best_cluster = bc;
+    if (best_threads) *best_threads = bt;
+    if (best_ms) *best_ms = bms;
+    return SF_OK;
 }
 
 extern "C" int sf_get_launch(const sf_handle *h, int32_t *cluster, int32_t *threads, int32_t *p_rows)

@@ -77,70 +77,98 @@ __device__ __forceinline__ T qdist(const T (&d)[ND], T kz)
     return q;
 }
 
-// Rows of the items (i, k) of one chunk: positions P[i][kl] (vectors), obstacle records
-// ob[m] = (c_x, c_y, [c_z,] a_o^2, ...), result R written to Rb[ax][i][kl].
+// Far-away stand-ins: padded robots sit at +kFar, lanes without an item at -kFar, so
+// every distance test against them fails without a bounds check.
+template <typename T> struct Far { static constexpr T v = T(1e15); };
+
+// Rows of the items (i, k) of one chunk: positions P[i][kl] (vectors; robots padded to a
+// multiple of 4 with far dummies), obstacle records ob[m] = (c_x, c_y, [c_z,] a_o^2, kz_o,
+// 1/a_o^2, a_o, b_o) padded the same way; R is written to Rb[ax][i][kl].  Partners and
+// obstacles are tested four at a time (independent loads and tests); the warp votes once
+// per block and takes the rare active-row path only when one of its lanes needs it.
 template <typename T, int ND>
 __device__ __forceinline__ void rows_chunk(const Inst<T> &I, const Vec<T, NDP<ND>::v> *P, const T *ob,
                                            const T *obs_g, T *Rb, int k0, int hcc, T &rp2, T &mx2)
 {
     using VP = Vec<T, NDP<ND>::v>;
-    const int n = I.n, nobs = I.n_obs;
+    const int n = I.n, nobs = I.n_obs, items = n * hcc;
+    const int npad = (n + 3) & ~3, opad = (nobs + 3) & ~3;
     const T a2 = I.a * I.a, ia2 = I.ia2, kz = (I.a * I.a) * I.ib2;
     T tie_f[ND], tie_b[ND];   // r_1 of a coincident pair seen from the row's first / second robot
 #pragma unroll
     for (int ax = 0; ax < ND; ++ax) tie_f[ax] = tie_b[ax] = T(0);
     if (ND == 2) { tie_f[0] = -I.a; tie_b[0] = I.a; }
     else { tie_f[ND - 1] = -I.b; tie_b[ND - 1] = I.b; }
-    for (int e = threadIdx.x; e < n * hcc; e += blockDim.x) {
-        const int i = e / hcc, kl = e - i * hcc, k = k0 + kl;
-        const VP pi = P[i * hcc + kl];
+    for (int e0 = 0; e0 < items; e0 += blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        const bool valid = e < items;
+        if (__all_sync(0xffffffffu, !valid)) continue;   // a whole warp without items skips the round
+        const int ee = valid ? e : 0;
+        const int i = ee / hcc, kl = ee - i * hcc, k = k0 + kl;
+        VP pi = P[i * hcc + kl];
+        if (!valid)
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) pi.v[ax] = -Far<T>::v;
         T R[ND];
 #pragma unroll
         for (int ax = 0; ax < ND; ++ax) R[ax] = T(0);
-        // pairs (j, i), j < i: the row's first robot is j
-#pragma unroll 4
-        for (int j = 0; j < i; ++j) {
-            const VP pj = P[j * hcc + kl];
-            T d[ND];
+        // robot pairs: the row of pair (min(i,j), max(i,j)); j == i (q = 0) is sorted out in
+        // the slow path
+        for (int j0 = 0; j0 < npad; j0 += 4) {
+            T d[4][ND], q[4];
 #pragma unroll
-            for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - pj.v[ax];
-            const T q = qdist<T, ND>(d, kz);
-            if (q <= a2) row_active<T, ND>(d, q, ia2, tie_b, R, rp2, mx2, false);
-        }
-        // pairs (i, j), j > i: the row's first robot is i
-#pragma unroll 4
-        for (int j = i + 1; j < n; ++j) {
-            const VP pj = P[j * hcc + kl];
-            T d[ND];
+            for (int u = 0; u < 4; ++u) {
+                const VP pj = P[(j0 + u) * hcc + kl];
 #pragma unroll
-            for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - pj.v[ax];
-            const T q = qdist<T, ND>(d, kz);
-            if (q <= a2) row_active<T, ND>(d, q, ia2, tie_f, R, rp2, mx2, true);
-        }
-        // obstacles: record (c_x, c_y, [c_z], a_o^2 | kz_o, 1/a_o^2, a_o, b_o)
-#pragma unroll 2
-        for (int m = 0; m < nobs; ++m) {
-            const Vec<T, 4> r0 = reinterpret_cast<const Vec<T, 4> *>(ob)[2 * m];
-            T d[ND];
-            if (I.dyn) {
-                const T *c = obs_g + ((int64_t)m * I.H + k) * ND;
-#pragma unroll
-                for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - c[ax];
-            } else {
-#pragma unroll
-                for (int ax = 0; ax < ND; ++ax) d[ax] = pi.v[ax] - r0.v[ax];
+                for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - pj.v[ax];
+                q[u] = qdist<T, ND>(d[u], kz);
             }
-            const T a2o = r0.v[3];
-            T q = d[0] * d[0] + d[1] * d[1];
-            if (ND == 3) q += ob[8 * m + 4] * d[ND - 1] * d[ND - 1];
-            if (q <= a2o) {
-                T tie[ND];
+            const bool any = (q[0] <= a2) | (q[1] <= a2) | (q[2] <= a2) | (q[3] <= a2);
+            if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
-                for (int ax = 0; ax < ND; ++ax) tie[ax] = T(0);
-                if (ND == 2) tie[0] = -ob[8 * m + 6]; else tie[ND - 1] = -ob[8 * m + 7];
-                row_active<T, ND>(d, q, ob[8 * m + 5], tie, R, rp2, mx2, true);
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u;
+                    if (q[u] <= a2 && j != i) {
+                        if (j > i) row_active<T, ND>(d[u], q[u], ia2, tie_f, R, rp2, mx2, true);
+                        else row_active<T, ND>(d[u], q[u], ia2, tie_b, R, rp2, mx2, false);
+                    }
+                }
             }
         }
+        // obstacles
+        for (int m0 = 0; m0 < opad; m0 += 4) {
+            T d[4][ND], q[4], lim[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int m = m0 + u;
+                const Vec<T, 4> r0 = reinterpret_cast<const Vec<T, 4> *>(ob)[2 * m];
+                if (I.dyn && m < nobs) {
+                    const T *c = obs_g + ((int64_t)m * I.H + k) * ND;
+#pragma unroll
+                    for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - c[ax];
+                } else {
+#pragma unroll
+                    for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - r0.v[ax];
+                }
+                q[u] = d[u][0] * d[u][0] + d[u][1] * d[u][1];
+                if (ND == 3) q[u] += ob[8 * m + 4] * d[u][ND - 1] * d[u][ND - 1];
+                lim[u] = r0.v[3];
+            }
+            const bool any = (q[0] <= lim[0]) | (q[1] <= lim[1]) | (q[2] <= lim[2]) | (q[3] <= lim[3]);
+            if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (q[u] <= lim[u]) {
+                        const int m = m0 + u;
+                        T tie[ND];
+#pragma unroll
+                        for (int ax = 0; ax < ND; ++ax) tie[ax] = T(0);
+                        if (ND == 2) tie[0] = -ob[8 * m + 6]; else tie[ND - 1] = -ob[8 * m + 7];
+                        row_active<T, ND>(d[u], q[u], ob[8 * m + 5], tie, R, rp2, mx2, true);
+                    }
+            }
+        }
+        if (!valid) continue;
         // workspace box (G rows: upper side p <= p_max, lower side -p <= -p_min)
 #pragma unroll
         for (int ax = 0; ax < ND; ++ax) {
@@ -231,6 +259,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(FwdArgs<T> A)
         lam[e] = A.l0 ? A.l0[I.off_xi + e] : T(0);
     }
     for (int e = tid; e < ND * n * 2; e += nt) bd[e] = A.bnd[I.off_bnd + e];
+    for (int m = nobs + tid; m < ((nobs + 3) & ~3); m += nt) {   // padding records: far away, zero radius
+        T *o = ob + 8 * m;
+        for (int q = 0; q < 8; ++q) o[q] = T(0);
+        for (int ax = 0; ax < ND; ++ax) o[ax] = Far<T>::v;
+        o[4] = T(1);
+    }
     for (int m = tid; m < nobs; m += nt) {
         const T ao = A.oab[I.off_oab + 2 * m], bo = A.oab[I.off_oab + 2 * m + 1];
         T *o = ob + 8 * m;
@@ -317,6 +351,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(FwdArgs<T> A)
                     }
                     P[i * hcc + kl] = p;
                 }
+                for (int e = n * hcc + tid; e < ((n + 3) & ~3) * hcc; e += nt) {   // padding robots
+                    Vec<T, NDP<ND>::v> p;
+#pragma unroll
+                    for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = Far<T>::v;
+                    P[e] = p;
+                }
                 __syncthreads();
                 rows_chunk<T, ND>(I, P, ob, A.obs + I.off_obs, Rb, k0, hcc, rp2, mx2);
                 __syncthreads();
@@ -324,14 +364,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(FwdArgs<T> A)
                     const int r = e / nxi, c = e - r * nxi;
                     const T *rr = Rb + r * hcc;
                     const T *wc = W + k0 * nxi + c;
-                    T s0 = T(0), s1 = T(0);
+                    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
                     int kl = 0;
-                    for (; kl + 1 < hcc; kl += 2) {
+                    for (; kl + 3 < hcc; kl += 4) {
                         s0 += wc[kl * nxi] * rr[kl];
                         s1 += wc[(kl + 1) * nxi] * rr[kl + 1];
+                        s2 += wc[(kl + 2) * nxi] * rr[kl + 2];
+                        s3 += wc[(kl + 3) * nxi] * rr[kl + 3];
                     }
-                    if (kl < hcc) s0 += wc[kl * nxi] * rr[kl];
-                    gme[e] += s0 + s1;
+                    for (; kl < hcc; ++kl) s0 += wc[kl * nxi] * rr[kl];
+                    gme[e] += (s0 + s1) + (s2 + s3);
                 }
             }
         }

@@ -60,9 +60,10 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n,
     c.v = o;   o += carve_round(NN, esz);
     c.gp = o;  o += 2 * carve_round(NN + 4, esz);                 // partial g + stats, two buffers
     c.dl = o;  o += carve_round(NN, esz);                         // projection rows of this CTA
-    c.pb = o;  o += carve_round((int64_t)n * hc * ndp, esz);      // positions [i][k] as vectors
+    const int64_t npad = (n + 3) / 4 * 4, opad = (nobs + 3) / 4 * 4;
+    c.pb = o;  o += carve_round(npad * hc * ndp, esz);            // positions [i][k] as vectors (+ far dummies)
     c.Rb = o;  o += carve_round((int64_t)nd * n * hc, esz);       // row sums R [ax][i][k]
-    c.ob = o;  o += carve_round((int64_t)nobs * 8, esz);          // obstacle records
+    c.ob = o;  o += carve_round(opad * 8, esz);                   // obstacle records (+ dummies)
     c.bd = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b
     c.db = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b - A xi_bar^0
     c.sx = o;  o += carve_round(2 * (int64_t)nxi * nxi + 4 * nxi + 2 * (int64_t)nd * nxi + 2 * nd, esz);

@@ -28,7 +28,7 @@ PROJECTIONS = {"dense": SF_PROJ_DENSE, "structured": SF_PROJ_STRUCTURED}
 # every symbol declared in include/sf.h
 EXPORTS = ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
            "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch",
-           "sf_get_launch", "sf_strerror", "sf_version")
+           "sf_get_launch", "sf_autotune", "sf_strerror", "sf_version")
 SF_KT_FORWARD, SF_KT_RESIDUAL, SF_KT_BACKWARD, SF_NKT = range(4)
 
 
@@ -78,12 +78,14 @@ def lib(path: str | None = None):
         L.sf_solve_noalloc.argtypes = [i32, i32, ct.c_double, ct.POINTER(sf_shape), i32, vp, vp, vp, vp, i32, vp,
                                        vp, vp, vp]
         L.sf_set_launch.argtypes = [vp, i32, i32]
+        L.sf_autotune.argtypes = [vp, ct.POINTER(sf_instance_data), vp, i32, i32, vp, ct.POINTER(i32),
+                                  ct.POINTER(i32), ct.POINTER(ct.c_float)]
         L.sf_get_launch.argtypes = [vp, ct.POINTER(i32), ct.POINTER(i32), ct.POINTER(i32)]
         L.sf_strerror.argtypes = [i32]
         L.sf_strerror.restype = ct.c_char_p
         L.sf_version.restype = i32
         for f in ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
-                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch"):
+                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch", "sf_autotune"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -203,6 +205,14 @@ class SFSolver:
     def set_launch(self, cluster=0, threads=0):
         """sf_set_launch: CTAs per instance (0 = automatic) and threads per CTA (0 = 512)."""
         _check(lib().sf_set_launch(self.h, int(cluster), int(threads)), "sf_set_launch")
+
+    def autotune(self, data, xi_cand, iters, reps=2, stream=None):
+        """sf_autotune: returns (cluster, threads, best ms) and keeps that geometry."""
+        c, t, ms = ct.c_int32(), ct.c_int32(), ct.c_float()
+        dd = self._data(data)
+        _check(lib().sf_autotune(self.h, ct.byref(dd), _ptr(xi_cand), int(iters), int(reps), _stream(stream),
+                                 ct.byref(c), ct.byref(t), ct.byref(ms)), "sf_autotune")
+        return c.value, t.value, ms.value
 
     def launch(self):
         """(cluster, threads, staged projection rows) in use."""

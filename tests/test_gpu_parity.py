@@ -200,3 +200,18 @@ def test_set_launch_rejects_bad_geometry():
     for bad in [(9, 0), (-1, 0), (1, 48), (1, 100), (1, 1024)]:
         with pytest.raises(SFError):
             s.set_launch(*bad)
+
+
+def test_autotune_keeps_a_valid_geometry_and_results():
+    insts = sfgen.make_batch(2, B=3)
+    out = gpu_solve(insts, 20)
+    s, data = out["solver"], out["data"]
+    c, t, ms = s.autotune(data, data["xi"], 20, reps=1)
+    assert 1 <= c <= 8 and t in (128, 256, 512) and ms > 0
+    assert s.launch()[:2] == (c, t)
+    xo, lo, res = s.solve(data, data["xi"], 20)
+    import torch
+    torch.cuda.synchronize()
+    for k, inst in enumerate(insts):
+        ref = oracle.solve(inst, 20, rho=RHO)
+        assert rel(s.unpack(xo, k).cpu().numpy(), ref["xi"]) <= 1e-10
