@@ -279,7 +279,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
             vH[i] = h->shp[i].H;
         }
         h->hc.resize(B);
-        int c0 = 0, t0 = kMaxThreads;
+        int c0 = 0, t0 = kDefaultThreads;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(tune_key(h->d, h->shp));
@@ -291,7 +291,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
         int prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
                                h->smem_optin, c0, t0, &h->plan, h->hc.data());
         if (prc && c0) prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                                          h->smem_optin, 0, kMaxThreads, &h->plan, h->hc.data());
+                                          h->smem_optin, 0, kDefaultThreads, &h->plan, h->hc.data());
         if (prc) { destroy_all(h); delete h; return prc; }
     }
 
@@ -467,7 +467,7 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
         r.smem_doubles = (int64_t)(h->plan.smem_res / sizeof(double));
         r.csize = h->plan.csize;
         if (h->profile) SF_TRY(cudaEventRecord(h->ev[2], st));
-        SF_TRY(launch_residual(r, h->plan.threads, h->plan.smem_res, st));
+        SF_TRY(launch_residual(r, std::min(h->plan.threads, 512), h->plan.smem_res, st));
         if (h->profile) {
             SF_TRY(cudaEventRecord(h->ev[3], st));
             h->ev_used[SF_KT_RESIDUAL] = true;
@@ -511,7 +511,7 @@ extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void 
 
 extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
 {
-    if (!h || cluster < 0 || cluster > kMaxCluster || threads < 0 || threads > kMaxThreads || threads % 32 ||
+    if (!h || cluster < 0 || cluster > kMaxCluster || threads < 0 || threads > max_threads(h->esz) || threads % 32 ||
         (threads > 0 && threads < 64))
         return SF_EINVAL;
     const int B = h->d.n_inst;
@@ -523,7 +523,7 @@ extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
     }
     Plan p;
     int rc = plan_forward(h->d.n_d, h->d.n_xi, h->esz, h->d.proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                          h->smem_optin, cluster, threads ? threads : kMaxThreads, &p, hc.data());
+                          h->smem_optin, cluster, threads ? threads : kDefaultThreads, &p, hc.data());
     if (rc) return rc;
     SF_TRY(cudaDeviceSynchronize());
     h->plan = p;
@@ -554,9 +554,10 @@ extern "C" int sf_autotune(sf_handle *h, const sf_instance_data *data, const voi
     const SolveRecord keep_last = h->last;
     int bc = keep.csize, bt = keep.threads;
     float bms = 1e30f;
-    const int clusters[] = {1, 2, 4, 8}, threads[] = {128, 256, 512};
+    const int clusters[] = {1, 2, 4, 8}, threads[] = {128, 256, 512, 1024};
     for (int c : clusters)
         for (int t : threads) {
+            if (t > max_threads(h->esz)) continue;
             if (sf_set_launch(h, c, t) != SF_OK) continue;
             float best = 1e30f;
             bool ok = true;

@@ -221,8 +221,9 @@ __device__ __forceinline__ void block_reduce3_to(T a, T b, T c, T *red)
     }
 }
 
-template <typename T, int ND>
-__global__ void __launch_bounds__(kMaxThreads) k_forward(FwdArgs<T> A)
+// MAXT: the launch bound this instantiation is compiled for (512 or, FP32 only, 1024).
+template <typename T, int ND, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -331,25 +332,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(FwdArgs<T> A)
             for (int k0 = k_lo; k0 < k_hi; k0 += hc) {
                 const int hcc = min(hc, k_hi - k0);
                 __syncthreads();
-                for (int e = tid; e < n * hcc; e += nt) {
-                    const int i = e / hcc, kl = e - i * hcc;
+                // p[ax][i][k] = sum_c W[k][c] xi_bar[ax][i][c], one (axis, robot, timestep) per thread
+                T *Ps_ = reinterpret_cast<T *>(P);
+                for (int e = tid; e < ND * n * hcc; e += nt) {
+                    const int r = e / hcc, kl = e - r * hcc, ax = r / n, i = r - ax * n;
                     const T *wr = W + (k0 + kl) * nxi;
-                    Vec<T, NDP<ND>::v> p;
-#pragma unroll
-                    for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = T(0);
-#pragma unroll
-                    for (int ax = 0; ax < ND; ++ax) {
-                        const T *xr = xb + (ax * n + i) * nxi;
-                        T s0 = T(0), s1 = T(0);
-                        int c = 0;
-                        for (; c + 1 < nxi; c += 2) {
-                            s0 += wr[c] * xr[c];
-                            s1 += wr[c + 1] * xr[c + 1];
-                        }
-                        if (c < nxi) s0 += wr[c] * xr[c];
-                        p.v[ax] = s0 + s1;
+                    const T *xr = xb + r * nxi;
+                    T s0 = T(0), s1 = T(0), s2 = T(0);
+                    int c = 0;
+                    for (; c + 2 < nxi; c += 3) {
+                        s0 += wr[c] * xr[c];
+                        s1 += wr[c + 1] * xr[c + 1];
+                        s2 += wr[c + 2] * xr[c + 2];
                     }
-                    P[i * hcc + kl] = p;
+                    for (; c < nxi; ++c) s0 += wr[c] * xr[c];
+                    Ps_[(i * hcc + kl) * NDP<ND>::v + ax] = (s0 + s1) + s2;
                 }
                 for (int e = n * hcc + tid; e < ((n + 3) & ~3) * hcc; e += nt) {   // padding robots
                     Vec<T, NDP<ND>::v> p;
@@ -469,11 +466,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(FwdArgs<T> A)
         } else {
             // Kronecker form, per axis with robot mean m of v:
             //   delta_i = P_dev v_i + (P_mean - P_dev) m   (+ the same with B for b - A xi_bar)
-            for (int e = tid; e < ND * nxi; e += nt) {
-                const int ax = e / nxi, c = e - ax * nxi;
-                T s = T(0);
-                for (int i = 0; i < n; ++i) s += v[(ax * n + i) * nxi + c];
-                mv[e] = s * invn;
+            {   // robot means, one warp per (axis, coefficient), lanes over robots
+                const int lane = tid & 31, nw = nt >> 5;
+                for (int pq = tid >> 5; pq < ND * nxi; pq += nw) {
+                    const int ax = pq / nxi, c = pq - ax * nxi;
+                    T s = T(0);
+                    for (int i = lane; i < n; i += 32) s += v[(ax * n + i) * nxi + c];
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (lane == 0) mv[pq] = s * invn;
+                }
             }
             __syncthreads();
             for (int e = tid; e < ND * nxi; e += nt) {
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(FwdArgs<T> A)
 // ||r_p||_2 and the max row residual in metres, whatever the solve precision.
 // One cluster per instance, CTA r evaluating its share of the timesteps.
 template <typename T, int ND>
-__global__ void __launch_bounds__(kMaxThreads) k_residual(ResArgs<T> A)
+__global__ void __launch_bounds__(512) k_residual(ResArgs<T> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double *sm = reinterpret_cast<double *>(smem_raw);
@@ -677,8 +679,14 @@ template <typename T>
 static cudaError_t launch_forward_t(const FwdArgs<T> &a, int threads, size_t smem, cudaStream_t s)
 {
     if (a.n_inst < 1 || a.csize < 1 || a.csize > kMaxCluster) return cudaErrorInvalidValue;
-    if (a.nd == 2) return launch_cluster(k_forward<T, 2>, a, a.n_inst, a.csize, threads, smem, s);
-    return launch_cluster(k_forward<T, 3>, a, a.n_inst, a.csize, threads, smem, s);
+    if (threads > max_threads((int)sizeof(T))) return cudaErrorInvalidValue;
+    constexpr int big = sizeof(T) == 8 ? 512 : 1024;
+    if (threads > 512) {
+        if (a.nd == 2) return launch_cluster(k_forward<T, 2, big>, a, a.n_inst, a.csize, threads, smem, s);
+        return launch_cluster(k_forward<T, 3, big>, a, a.n_inst, a.csize, threads, smem, s);
+    }
+    if (a.nd == 2) return launch_cluster(k_forward<T, 2, 512>, a, a.n_inst, a.csize, threads, smem, s);
+    return launch_cluster(k_forward<T, 3, 512>, a, a.n_inst, a.csize, threads, smem, s);
 }
 
 cudaError_t launch_forward(const FwdArgs<double> &a, int threads, size_t smem, cudaStream_t s)

@@ -7,7 +7,10 @@
 
 namespace sf {
 
-constexpr int kMaxThreads = 512;
+constexpr int kMaxThreads = 1024;    // largest CTA of any kernel (FP32 forward)
+constexpr int kDefaultThreads = 512;
+// Largest CTA of the forward kernel for element size esz: FP64 keeps 128 registers per thread.
+__host__ __device__ constexpr int max_threads(int esz) { return esz == 8 ? 512 : 1024; }
 constexpr int kMaxCluster = 8;     // CTAs per instance (portable cluster size)
 constexpr int kRedDoubles = 100;   // block-reduction scratch of the residual kernel
 
@@ -118,7 +121,7 @@ struct ResArgs {
 // Launch geometry shared by every entry point that runs the forward kernel.
 struct Plan {
     int csize = 1;        // CTAs per instance
-    int threads = kMaxThreads;
+    int threads = kDefaultThreads;
     int p_rows = 0;       // rows of P_eta staged per CTA (dense projection), 0 = read from global
     size_t smem_fwd = 0;  // dynamic shared memory of the forward launch
     size_t smem_res = 0;  // and of the residual launch

@@ -166,7 +166,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
         int vn = s.n, vo = s.n_obs, vH = s.H;
         // every instance has the same shape: plan one and reuse it
         if (plan_forward(nd, nxi, (int)sizeof(float), SF_PROJ_STRUCTURED, 1, &vn, &vo, &vH,
-                         std::max(1, num_sms / n_inst), optin, 0, kMaxThreads, &plan, &hc) != SF_OK)
+                         std::max(1, num_sms / n_inst), optin, 0, kDefaultThreads, &plan, &hc) != SF_OK)
             return SF_ETOOBIG;
     }
     const int threads = plan.threads;
@@ -253,7 +253,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
         r.status = S->status;
         r.smem_doubles = (int64_t)(plan.smem_res / sizeof(double));
         r.csize = plan.csize;
-        if (launch_residual(r, threads, plan.smem_res, st) != cudaSuccess) return SF_ECUDA;
+        if (launch_residual(r, std::min(threads, 512), plan.smem_res, st) != cudaSuccess) return SF_ECUDA;
     }
     return SF_OK;
 }

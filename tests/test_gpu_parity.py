@@ -215,3 +215,13 @@ def test_autotune_keeps_a_valid_geometry_and_results():
     for k, inst in enumerate(insts):
         ref = oracle.solve(inst, 20, rho=RHO)
         assert rel(s.unpack(xo, k).cpu().numpy(), ref["xi"]) <= 1e-10
+
+
+@pytest.mark.parametrize("cluster,threads", [(4, 1024), (1, 1024), (8, 1024)])
+def test_fp32_large_ctas_within_tolerance(cluster, threads):
+    insts = sfgen.make_batch(2, B=2)
+    out = gpu_solve(insts, 100, precision="fp32", proj="structured", cluster=cluster, threads=threads)
+    W = oracle.basis(insts[0]["H"], 11)
+    for k, inst in enumerate(insts):
+        ref = oracle.solve(inst, 100, rho=RHO)
+        assert max_pos_err(inst, out["xi"][k], ref["xi"], W) <= 1e-4
