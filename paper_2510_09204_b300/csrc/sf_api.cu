@@ -58,6 +58,7 @@ struct sf_handle {
     DevBuf W64, P64, Pb64, S64;        // FP64 factors
     DevBuf Wt, Pt, Pbt, St;            // in T (aliases of the FP64 pools when T = double)
     DevBuf ck_x, ck_l;
+    DevBuf seg;                        // adjoint: recomputed iterates of a checkpoint segment
     int n_slots = 0;
     int64_t xi_total = 0;
     // launch configuration
@@ -135,6 +136,10 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     }
     p.smem_fwd = need;
     p.smem_res = std::min((size_t)optin, need_r);
+    size_t need_b = 0;
+    for (int i = 0; i < n_inst; ++i)
+        need_b = std::max(need_b, (size_t)backward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], p.p_rows, esz).total * esz);
+    p.smem_bwd = need_b <= (size_t)optin ? need_b : 0;
     *out = p;
     return SF_OK;
 }
@@ -200,7 +205,7 @@ static void destroy_all(sf_handle *h)
             h->ev[k] = nullptr;
         }
     DevBuf *bufs[] = {&h->inst_dev, &h->shapes_dev, &h->order_dev, &h->status_dev, &h->W64, &h->P64,
-                      &h->Pb64, &h->S64, &h->ck_x, &h->ck_l};
+                      &h->Pb64, &h->S64, &h->ck_x, &h->ck_l, &h->seg};
     if (h->esz == 4) {
         h->Wt.release();
         h->Pt.release();
@@ -373,7 +378,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
     }
     // checkpoints
     if (desc->ckpt_every > 0) {
-        h->n_slots = desc->max_iters / desc->ckpt_every + 1;
+        h->n_slots = desc->max_iters / desc->ckpt_every + 2;   // every c-th iterate, then the final one
         size_t b = (size_t)h->n_slots * h->xi_total * h->esz;
         if ((r = cuda_status(h->ck_x.alloc(b))) || (r = cuda_status(h->ck_l.alloc(b)))) {
             destroy_all(h);
@@ -401,9 +406,10 @@ extern "C" int sf_layout(const sf_handle *h, int32_t kind, int64_t *offsets)
     return SF_OK;
 }
 
+// The forward kernel's arguments for one solve (also the adjoint's view of that solve).
 template <typename T>
-static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, const void *x0, const void *l0,
-                   int iters, void *xo, void *lo, double *resid, int32_t *its, cudaStream_t st)
+static FwdArgs<T> fwd_args(const sf_handle *h, const void *bnd, const void *obs, const void *oab, const void *xc,
+                           const void *x0, const void *l0, int iters)
 {
     FwdArgs<T> a;
     memset(&a, 0, sizeof(a));
@@ -426,20 +432,29 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
     a.xc = (const T *)xc;
     a.x0 = (const T *)x0;
     a.l0 = (const T *)l0;
-    a.bnd = (const T *)data->bnd;
-    a.obs = (const T *)data->obs_c;
-    a.oab = (const T *)data->obs_ab;
-    a.xo = (T *)xo;
-    a.lo = (T *)lo;
-    a.resid = resid;
-    a.its = its;
+    a.bnd = (const T *)bnd;
+    a.obs = (const T *)obs;
+    a.oab = (const T *)oab;
     a.status = (int32_t *)h->status_dev.p;
     if (h->d.ckpt_every > 0) {
         a.ck_x = (T *)h->ck_x.p;
         a.ck_l = (T *)h->ck_l.p;
         a.ck_every = h->d.ckpt_every;
+        a.ck_final = h->n_slots - 1;
         a.ck_slot = h->xi_total;
     }
+    return a;
+}
+
+template <typename T>
+static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, const void *x0, const void *l0,
+                   int iters, void *xo, void *lo, double *resid, int32_t *its, cudaStream_t st)
+{
+    FwdArgs<T> a = fwd_args<T>(h, data->bnd, data->obs_c, data->obs_ab, xc, x0, l0, iters);
+    a.xo = (T *)xo;
+    a.lo = (T *)lo;
+    a.resid = resid;
+    a.its = its;
     for (int k = 0; k < SF_NKT; ++k) h->ev_used[k] = false;
     if (h->profile) SF_TRY(cudaEventRecord(h->ev[0], st));
     SF_TRY(launch_forward(a, h->plan.threads, h->plan.smem_fwd, st));
@@ -503,10 +518,43 @@ extern "C" int sf_solve(sf_handle *h, const sf_instance_data *data, const void *
 extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void *g_lam_out, const double *g_rp2,
                                  void *g_xi_cand, void *g_xi0, void *g_lam0, void *stream)
 {
-    (void)g_xi_out; (void)g_lam_out; (void)g_rp2; (void)g_xi_cand; (void)g_xi0; (void)g_lam0; (void)stream;
-    if (!h) return SF_EINVAL;
+    if (!h || !g_xi_cand) return SF_EINVAL;
     if (!h->last.valid) return SF_ESTATE;
-    return SF_EUNSUPPORTED;
+    if (!h->plan.smem_bwd) return SF_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t seg_bytes = (size_t)h->xi_total * h->plan.csize * h->d.ckpt_every * h->esz;
+    if (h->seg.bytes < seg_bytes) {
+        SF_TRY(cudaStreamSynchronize(st));
+        h->seg.release();
+        SF_TRY(h->seg.alloc(seg_bytes));
+    }
+    const SolveRecord &R = h->last;
+    int rc;
+    auto go = [&](auto tag) -> int {
+        using T = decltype(tag);
+        BwdArgs<T> b;
+        memset(&b, 0, sizeof(b));
+        b.f = fwd_args<T>(h, R.bnd, R.obs, R.oab, R.xc, R.x0, R.l0, R.iters);
+        b.gxo = (const T *)g_xi_out;
+        b.glo = (const T *)g_lam_out;
+        b.grp2 = g_rp2;
+        b.gxc = (T *)g_xi_cand;
+        b.gx0 = (T *)g_xi0;
+        b.gl0 = (T *)g_lam0;
+        b.seg = (T *)h->seg.p;
+        b.x0_null = R.x0 == nullptr;
+        if (h->profile) SF_TRY(cudaEventRecord(h->ev[2 * SF_KT_BACKWARD], st));
+        SF_TRY(launch_backward(b, h->plan.threads, h->plan.smem_bwd, st));
+        if (h->profile) {
+            SF_TRY(cudaEventRecord(h->ev[2 * SF_KT_BACKWARD + 1], st));
+            h->ev_used[SF_KT_BACKWARD] = true;
+        }
+        return SF_OK;
+    };
+    rc = h->esz == 8 ? go(double(0)) : go(float(0));
+    if (rc) return rc;
+    h->last_stream = st;
+    return SF_OK;
 }
 
 extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)

@@ -1,0 +1,181 @@
+// Hand-written adjoint of the unrolled SF iterations (the differentiable chain of T
+// in Fig. unroll_learning and Sec. IV-B): the vector-Jacobian product with respect to
+// the candidate xi and the initialisation (xi_bar^0, lambda^0).
+//
+// One thread-block cluster per instance, the same timestep split as the forward
+// kernel.  The forward kept (xi_bar, lambda) every c iterations; segments are
+// processed from the last to the first: the segment's iterates are recomputed with
+// the forward's own code (stored per CTA in global scratch) and then reversed.
+//
+// Adjoint of one iteration l in correction form, xi_bar' = xi_bar + P_eta v +
+// P_b (b - A xi_bar) with v = xi - xi_bar + lambda - 2 rho g and lambda' = lambda -
+// rho g, g = W'R(p), p = W xi_bar, from (xi_bar'*, lambda'*):
+//   x*  = xi_bar'* with its end coefficients cleared (they are overwritten by b)
+//   v*  = P_eta x*                        (P_eta symmetric)
+//   xi*      += v*,   lambda* = lambda'* + v*,   g* = -rho lambda'* - 2 rho v*
+//   R*  = W g*;  p* = sum over active rows of J' (R*_i - R*_j) (pairs; J even, r_1 odd),
+//                J' R*_i (obstacles), mask R*_i (box)
+//   xi_bar*  = x* - v* + W' p*   [- A' P_b' x* at l = 0, the end coefficients of xi_bar^0]
+// with J = dr_1/dDelta = (1 - s) I + s^3 Delta (M^-2 Delta)' on active rows and 0 on
+// inactive ones (derivative conventions of the kinks: the clamped branch counts as
+// active, Delta = 0 has zero derivative).
+#include "sf_iter.cuh"
+
+namespace sf {
+
+template <typename T, int ND, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
+{
+    using VP = Vec<T, NDP<ND>::v>;
+    const FwdArgs<T> &A = B.f;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = A.csize, cr = (int)cl.block_rank();
+    const int w = blockIdx.x / C;
+    const int ii = A.order ? A.order[w] : w;
+    const Inst<T> I0 = A.inst[ii];
+    const BwdCarve cv = backward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T));
+    Cta<T, ND> X;
+    X.init(A, smem_raw, cv.f, ii, cr, C);
+    X.load_constants(A, A.p_rows);
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T *xs = sm + cv.xs, *ls = sm + cv.ls, *cs = sm + cv.cs;
+    VP *Rs = reinterpret_cast<VP *>(sm + cv.Rs);
+    const int tid = X.tid, nt = X.nt, NN = X.NN, nxi = X.nxi, N = X.N, n = X.n;
+    const int64_t off = X.I.off_xi;
+    const T rho = X.rho;
+    for (int e = tid; e < NN; e += nt) {
+        xs[e] = B.gxo ? B.gxo[off + e] : T(0);
+        ls[e] = B.glo ? B.glo[off + e] : T(0);
+        cs[e] = T(0);
+    }
+    const int Lit = A.iters, ce = A.ck_every;
+    T *seg = B.seg + (off * C + (int64_t)cr * NN) * ce;   // this CTA's copy of a segment's iterates
+    int step = 0;                                         // parity of the all-reduce buffer
+
+    // seed from dL/d||r_p(xi_bar^L)||^2: gradient w r_1-weighted rows (w = 2 dL/d||r_p||^2)
+    const T wseed = B.grp2 ? T(2.0 * B.grp2[ii]) : T(0);
+    if (wseed != T(0)) {
+        for (int e = tid; e < NN; e += nt) X.xb[e] = A.ck_x[(int64_t)A.ck_final * A.ck_slot + off + e];
+        T *gme = X.gp + (step & 1) * X.gstride;
+        ++step;
+        for (int e = tid; e < NN; e += nt) gme[e] = T(0);
+        for (int k0 = X.k_lo; k0 < X.k_hi; k0 += X.hc) {
+            const int hcc = min(X.hc, X.k_hi - k0);
+            __syncthreads();
+            X.positions(k0, hcc, X.xb);
+            __syncthreads();
+            X.rows_adjoint(k0, hcc, Rs, wseed);
+            __syncthreads();
+            X.wt_acc(k0, hcc, X.Rb, gme);
+        }
+        cl.sync();
+        for (int e = tid; e < NN; e += nt) {
+            T s = T(0);
+            for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, q)[e];
+            xs[e] += s;
+        }
+    }
+
+    const int S = ce > 0 ? (Lit + ce - 1) / ce : 0;
+    for (int sg = S - 1; sg >= 0; --sg) {
+        const int l0 = sg * ce, l1 = min(Lit, l0 + ce);
+        __syncthreads();
+        for (int e = tid; e < NN; e += nt) {
+            X.xb[e] = A.ck_x[(int64_t)sg * A.ck_slot + off + e];
+            X.lam[e] = A.ck_l[(int64_t)sg * A.ck_slot + off + e];
+        }
+        if (sg == 0) X.boundary_gap();   // b - A xi_bar^0 for the first step's P_b term
+        // recompute the segment's iterates with the forward's code
+        for (int l = l0; l < l1; ++l) {
+            for (int e = tid; e < NN; e += nt) seg[(int64_t)(l - l0) * NN + e] = X.xb[e];
+            T *gme = X.gp + (step & 1) * X.gstride;
+            ++step;
+            T rp2 = T(0), mx2 = T(0);
+            X.rows_and_g(gme, rp2, mx2);
+            cl.sync();
+            X.update(cl, gme, X.need_b && l == 0);
+        }
+        // reverse through the segment
+        for (int l = l1 - 1; l >= l0; --l) {
+            const T *xl = seg + (int64_t)(l - l0) * NN;
+            T *xz = X.v, *vs = X.dd, *gs = X.lam, *xn = X.xb;
+            __syncthreads();
+            for (int e = tid; e < NN; e += nt) {
+                const int c = e - (e / nxi) * nxi;
+                xz[e] = (c == 0 || c == nxi - 1) ? T(0) : xs[e];
+            }
+            __syncthreads();
+            X.project(cl, xz, vs, false);
+            for (int e = tid; e < NN; e += nt) {
+                const T vst = vs[e];
+                gs[e] = -rho * ls[e] - T(2) * rho * vst;
+                xn[e] = xz[e] - vst;
+                cs[e] += vst;
+                ls[e] += vst;
+            }
+            __syncthreads();
+            if (l == 0) {   // - A' P_b' x*: the end coefficients of xi_bar^0
+                for (int q2 = tid; q2 < ND * 2 * n; q2 += nt) {
+                    const int ax = q2 / (2 * n), q = q2 - ax * 2 * n;
+                    T s = T(0);
+                    for (int r = 0; r < N; ++r) s += X.Pbg[(int64_t)r * 2 * n + q] * xz[ax * N + r];
+                    xn[(ax * n + (q >> 1)) * nxi + ((q & 1) ? nxi - 1 : 0)] -= s;
+                }
+            }
+            T *gme = X.gp + (step & 1) * X.gstride;
+            ++step;
+            for (int e = tid; e < NN; e += nt) gme[e] = T(0);
+            for (int k0 = X.k_lo; k0 < X.k_hi; k0 += X.hc) {
+                const int hcc = min(X.hc, X.k_hi - k0);
+                __syncthreads();
+                X.positions(k0, hcc, xl);
+                X.wvec(k0, hcc, gs, Rs);
+                __syncthreads();
+                X.rows_adjoint(k0, hcc, Rs, T(0));
+                __syncthreads();
+                X.wt_acc(k0, hcc, X.Rb, gme);
+            }
+            cl.sync();
+            for (int e = tid; e < NN; e += nt) {
+                T s = T(0);
+                for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, q)[e];
+                xs[e] = xn[e] + s;
+            }
+        }
+    }
+    if (cr == 0) {
+        for (int e = tid; e < NN; e += nt) {
+            B.gxc[off + e] = cs[e] + (B.x0_null ? xs[e] : T(0));
+            if (B.gx0) B.gx0[off + e] = xs[e];
+            if (B.gl0) B.gl0[off + e] = ls[e];
+        }
+    }
+    cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+template <typename T>
+static cudaError_t launch_backward_t(const BwdArgs<T> &a, int threads, size_t smem, cudaStream_t s)
+{
+    const FwdArgs<T> &f = a.f;
+    if (f.n_inst < 1 || f.csize < 1 || f.csize > kMaxCluster) return cudaErrorInvalidValue;
+    if (threads > max_threads((int)sizeof(T))) return cudaErrorInvalidValue;
+    constexpr int big = sizeof(T) == 8 ? 512 : 1024;
+    if (threads > 512) {
+        if (f.nd == 2) return launch_cluster(k_backward<T, 2, big>, a, f.n_inst, f.csize, threads, smem, s);
+        return launch_cluster(k_backward<T, 3, big>, a, f.n_inst, f.csize, threads, smem, s);
+    }
+    if (f.nd == 2) return launch_cluster(k_backward<T, 2, 512>, a, f.n_inst, f.csize, threads, smem, s);
+    return launch_cluster(k_backward<T, 3, 512>, a, f.n_inst, f.csize, threads, smem, s);
+}
+
+cudaError_t launch_backward(const BwdArgs<double> &a, int threads, size_t smem, cudaStream_t s)
+{
+    return launch_backward_t(a, threads, smem, s);
+}
+cudaError_t launch_backward(const BwdArgs<float> &a, int threads, size_t smem, cudaStream_t s)
+{
+    return launch_backward_t(a, threads, smem, s);
+}
+
+}  // namespace sf

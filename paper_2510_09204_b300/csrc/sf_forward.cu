@@ -23,364 +23,56 @@
 // The alpha/beta/d steps in algebraic form: with q = ||M^-1 Delta||, e = Delta when
 // q >= 1 and e = Delta / q otherwise; Delta = 0 gives e = (a, 0) in 2D and (0, 0, b)
 // in 3D for the row's own orientation (atan2(0, 0) = 0).
-#include <cooperative_groups.h>
-#include <math.h>
-
-#include "sf_internal.cuh"
-
-namespace cg = cooperative_groups;
+#include "sf_iter.cuh"
 
 namespace sf {
 
-template <typename T> __device__ __forceinline__ T rsq(T x);
-template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
-template <> __device__ __forceinline__ double rsq<double>(double x) { return 1.0 / sqrt(x); }
-
-template <typename T, int K>
-struct alignas(K * sizeof(T) >= 16 ? 16 : K * sizeof(T)) Vec {
-    T v[K];
-};
-
-template <int ND> struct NDP { static constexpr int v = ND == 2 ? 2 : 4; };
-
-// An active row (q <= a^2): r_1 = Delta (1 - 1/||M^-1 Delta||), or the tie value tie
-// when Delta = 0.  Adds r_1 to R, its squared norm to rp2 (if count) and to the max.
-template <typename T, int ND>
-__device__ __forceinline__ void row_active(const T (&d)[ND], T q, T ia2, const T (&tie)[ND], T (&R)[ND], T &rp2,
-                                           T &mx2, bool count)
-{
-    T r1[ND];
-    if (q > T(0)) {
-        const T f = T(1) - rsq(q * ia2);
-#pragma unroll
-        for (int ax = 0; ax < ND; ++ax) r1[ax] = d[ax] * f;
-    } else {
-#pragma unroll
-        for (int ax = 0; ax < ND; ++ax) r1[ax] = tie[ax];
-    }
-    T nn = T(0);
-#pragma unroll
-    for (int ax = 0; ax < ND; ++ax) {
-        R[ax] += r1[ax];
-        nn += r1[ax] * r1[ax];
-    }
-    if (count) rp2 += nn;
-    mx2 = fmax(mx2, nn);
-}
-
-// squared scaled distance: dx^2 + dy^2 + kz dz^2 with kz = a^2 / b^2
-template <typename T, int ND>
-__device__ __forceinline__ T qdist(const T (&d)[ND], T kz)
-{
-    T q = d[0] * d[0] + d[1] * d[1];
-    if (ND == 3) q += kz * d[ND - 1] * d[ND - 1];
-    return q;
-}
-
-// Far-away stand-ins: padded robots sit at +kFar, lanes without an item at -kFar, so
-// every distance test against them fails without a bounds check.
-template <typename T> struct Far { static constexpr T v = T(1e15); };
-
-// Rows of the items (i, k) of one chunk: positions P[i][kl] (vectors; robots padded to a
-// multiple of 4 with far dummies), obstacle records ob[m] = (c_x, c_y, [c_z,] a_o^2, kz_o,
-// 1/a_o^2, a_o, b_o) padded the same way; R is written to Rb[ax][i][kl].  Partners and
-// obstacles are tested four at a time (independent loads and tests); the warp votes once
-// per block and takes the rare active-row path only when one of its lanes needs it.
-template <typename T, int ND>
-__device__ __forceinline__ void rows_chunk(const Inst<T> &I, const Vec<T, NDP<ND>::v> *P, const T *ob,
-                                           const T *obs_g, T *Rb, int k0, int hcc, T &rp2, T &mx2)
-{
-    using VP = Vec<T, NDP<ND>::v>;
-    const int n = I.n, nobs = I.n_obs, items = n * hcc;
-    const int npad = (n + 3) & ~3, opad = (nobs + 3) & ~3;
-    const T a2 = I.a * I.a, ia2 = I.ia2, kz = (I.a * I.a) * I.ib2;
-    T tie_f[ND], tie_b[ND];   // r_1 of a coincident pair seen from the row's first / second robot
-#pragma unroll
-    for (int ax = 0; ax < ND; ++ax) tie_f[ax] = tie_b[ax] = T(0);
-    if (ND == 2) { tie_f[0] = -I.a; tie_b[0] = I.a; }
-    else { tie_f[ND - 1] = -I.b; tie_b[ND - 1] = I.b; }
-    for (int e0 = 0; e0 < items; e0 += blockDim.x) {
-        const int e = e0 + threadIdx.x;
-        const bool valid = e < items;
-        if (__all_sync(0xffffffffu, !valid)) continue;   // a whole warp without items skips the round
-        const int ee = valid ? e : 0;
-        const int i = ee / hcc, kl = ee - i * hcc, k = k0 + kl;
-        VP pi = P[i * hcc + kl];
-        if (!valid)
-#pragma unroll
-            for (int ax = 0; ax < ND; ++ax) pi.v[ax] = -Far<T>::v;
-        T R[ND];
-#pragma unroll
-        for (int ax = 0; ax < ND; ++ax) R[ax] = T(0);
-        // robot pairs: the row of pair (min(i,j), max(i,j)); j == i (q = 0) is sorted out in
-        // the slow path
-        for (int j0 = 0; j0 < npad; j0 += 4) {
-            T d[4][ND], q[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const VP pj = P[(j0 + u) * hcc + kl];
-#pragma unroll
-                for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - pj.v[ax];
-                q[u] = qdist<T, ND>(d[u], kz);
-            }
-            const bool any = (q[0] <= a2) | (q[1] <= a2) | (q[2] <= a2) | (q[3] <= a2);
-            if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u;
-                    if (q[u] <= a2 && j != i) {
-                        if (j > i) row_active<T, ND>(d[u], q[u], ia2, tie_f, R, rp2, mx2, true);
-                        else row_active<T, ND>(d[u], q[u], ia2, tie_b, R, rp2, mx2, false);
-                    }
-                }
-            }
-        }
-        // obstacles
-        for (int m0 = 0; m0 < opad; m0 += 4) {
-            T d[4][ND], q[4], lim[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int m = m0 + u;
-                const Vec<T, 4> r0 = reinterpret_cast<const Vec<T, 4> *>(ob)[2 * m];
-                if (I.dyn && m < nobs) {
-                    const T *c = obs_g + ((int64_t)m * I.H + k) * ND;
-#pragma unroll
-                    for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - c[ax];
-                } else {
-#pragma unroll
-                    for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - r0.v[ax];
-                }
-                q[u] = d[u][0] * d[u][0] + d[u][1] * d[u][1];
-                if (ND == 3) q[u] += ob[8 * m + 4] * d[u][ND - 1] * d[u][ND - 1];
-                lim[u] = r0.v[3];
-            }
-            const bool any = (q[0] <= lim[0]) | (q[1] <= lim[1]) | (q[2] <= lim[2]) | (q[3] <= lim[3]);
-            if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (q[u] <= lim[u]) {
-                        const int m = m0 + u;
-                        T tie[ND];
-#pragma unroll
-                        for (int ax = 0; ax < ND; ++ax) tie[ax] = T(0);
-                        if (ND == 2) tie[0] = -ob[8 * m + 6]; else tie[ND - 1] = -ob[8 * m + 7];
-                        row_active<T, ND>(d[u], q[u], ob[8 * m + 5], tie, R, rp2, mx2, true);
-                    }
-            }
-        }
-        if (!valid) continue;
-        // workspace box (G rows: upper side p <= p_max, lower side -p <= -p_min)
-#pragma unroll
-        for (int ax = 0; ax < ND; ++ax) {
-            const T u = pi.v[ax] - I.pmax[ax];
-            const T l = I.pmin[ax] - pi.v[ax];
-            if (u > T(0)) {
-                R[ax] += u;
-                rp2 += u * u;
-                mx2 = fmax(mx2, u * u);
-            }
-            if (l > T(0)) {
-                R[ax] -= l;
-                rp2 += l * l;
-                mx2 = fmax(mx2, l * l);
-            }
-        }
-#pragma unroll
-        for (int ax = 0; ax < ND; ++ax) Rb[(ax * n + i) * hcc + kl] = R[ax];
-    }
-}
-
-// Warp then block reduction of (sum, max, sum) into red[0..2] (all threads participate;
-// the result is valid after the caller's next barrier).
-template <typename T>
-__device__ __forceinline__ void block_reduce3_to(T a, T b, T c, T *red)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-    if (l == 0) {
-        red[w] = a;
-        red[32 + w] = b;
-        red[64 + w] = c;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        T x = T(0), y = T(0), z = T(0);
-        for (int q = 0; q < nw; ++q) {
-            x += red[q];
-            y = fmax(y, red[32 + q]);
-            z += red[64 + q];
-        }
-        red[96] = x;
-        red[97] = y;
-        red[98] = z;
-    }
-}
-
-// MAXT: the launch bound this instantiation is compiled for (512 or, FP32 only, 1024).
 template <typename T, int ND, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
     cg::cluster_group cl = cg::this_cluster();
-    const int tid = threadIdx.x, nt = blockDim.x;
     const int C = A.csize, cr = (int)cl.block_rank();
-    const int nxi = A.nxi;
     const int w = blockIdx.x / C;
     const int ii = A.order ? A.order[w] : w;
-    const Inst<T> I = A.inst[ii];
-    const Shape S = A.shapes[I.shape];
-    const int n = I.n, H = I.H, N = I.N, nobs = I.n_obs, hc = I.hc;
-    const int NN = ND * N;
-    const T rho = A.rho;
-    const bool dense = A.proj == SF_PROJ_DENSE;
-    const T invn = T(1) / T(n);
-    // this CTA's timesteps and projection rows
-    const int k_lo = (int)((int64_t)cr * H / C), k_hi = (int)((int64_t)(cr + 1) * H / C);
-    const int L = (N + C - 1) / C, r_lo = min(N, cr * L), r_hi = min(N, r_lo + L);
-    const FwdCarve cv = forward_carve(ND, nxi, H, n, nobs, hc, A.p_rows, (int)sizeof(T));
-    T *W = sm + cv.W, *xb = sm + cv.xb, *lam = sm + cv.lam, *xc = sm + cv.xc, *v = sm + cv.v;
-    T *gp = sm + cv.gp, *dl = sm + cv.dl, *Rb = sm + cv.Rb, *ob = sm + cv.ob, *bd = sm + cv.bd;
-    T *db = sm + cv.db, *sx = sm + cv.sx, *red = sm + cv.red, *Ps = sm + cv.Ps;
-    Vec<T, NDP<ND>::v> *P = reinterpret_cast<Vec<T, NDP<ND>::v> *>(sm + cv.pb);
-    const int64_t gstride = carve_round(NN + 4, (int)sizeof(T));
-    // ---- load
-    const T *Wg = A.W + S.off_W;
-    for (int e = tid; e < H * nxi; e += nt) W[e] = Wg[e];
-    const T *xcg = A.xc + I.off_xi;
-    const T *x0g = A.x0 ? A.x0 + I.off_xi : xcg;
+    const Inst<T> I0 = A.inst[ii];
+    const FwdCarve cv = forward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T));
+    Cta<T, ND> X;
+    X.init(A, smem_raw, cv, ii, cr, C);
+    X.load_constants(A, A.p_rows);
+    const int tid = X.tid, nt = X.nt, NN = X.NN;
+    const int64_t off = X.I.off_xi;
+    const T *x0g = A.x0 ? A.x0 + off : A.xc + off;
     for (int e = tid; e < NN; e += nt) {
-        xc[e] = xcg[e];
-        xb[e] = x0g[e];
-        lam[e] = A.l0 ? A.l0[I.off_xi + e] : T(0);
+        X.xb[e] = x0g[e];
+        X.lam[e] = A.l0 ? A.l0[off + e] : T(0);
     }
-    for (int e = tid; e < ND * n * 2; e += nt) bd[e] = A.bnd[I.off_bnd + e];
-    for (int m = nobs + tid; m < ((nobs + 3) & ~3); m += nt) {   // padding records: far away, zero radius
-        T *o = ob + 8 * m;
-        for (int q = 0; q < 8; ++q) o[q] = T(0);
-        for (int ax = 0; ax < ND; ++ax) o[ax] = Far<T>::v;
-        o[4] = T(1);
-    }
-    for (int m = tid; m < nobs; m += nt) {
-        const T ao = A.oab[I.off_oab + 2 * m], bo = A.oab[I.off_oab + 2 * m + 1];
-        T *o = ob + 8 * m;
-        for (int ax = 0; ax < 3; ++ax) o[ax] = (!I.dyn && ax < ND) ? A.obs[I.off_obs + (int64_t)m * ND + ax] : T(0);
-        o[3] = ao * ao;                 // compare d_x^2 + d_y^2 + kz_o d_z^2 with a_o^2
-        o[4] = (ao * ao) / (bo * bo);   // kz_o
-        o[5] = T(1) / (ao * ao);
-        o[6] = ao;
-        o[7] = bo;
-    }
-    const T *Pg = A.P + S.off_P;
-    const T *Pbg = A.Pb + S.off_Pb;
-    if (dense && A.p_rows > 0)
-        for (int e = tid; e < (r_hi - r_lo) * N; e += nt) Ps[e] = Pg[(int64_t)r_lo * N + e];
-    const T *Prow = (dense && A.p_rows > 0) ? Ps - (int64_t)r_lo * N : Pg;   // Prow[r * N + c], r in [r_lo, r_hi)
-    // structured blocks: P_dev, P_mean - P_dev, B_dev, B_mean - B_dev, then mv, pm, mb
-    T *Pdev = sx, *Pdif = sx + nxi * nxi, *Bdev = sx + 2 * nxi * nxi, *Bdif = Bdev + 2 * nxi;
-    T *mv = Bdif + 2 * nxi, *pm = mv + ND * nxi, *mb = pm + ND * nxi;
-    if (!dense) {
-        const T *Sg = A.Sx + S.off_S;
-        for (int e = tid; e < nxi * nxi; e += nt) {
-            Pdev[e] = Sg[e];
-            Pdif[e] = Sg[nxi * nxi + e] - Sg[e];
-        }
-        for (int e = tid; e < 2 * nxi; e += nt) {
-            Bdev[e] = Sg[2 * nxi * nxi + e];
-            Bdif[e] = Sg[2 * nxi * nxi + 2 * nxi + e] - Sg[2 * nxi * nxi + e];
-        }
-    }
-    __syncthreads();
-    // b - A xi_bar^0: nonzero only when the initial iterate misses the boundary values
-    int need_b = 0;
-    for (int e = tid; e < ND * n * 2; e += nt) {
-        const int r = e >> 1, s = e & 1;
-        db[e] = bd[e] - xb[r * nxi + (s ? nxi - 1 : 0)];
-        if (db[e] != T(0)) need_b = 1;
-    }
-    need_b = __syncthreads_or(need_b);
-    if (need_b && !dense)
-        for (int e = tid; e < ND * 2; e += nt) {
-            const int ax = e >> 1, s = e & 1;
-            T acc = T(0);
-            for (int i = 0; i < n; ++i) acc += db[(ax * n + i) * 2 + s];
-            mb[e] = acc * invn;
-        }
+    X.boundary_gap();
 
     int its_tol = -1;
     T fp = T(0), fp_prev = T(0);
-    T gstat[3] = {T(0), T(0), T(0)};
     bool bad = false;
     for (int it = 0; it <= A.iters; ++it) {
         const bool last = it == A.iters;   // the final pass only reduces the last fixed-point step
-        T *gme = gp + (it & 1) * gstride;
+        T *gme = X.gp + (it & 1) * X.gstride;
         T rp2 = T(0), mx2 = T(0);
         if (!last) {
             if (cr == 0 && A.ck_every > 0 && it % A.ck_every == 0) {
-                const int64_t base = (int64_t)(it / A.ck_every) * A.ck_slot + I.off_xi;
+                const int64_t base = (int64_t)(it / A.ck_every) * A.ck_slot + off;
                 for (int e = tid; e < NN; e += nt) {
-                    A.ck_x[base + e] = xb[e];
-                    A.ck_l[base + e] = lam[e];
+                    A.ck_x[base + e] = X.xb[e];
+                    A.ck_l[base + e] = X.lam[e];
                 }
             }
-            for (int e = tid; e < NN; e += nt) gme[e] = T(0);
-            for (int k0 = k_lo; k0 < k_hi; k0 += hc) {
-                const int hcc = min(hc, k_hi - k0);
-                __syncthreads();
-                // p[ax][i][k] = sum_c W[k][c] xi_bar[ax][i][c], one (axis, robot, timestep) per thread
-                T *Ps_ = reinterpret_cast<T *>(P);
-                for (int e = tid; e < ND * n * hcc; e += nt) {
-                    const int r = e / hcc, kl = e - r * hcc, ax = r / n, i = r - ax * n;
-                    const T *wr = W + (k0 + kl) * nxi;
-                    const T *xr = xb + r * nxi;
-                    T s0 = T(0), s1 = T(0), s2 = T(0);
-                    int c = 0;
-                    for (; c + 2 < nxi; c += 3) {
-                        s0 += wr[c] * xr[c];
-                        s1 += wr[c + 1] * xr[c + 1];
-                        s2 += wr[c + 2] * xr[c + 2];
-                    }
-                    for (; c < nxi; ++c) s0 += wr[c] * xr[c];
-                    Ps_[(i * hcc + kl) * NDP<ND>::v + ax] = (s0 + s1) + s2;
-                }
-                for (int e = n * hcc + tid; e < ((n + 3) & ~3) * hcc; e += nt) {   // padding robots
-                    Vec<T, NDP<ND>::v> p;
-#pragma unroll
-                    for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = Far<T>::v;
-                    P[e] = p;
-                }
-                __syncthreads();
-                rows_chunk<T, ND>(I, P, ob, A.obs + I.off_obs, Rb, k0, hcc, rp2, mx2);
-                __syncthreads();
-                for (int e = tid; e < NN; e += nt) {
-                    const int r = e / nxi, c = e - r * nxi;
-                    const T *rr = Rb + r * hcc;
-                    const T *wc = W + k0 * nxi + c;
-                    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-                    int kl = 0;
-                    for (; kl + 3 < hcc; kl += 4) {
-                        s0 += wc[kl * nxi] * rr[kl];
-                        s1 += wc[(kl + 1) * nxi] * rr[kl + 1];
-                        s2 += wc[(kl + 2) * nxi] * rr[kl + 2];
-                        s3 += wc[(kl + 3) * nxi] * rr[kl + 3];
-                    }
-                    for (; kl < hcc; ++kl) s0 += wc[kl * nxi] * rr[kl];
-                    gme[e] += (s0 + s1) + (s2 + s3);
-                }
-            }
+            X.rows_and_g(gme, rp2, mx2);
         }
         // per-CTA stats (this iteration's rows, the previous iteration's step) -> gme[NN..]
-        block_reduce3_to<T>(rp2, mx2, fp, red);
+        block_reduce3_to<T>(rp2, mx2, fp, X.red);
         __syncthreads();
         if (tid == 0) {
-            gme[NN] = red[96];
-            gme[NN + 1] = red[97];
-            gme[NN + 2] = red[98];
+            gme[NN] = X.red[96];
+            gme[NN + 1] = X.red[97];
+            gme[NN + 2] = X.red[98];
         }
         cl.sync();
         if (tid == 0) {
@@ -390,9 +82,6 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
                 s_rp2 += rg[NN];
                 s_mx2 = fmax(s_mx2, rg[NN + 1]);
             }
-            gstat[0] = s_rp2;
-            gstat[1] = s_mx2;
-            gstat[2] = gme[NN + 2];
             if (it > 0) {
                 fp_prev = gme[NN + 2];
                 if (!isfinite(fp_prev)) bad = true;
@@ -405,118 +94,18 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
             }
         }
         if (last) break;
-        // g over the cluster (fixed order: the same bits in every CTA), lambda step, correction
-        fp = T(0);
-        for (int e = tid; e < NN; e += nt) {
-            T gg = T(0);
-            for (int q = 0; q < C; ++q) gg += cl.map_shared_rank(gme, q)[e];
-            const T ln = lam[e] - rho * gg;
-            const T dlam = ln - lam[e];
-            fp += dlam * dlam;
-            v[e] = xc[e] - xb[e] + ln - rho * gg;
-            lam[e] = ln;
-        }
-        __syncthreads();
-        const bool corr_b = need_b && it == 0;
-        if (dense) {
-            // rows [r_lo, r_hi) of P_eta v: 8 lanes per row, interleaved columns
-            const int seg = 8, rows = r_hi - r_lo;
-            // the trip count is the same for every thread, so whole warps take part in the shuffles
-            for (int t0 = 0; t0 < rows * seg; t0 += nt) {
-                const int t = t0 + tid;
-                const bool act = t < rows * seg;
-                const int r = r_lo + t / seg, s = t % seg;
-                T acc[ND];
-#pragma unroll
-                for (int ax = 0; ax < ND; ++ax) acc[ax] = T(0);
-                if (act) {
-                    const T *pr = Prow + (int64_t)r * N;
-                    for (int c = s; c < N; c += seg) {
-                        const T pv = pr[c];
-#pragma unroll
-                        for (int ax = 0; ax < ND; ++ax) acc[ax] += pv * v[ax * N + c];
-                    }
-                    if (corr_b)
-                        for (int q = s; q < 2 * n; q += seg) {
-                            const T pbq = Pbg[(int64_t)r * 2 * n + q];
-#pragma unroll
-                            for (int ax = 0; ax < ND; ++ax) acc[ax] += pbq * db[(ax * n + (q >> 1)) * 2 + (q & 1)];
-                        }
-                }
-#pragma unroll
-                for (int ax = 0; ax < ND; ++ax) {
-                    T a = acc[ax];
-                    a += __shfl_xor_sync(0xffffffffu, a, 4);
-                    a += __shfl_xor_sync(0xffffffffu, a, 2);
-                    a += __shfl_xor_sync(0xffffffffu, a, 1);
-                    if (act && s == 0) dl[ax * N + r] = a;
-                }
-            }
-            cl.sync();
-            for (int e = tid; e < NN; e += nt) {
-                const int r = e / nxi, c = e - r * nxi, row = e - (e / N) * N;
-                const T *src = cl.map_shared_rank(dl, row / L);
-                T xn = xb[e] + src[e];
-                if (c == 0) xn = bd[r * 2];                  // A xi_bar = b holds exactly
-                else if (c == nxi - 1) xn = bd[r * 2 + 1];
-                const T dx = xn - xb[e];
-                fp += dx * dx;
-                xb[e] = xn;
-            }
-        } else {
-            // Kronecker form, per axis with robot mean m of v:
-            //   delta_i = P_dev v_i + (P_mean - P_dev) m   (+ the same with B for b - A xi_bar)
-            {   // robot means, one warp per (axis, coefficient), lanes over robots
-                const int lane = tid & 31, nw = nt >> 5;
-                for (int pq = tid >> 5; pq < ND * nxi; pq += nw) {
-                    const int ax = pq / nxi, c = pq - ax * nxi;
-                    T s = T(0);
-                    for (int i = lane; i < n; i += 32) s += v[(ax * n + i) * nxi + c];
-#pragma unroll
-                    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                    if (lane == 0) mv[pq] = s * invn;
-                }
-            }
-            __syncthreads();
-            for (int e = tid; e < ND * nxi; e += nt) {
-                const int ax = e / nxi, u = e - ax * nxi;
-                T s = T(0);
-                for (int c = 0; c < nxi; ++c) s += Pdif[u * nxi + c] * mv[ax * nxi + c];
-                if (corr_b) s += Bdif[u * 2] * mb[ax * 2] + Bdif[u * 2 + 1] * mb[ax * 2 + 1];
-                pm[e] = s;
-            }
-            __syncthreads();
-            for (int e = tid; e < NN; e += nt) {
-                const int r = e / nxi, u = e - r * nxi, ax = r / n;
-                const T *vr = v + r * nxi;
-                const T *pu = Pdev + u * nxi;
-                T s0 = pm[ax * nxi + u], s1 = T(0);
-                int c = 0;
-                for (; c + 1 < nxi; c += 2) {
-                    s0 += pu[c] * vr[c];
-                    s1 += pu[c + 1] * vr[c + 1];
-                }
-                if (c < nxi) s0 += pu[c] * vr[c];
-                if (corr_b) s1 += Bdev[u * 2] * db[r * 2] + Bdev[u * 2 + 1] * db[r * 2 + 1];
-                T xn = xb[e] + (s0 + s1);
-                if (u == 0) xn = bd[r * 2];
-                else if (u == nxi - 1) xn = bd[r * 2 + 1];
-                const T dx = xn - xb[e];
-                fp += dx * dx;
-                xb[e] = xn;
-            }
-        }
+        fp = X.update(cl, gme, X.need_b && it == 0);
     }
     if (cr == 0) {
         for (int e = tid; e < NN; e += nt) {
-            A.xo[I.off_xi + e] = xb[e];
-            if (A.lo) A.lo[I.off_xi + e] = lam[e];
+            A.xo[off + e] = X.xb[e];
+            if (A.lo) A.lo[off + e] = X.lam[e];
         }
-        if (A.ck_every > 0 && A.iters % A.ck_every == 0) {
-            const int64_t base = (int64_t)(A.iters / A.ck_every) * A.ck_slot + I.off_xi;
+        if (A.ck_every > 0) {   // the final iterate, for the adjoint's residual seed
+            const int64_t base = (int64_t)A.ck_final * A.ck_slot + off;
             for (int e = tid; e < NN; e += nt) {
-                A.ck_x[base + e] = xb[e];
-                A.ck_l[base + e] = lam[e];
+                A.ck_x[base + e] = X.xb[e];
+                A.ck_l[base + e] = X.lam[e];
             }
         }
         if (tid == 0) {
@@ -652,27 +241,6 @@ __global__ void __launch_bounds__(512) k_residual(ResArgs<T> A)
         if (!isfinite(s_rp2)) A.status[ii] = SF_ENONFINITE;
     }
     cl.sync();
-}
-
-template <typename K, typename Arg>
-static cudaError_t launch_cluster(K kernel, const Arg &a, int n_inst, int csize, int threads, size_t smem,
-                                  cudaStream_t s)
-{
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(n_inst * csize), 1, 1);
-    cfg.blockDim = dim3((unsigned)threads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)csize;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
 template <typename T>

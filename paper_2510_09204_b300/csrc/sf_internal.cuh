@@ -40,7 +40,7 @@ struct Shape {
 // Shared-memory carve of the forward kernel, in elements of T.  Every region starts on a
 // 32-byte boundary.  Host and kernel both call forward_carve, so they cannot disagree.
 struct FwdCarve {
-    int64_t W, xb, lam, xc, v, gp, dl, pb, Rb, ob, bd, db, sx, red, Ps, total;
+    int64_t W, xb, lam, xc, v, gp, dl, dd, pb, Rb, ob, bd, db, sx, red, Ps, total;
 };
 
 __host__ __device__ inline int64_t carve_round(int64_t cnt, int esz)
@@ -63,6 +63,7 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n,
     c.v = o;   o += carve_round(NN, esz);
     c.gp = o;  o += 2 * carve_round(NN + 4, esz);                 // partial g + stats, two buffers
     c.dl = o;  o += carve_round(NN, esz);                         // projection rows of this CTA
+    c.dd = o;  o += carve_round(NN, esz);                         // projection output
     const int64_t npad = (n + 3) / 4 * 4, opad = (nobs + 3) / 4 * 4;
     c.pb = o;  o += carve_round(npad * hc * ndp, esz);            // positions [i][k] as vectors (+ far dummies)
     c.Rb = o;  o += carve_round((int64_t)nd * n * hc, esz);       // row sums R [ax][i][k]
@@ -74,6 +75,27 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n,
     c.Ps = o;  o += carve_round((int64_t)p_rows * N, esz);
     c.total = o;
     return c;
+}
+
+// The adjoint kernel's carve: the forward carve followed by the adjoint state
+// (dL/dxi_bar, dL/dlambda, dL/dxi_cand) and R* in the vector layout of the positions.
+struct BwdCarve {
+    FwdCarve f;
+    int64_t xs, ls, cs, Rs, total;
+};
+
+__host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz)
+{
+    BwdCarve b;
+    b.f = forward_carve(nd, nxi, H, n, nobs, hc, p_rows, esz);
+    const int64_t NN = (int64_t)nd * n * nxi, npad = (n + 3) / 4 * 4, ndp = nd == 2 ? 2 : 4;
+    int64_t o = b.f.total;
+    b.xs = o; o += carve_round(NN, esz);
+    b.ls = o; o += carve_round(NN, esz);
+    b.cs = o; o += carve_round(NN, esz);
+    b.Rs = o; o += carve_round(npad * hc * ndp, esz);
+    b.total = o;
+    return b;
 }
 
 template <typename T>
@@ -96,8 +118,19 @@ struct FwdArgs {
     float *hist;                // [n_inst][iters] (nullable)
     T *ck_x, *ck_l;             // checkpoints: slot-major, packed like xi (nullable)
     int ck_every;
+    int ck_final;               // slot that receives the final iterate
     int64_t ck_slot;            // elements per checkpoint slot (= packed xi length)
     int32_t *status;            // [n_inst]
+};
+
+template <typename T>
+struct BwdArgs {
+    FwdArgs<T> f;               // instance data, operators, checkpoints, iteration count
+    const T *gxo, *glo;         // seeds dL/dxi_bar^L, dL/dlambda^L (nullable)
+    const double *grp2;         // dL/d||r_p(xi_bar^L)||^2 per instance (nullable)
+    T *gxc, *gx0, *gl0;         // dL/dxi_cand, dL/dxi_bar^0, dL/dlambda^0 (gx0, gl0 nullable)
+    T *seg;                     // recomputed iterates of a segment, per instance and CTA
+    int x0_null;                // the solve started from xi_bar^0 = xi_cand
 };
 
 template <typename T>
@@ -125,6 +158,7 @@ struct Plan {
     int p_rows = 0;       // rows of P_eta staged per CTA (dense projection), 0 = read from global
     size_t smem_fwd = 0;  // dynamic shared memory of the forward launch
     size_t smem_res = 0;  // and of the residual launch
+    size_t smem_bwd = 0;  // and of the adjoint launch (0: does not fit)
 };
 
 // Chooses the cluster size (csize_req > 0 forces it), each instance's timestep chunk
@@ -138,6 +172,8 @@ cudaError_t launch_forward(const FwdArgs<double> &a, int threads, size_t smem, c
 cudaError_t launch_forward(const FwdArgs<float> &a, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_residual(const ResArgs<double> &a, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_residual(const ResArgs<float> &a, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_backward(const BwdArgs<double> &a, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_backward(const BwdArgs<float> &a, int threads, size_t smem, cudaStream_t s);
 
 // Shared memory (doubles) the residual kernel needs for one instance at a chunk of hc timesteps.
 __host__ __device__ inline int64_t residual_doubles(int nd, int nxi, int H, int n, int nobs, int hc)

@@ -1,0 +1,635 @@
+// Device pieces of one SF iteration shared by the forward and the adjoint kernels.
+//
+// An instance is owned by a thread-block cluster of C CTAs; CTA r takes a contiguous
+// share [k_lo, k_hi) of the H timesteps and keeps a full copy of the iterate.  The
+// phases of an iteration (positions, constraint rows, the W' aggregation, the
+// cluster all-reduce through distributed shared memory, the multiplier step and the
+// projection) are methods of Cta so that the adjoint kernel recomputes checkpoint
+// segments with exactly the forward's arithmetic.
+#pragma once
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "sf_internal.cuh"
+
+namespace sf {
+
+namespace cg = cooperative_groups;
+
+template <typename T> __device__ __forceinline__ T rsq(T x);
+template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsq<double>(double x) { return 1.0 / sqrt(x); }
+
+template <typename T, int K>
+struct alignas(K * sizeof(T) >= 16 ? 16 : K * sizeof(T)) Vec {
+    T v[K];
+};
+
+template <int ND> struct NDP { static constexpr int v = ND == 2 ? 2 : 4; };
+
+// Far-away stand-ins: padded robots sit at +kFar, lanes without an item at -kFar, so
+// every distance test against them fails without a bounds check.
+template <typename T> struct Far { static constexpr T v = T(1e15); };
+
+// An active row (q <= a^2): r_1 = Delta (1 - 1/||M^-1 Delta||), or the tie value tie
+// when Delta = 0.  Adds r_1 to R, its squared norm to rp2 (if count) and to the max.
+template <typename T, int ND>
+__device__ __forceinline__ void row_active(const T (&d)[ND], T q, T ia2, const T (&tie)[ND], T (&R)[ND], T &rp2,
+                                           T &mx2, bool count)
+{
+    T r1[ND];
+    if (q > T(0)) {
+        const T f = T(1) - rsq(q * ia2);
+#pragma unroll
+        for (int ax = 0; ax < ND; ++ax) r1[ax] = d[ax] * f;
+    } else {
+#pragma unroll
+        for (int ax = 0; ax < ND; ++ax) r1[ax] = tie[ax];
+    }
+    T nn = T(0);
+#pragma unroll
+    for (int ax = 0; ax < ND; ++ax) {
+        R[ax] += r1[ax];
+        nn += r1[ax] * r1[ax];
+    }
+    if (count) rp2 += nn;
+    mx2 = fmax(mx2, nn);
+}
+
+// Transposed Jacobian of an active row (q > 0): with s = 1/||M^-1 d||,
+// r_1(d) = d (1 - s) and dr_1/dd = (1 - s) I + s^3 d (M^-2 d)'.  Adds J' y to out.
+// mode 0: y given; mode 1: y = w r_1(d) (gradient of w ||r_1||^2 / 2, times 2 by the caller).
+template <typename T, int ND>
+__device__ __forceinline__ void row_adjoint(const T (&d)[ND], T q, T ia2, T ib2, const T (&y_in)[ND], T w, bool seed,
+                                            T (&out)[ND])
+{
+    if (!(q > T(0))) return;   // Delta = 0: the row's e is constant there (zero derivative)
+    const T s = rsq(q * ia2), f = T(1) - s;
+    T y[ND];
+#pragma unroll
+    for (int ax = 0; ax < ND; ++ax) y[ax] = seed ? w * d[ax] * f : y_in[ax];
+    T dy = T(0);
+#pragma unroll
+    for (int ax = 0; ax < ND; ++ax) dy += d[ax] * y[ax];
+    const T s3dy = s * s * s * dy;
+#pragma unroll
+    for (int ax = 0; ax < ND; ++ax) out[ax] += f * y[ax] + s3dy * d[ax] * (ax == 2 ? ib2 : ia2);
+}
+
+// squared scaled distance: dx^2 + dy^2 + kz dz^2 with kz = a^2 / b^2
+template <typename T, int ND>
+__device__ __forceinline__ T qdist(const T (&d)[ND], T kz)
+{
+    T q = d[0] * d[0] + d[1] * d[1];
+    if (ND == 3) q += kz * d[ND - 1] * d[ND - 1];
+    return q;
+}
+
+// Warp then block reduction of (sum, max, sum) into red[96..98] (the result is valid
+// after the caller's next barrier).
+template <typename T>
+__device__ __forceinline__ void block_reduce3_to(T a, T b, T c, T *red)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    if (l == 0) {
+        red[w] = a;
+        red[32 + w] = b;
+        red[64 + w] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T x = T(0), y = T(0), z = T(0);
+        for (int q = 0; q < nw; ++q) {
+            x += red[q];
+            y = fmax(y, red[32 + q]);
+            z += red[64 + q];
+        }
+        red[96] = x;
+        red[97] = y;
+        red[98] = z;
+    }
+}
+
+template <typename T, int ND>
+struct Cta {
+    using VP = Vec<T, NDP<ND>::v>;
+    int tid, nt, C, cr, nxi, n, npad, H, N, NN, nobs, opad, hc, k_lo, k_hi, L, r_lo, r_hi, ii;
+    bool dense;
+    T rho, invn;
+    Inst<T> I;
+    Shape S;
+    T *W, *xb, *lam, *xc, *v, *gp, *dl, *dd, *Rb, *ob, *bd, *db, *sx, *red, *Ps;
+    VP *P;
+    const T *Prow, *Pbg, *obs_g;
+    int64_t gstride;
+    T *Pdev, *Pdif, *Bdev, *Bdif, *mv, *pm, *mb;
+    int need_b;
+
+    __device__ void init(const FwdArgs<T> &A, unsigned char *smem_raw, const FwdCarve &cv, int inst, int rank, int csize)
+    {
+        T *sm = reinterpret_cast<T *>(smem_raw);
+        tid = threadIdx.x;
+        nt = blockDim.x;
+        C = csize;
+        cr = rank;
+        ii = inst;
+        nxi = A.nxi;
+        I = A.inst[ii];
+        S = A.shapes[I.shape];
+        n = I.n;
+        npad = (n + 3) & ~3;
+        H = I.H;
+        N = I.N;
+        NN = ND * N;
+        nobs = I.n_obs;
+        opad = (nobs + 3) & ~3;
+        hc = I.hc;
+        rho = A.rho;
+        invn = T(1) / T(n);
+        dense = A.proj == SF_PROJ_DENSE;
+        k_lo = (int)((int64_t)cr * H / C);
+        k_hi = (int)((int64_t)(cr + 1) * H / C);
+        L = (N + C - 1) / C;
+        r_lo = min(N, cr * L);
+        r_hi = min(N, r_lo + L);
+        W = sm + cv.W; xb = sm + cv.xb; lam = sm + cv.lam; xc = sm + cv.xc; v = sm + cv.v;
+        gp = sm + cv.gp; dl = sm + cv.dl; dd = sm + cv.dd; Rb = sm + cv.Rb; ob = sm + cv.ob;
+        bd = sm + cv.bd; db = sm + cv.db; sx = sm + cv.sx; red = sm + cv.red; Ps = sm + cv.Ps;
+        P = reinterpret_cast<VP *>(sm + cv.pb);
+        gstride = carve_round(NN + 4, (int)sizeof(T));
+        Pbg = A.Pb + S.off_Pb;
+        obs_g = A.obs + I.off_obs;
+        Pdev = sx; Pdif = sx + nxi * nxi; Bdev = sx + 2 * nxi * nxi; Bdif = Bdev + 2 * nxi;
+        mv = Bdif + 2 * nxi; pm = mv + ND * nxi; mb = pm + ND * nxi;
+        Prow = nullptr;
+        need_b = 0;
+    }
+
+    // Basis, candidate, boundary values, obstacle records and projection operators.
+    __device__ void load_constants(const FwdArgs<T> &A, int p_rows)
+    {
+        const T *Wg = A.W + S.off_W;
+        for (int e = tid; e < H * nxi; e += nt) W[e] = Wg[e];
+        const T *xcg = A.xc + I.off_xi;
+        for (int e = tid; e < NN; e += nt) xc[e] = xcg[e];
+        for (int e = tid; e < ND * n * 2; e += nt) bd[e] = A.bnd[I.off_bnd + e];
+        for (int m = nobs + tid; m < opad; m += nt) {   // padding records: far away, zero radius
+            T *o = ob + 8 * m;
+            for (int q = 0; q < 8; ++q) o[q] = T(0);
+            for (int ax = 0; ax < ND; ++ax) o[ax] = Far<T>::v;
+            o[4] = T(1);
+        }
+        for (int m = tid; m < nobs; m += nt) {
+            const T ao = A.oab[I.off_oab + 2 * m], bo = A.oab[I.off_oab + 2 * m + 1];
+            T *o = ob + 8 * m;
+            for (int ax = 0; ax < 3; ++ax) o[ax] = (!I.dyn && ax < ND) ? A.obs[I.off_obs + (int64_t)m * ND + ax] : T(0);
+            o[3] = ao * ao;                 // compare d_x^2 + d_y^2 + kz_o d_z^2 with a_o^2
+            o[4] = (ao * ao) / (bo * bo);   // kz_o
+            o[5] = T(1) / (ao * ao);
+            o[6] = ao;
+            o[7] = bo;
+        }
+        const T *Pg = A.P + S.off_P;
+        if (dense && p_rows > 0)
+            for (int e = tid; e < (r_hi - r_lo) * N; e += nt) Ps[e] = Pg[(int64_t)r_lo * N + e];
+        Prow = (dense && p_rows > 0) ? Ps - (int64_t)r_lo * N : Pg;   // Prow[r * N + c], r in [r_lo, r_hi)
+        if (!dense) {
+            const T *Sg = A.Sx + S.off_S;
+            for (int e = tid; e < nxi * nxi; e += nt) {
+                Pdev[e] = Sg[e];
+                Pdif[e] = Sg[nxi * nxi + e] - Sg[e];
+            }
+            for (int e = tid; e < 2 * nxi; e += nt) {
+                Bdev[e] = Sg[2 * nxi * nxi + e];
+                Bdif[e] = Sg[2 * nxi * nxi + 2 * nxi + e] - Sg[2 * nxi * nxi + e];
+            }
+        }
+    }
+
+    // b - A xi_bar for the current xb (nonzero only when it misses the boundary values);
+    // sets need_b (block-uniform) and the robot means mb for the structured form.
+    __device__ void boundary_gap()
+    {
+        __syncthreads();
+        int nb = 0;
+        for (int e = tid; e < ND * n * 2; e += nt) {
+            const int r = e >> 1, s = e & 1;
+            db[e] = bd[e] - xb[r * nxi + (s ? nxi - 1 : 0)];
+            if (db[e] != T(0)) nb = 1;
+        }
+        need_b = __syncthreads_or(nb);
+        if (need_b && !dense)
+            for (int e = tid; e < ND * 2; e += nt) {
+                const int ax = e >> 1, s = e & 1;
+                T acc = T(0);
+                for (int i = 0; i < n; ++i) acc += db[(ax * n + i) * 2 + s];
+                mb[e] = acc * invn;
+            }
+        __syncthreads();
+    }
+
+    // out[i][kl][ax] = sum_c W[k0 + kl][c] coeff[ax][i][c] (vector layout, one (ax, i, kl) per thread)
+    __device__ void wvec(int k0, int hcc, const T *coeff, VP *out)
+    {
+        T *o = reinterpret_cast<T *>(out);
+        for (int e = tid; e < ND * n * hcc; e += nt) {
+            const int r = e / hcc, kl = e - r * hcc, ax = r / n, i = r - ax * n;
+            const T *wr = W + (k0 + kl) * nxi;
+            const T *xr = coeff + r * nxi;
+            T s0 = T(0), s1 = T(0), s2 = T(0);
+            int c = 0;
+            for (; c + 2 < nxi; c += 3) {
+                s0 += wr[c] * xr[c];
+                s1 += wr[c + 1] * xr[c + 1];
+                s2 += wr[c + 2] * xr[c + 2];
+            }
+            for (; c < nxi; ++c) s0 += wr[c] * xr[c];
+            o[(i * hcc + kl) * NDP<ND>::v + ax] = (s0 + s1) + s2;
+        }
+    }
+
+    // positions of coeff for the chunk, robots padded with far stand-ins
+    __device__ void positions(int k0, int hcc, const T *coeff)
+    {
+        wvec(k0, hcc, coeff, P);
+        for (int e = n * hcc + tid; e < npad * hcc; e += nt) {
+            VP p;
+#pragma unroll
+            for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = Far<T>::v;
+            P[e] = p;
+        }
+    }
+
+    // dst[ax][i][c] += sum_kl W[k0 + kl][c] src[ax][i][kl]
+    __device__ void wt_acc(int k0, int hcc, const T *src, T *dst)
+    {
+        for (int e = tid; e < NN; e += nt) {
+            const int r = e / nxi, c = e - r * nxi;
+            const T *rr = src + r * hcc;
+            const T *wc = W + k0 * nxi + c;
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+            int kl = 0;
+            for (; kl + 3 < hcc; kl += 4) {
+                s0 += wc[kl * nxi] * rr[kl];
+                s1 += wc[(kl + 1) * nxi] * rr[kl + 1];
+                s2 += wc[(kl + 2) * nxi] * rr[kl + 2];
+                s3 += wc[(kl + 3) * nxi] * rr[kl + 3];
+            }
+            for (; kl < hcc; ++kl) s0 += wc[kl * nxi] * rr[kl];
+            dst[e] += (s0 + s1) + (s2 + s3);
+        }
+    }
+
+    // Rows of the items (i, k) of one chunk: R written to Rb[ax][i][kl].  Partners and
+    // obstacles are tested four at a time; the warp votes once per block of four and takes
+    // the rare active-row path only when one of its lanes needs it.
+    __device__ void rows(int k0, int hcc, T &rp2, T &mx2)
+    {
+        const int items = n * hcc;
+        const T a2 = I.a * I.a, ia2 = I.ia2, kz = (I.a * I.a) * I.ib2;
+        T tie_f[ND], tie_b[ND];   // r_1 of a coincident pair seen from the row's first / second robot
+#pragma unroll
+        for (int ax = 0; ax < ND; ++ax) tie_f[ax] = tie_b[ax] = T(0);
+        if (ND == 2) { tie_f[0] = -I.a; tie_b[0] = I.a; }
+        else { tie_f[ND - 1] = -I.b; tie_b[ND - 1] = I.b; }
+        for (int e0 = 0; e0 < items; e0 += nt) {
+            const int e = e0 + tid;
+            const bool valid = e < items;
+            if (__all_sync(0xffffffffu, !valid)) continue;   // a whole warp without items skips the round
+            const int ee = valid ? e : 0;
+            const int i = ee / hcc, kl = ee - i * hcc, k = k0 + kl;
+            VP pi = P[i * hcc + kl];
+            if (!valid)
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax) pi.v[ax] = -Far<T>::v;
+            T R[ND];
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) R[ax] = T(0);
+            // robot pairs: the row of pair (min(i,j), max(i,j)); j == i (q = 0) is excluded in
+            // the slow path
+            for (int j0 = 0; j0 < npad; j0 += 4) {
+                T d[4][ND], q[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const VP pj = P[(j0 + u) * hcc + kl];
+#pragma unroll
+                    for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - pj.v[ax];
+                    q[u] = qdist<T, ND>(d[u], kz);
+                }
+                const bool any = (q[0] <= a2) | (q[1] <= a2) | (q[2] <= a2) | (q[3] <= a2);
+                if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = j0 + u;
+                        if (q[u] <= a2 && j != i) {
+                            if (j > i) row_active<T, ND>(d[u], q[u], ia2, tie_f, R, rp2, mx2, true);
+                            else row_active<T, ND>(d[u], q[u], ia2, tie_b, R, rp2, mx2, false);
+                        }
+                    }
+                }
+            }
+            // obstacles
+            for (int m0 = 0; m0 < opad; m0 += 4) {
+                T d[4][ND], q[4], lim[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int m = m0 + u;
+                    const Vec<T, 4> r0 = reinterpret_cast<const Vec<T, 4> *>(ob)[2 * m];
+                    if (I.dyn && m < nobs) {
+                        const T *c = obs_g + ((int64_t)m * H + k) * ND;
+#pragma unroll
+                        for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - c[ax];
+                    } else {
+#pragma unroll
+                        for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - r0.v[ax];
+                    }
+                    q[u] = d[u][0] * d[u][0] + d[u][1] * d[u][1];
+                    if (ND == 3) q[u] += ob[8 * m + 4] * d[u][ND - 1] * d[u][ND - 1];
+                    lim[u] = r0.v[3];
+                }
+                const bool any = (q[0] <= lim[0]) | (q[1] <= lim[1]) | (q[2] <= lim[2]) | (q[3] <= lim[3]);
+                if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (q[u] <= lim[u]) {
+                            const int m = m0 + u;
+                            T tie[ND];
+#pragma unroll
+                            for (int ax = 0; ax < ND; ++ax) tie[ax] = T(0);
+                            if (ND == 2) tie[0] = -ob[8 * m + 6]; else tie[ND - 1] = -ob[8 * m + 7];
+                            row_active<T, ND>(d[u], q[u], ob[8 * m + 5], tie, R, rp2, mx2, true);
+                        }
+                }
+            }
+            if (!valid) continue;
+            // workspace box (G rows: upper side p <= p_max, lower side -p <= -p_min)
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) {
+                const T u = pi.v[ax] - I.pmax[ax];
+                const T l = I.pmin[ax] - pi.v[ax];
+                if (u > T(0)) {
+                    R[ax] += u;
+                    rp2 += u * u;
+                    mx2 = fmax(mx2, u * u);
+                }
+                if (l > T(0)) {
+                    R[ax] -= l;
+                    rp2 += l * l;
+                    mx2 = fmax(mx2, l * l);
+                }
+            }
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) Rb[(ax * n + i) * hcc + kl] = R[ax];
+        }
+    }
+
+    // Adjoint of rows(): with R* (vector layout Rs[i][kl]) the adjoint of R, writes
+    // p* = sum over active rows of J' (R*_i - R*_j) (pairs), J' R*_i (obstacles) and the
+    // box mask times R*_i, to Rb[ax][i][kl].  seed_w > 0 instead differentiates
+    // seed_w / 2 * ||r_p||^2: y = seed_w r_1 on every active row and seed_w (u+ - l+) on the box.
+    __device__ void rows_adjoint(int k0, int hcc, const VP *Rs, T seed_w)
+    {
+        const bool seed = seed_w != T(0);
+        const int items = n * hcc;
+        const T a2 = I.a * I.a, ia2 = I.ia2, ib2 = I.ib2, kz = (I.a * I.a) * I.ib2;
+        for (int e0 = 0; e0 < items; e0 += nt) {
+            const int e = e0 + tid;
+            const bool valid = e < items;
+            if (__all_sync(0xffffffffu, !valid)) continue;
+            const int ee = valid ? e : 0;
+            const int i = ee / hcc, kl = ee - i * hcc, k = k0 + kl;
+            VP pi = P[i * hcc + kl];
+            if (!valid)
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax) pi.v[ax] = -Far<T>::v;
+            T Ri[ND], ps[ND];
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) {
+                Ri[ax] = seed ? T(0) : Rs[i * hcc + kl].v[ax];
+                ps[ax] = T(0);
+            }
+            for (int j0 = 0; j0 < npad; j0 += 4) {
+                T d[4][ND], q[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const VP pj = P[(j0 + u) * hcc + kl];
+#pragma unroll
+                    for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - pj.v[ax];
+                    q[u] = qdist<T, ND>(d[u], kz);
+                }
+                const bool any = (q[0] <= a2) | (q[1] <= a2) | (q[2] <= a2) | (q[3] <= a2);
+                if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = j0 + u;
+                        if (q[u] <= a2 && j != i) {
+                            T y[ND];
+#pragma unroll
+                            for (int ax = 0; ax < ND; ++ax) y[ax] = seed ? T(0) : Ri[ax] - Rs[j * hcc + kl].v[ax];
+                            row_adjoint<T, ND>(d[u], q[u], ia2, ib2, y, seed_w, seed, ps);
+                        }
+                    }
+                }
+            }
+            for (int m0 = 0; m0 < opad; m0 += 4) {
+                T d[4][ND], q[4], lim[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int m = m0 + u;
+                    const Vec<T, 4> r0 = reinterpret_cast<const Vec<T, 4> *>(ob)[2 * m];
+                    if (I.dyn && m < nobs) {
+                        const T *c = obs_g + ((int64_t)m * H + k) * ND;
+#pragma unroll
+                        for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - c[ax];
+                    } else {
+#pragma unroll
+                        for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - r0.v[ax];
+                    }
+                    q[u] = d[u][0] * d[u][0] + d[u][1] * d[u][1];
+                    if (ND == 3) q[u] += ob[8 * m + 4] * d[u][ND - 1] * d[u][ND - 1];
+                    lim[u] = r0.v[3];
+                }
+                const bool any = (q[0] <= lim[0]) | (q[1] <= lim[1]) | (q[2] <= lim[2]) | (q[3] <= lim[3]);
+                if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (q[u] <= lim[u]) {
+                            const int m = m0 + u;
+                            const T iao = ob[8 * m + 5], ibo = ob[8 * m + 4] * ob[8 * m + 5];
+                            row_adjoint<T, ND>(d[u], q[u], iao, ibo, Ri, seed_w, seed, ps);
+                        }
+                }
+            }
+            if (!valid) continue;
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) {
+                const T u = pi.v[ax] - I.pmax[ax];
+                const T l = I.pmin[ax] - pi.v[ax];
+                if (seed) {
+                    if (u > T(0)) ps[ax] += seed_w * u;
+                    if (l > T(0)) ps[ax] -= seed_w * l;
+                } else {
+                    if (u > T(0)) ps[ax] += Ri[ax];
+                    if (l > T(0)) ps[ax] += Ri[ax];
+                }
+            }
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) Rb[(ax * n + i) * hcc + kl] = ps[ax];
+        }
+    }
+
+    // dst = P_eta src (+ P_b db when corr_b); dst[e] is valid for the elements e this
+    // thread owns (e = tid + j nt).  src and dst must differ from each other and from dl.
+    __device__ void project(cg::cluster_group &cl, const T *src, T *dst, bool corr_b)
+    {
+        if (dense) {
+            // rows [r_lo, r_hi) of P_eta src: 8 lanes per row, interleaved columns; the trip
+            // count is the same for every thread, so whole warps take part in the shuffles
+            const int seg = 8, rows = r_hi - r_lo;
+            for (int t0 = 0; t0 < rows * seg; t0 += nt) {
+                const int t = t0 + tid;
+                const bool act = t < rows * seg;
+                const int r = r_lo + t / seg, s = t % seg;
+                T acc[ND];
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax) acc[ax] = T(0);
+                if (act) {
+                    const T *pr = Prow + (int64_t)r * N;
+                    for (int c = s; c < N; c += seg) {
+                        const T pv = pr[c];
+#pragma unroll
+                        for (int ax = 0; ax < ND; ++ax) acc[ax] += pv * src[ax * N + c];
+                    }
+                    if (corr_b)
+                        for (int q = s; q < 2 * n; q += seg) {
+                            const T pbq = Pbg[(int64_t)r * 2 * n + q];
+#pragma unroll
+                            for (int ax = 0; ax < ND; ++ax) acc[ax] += pbq * db[(ax * n + (q >> 1)) * 2 + (q & 1)];
+                        }
+                }
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax) {
+                    T a = acc[ax];
+                    a += __shfl_xor_sync(0xffffffffu, a, 4);
+                    a += __shfl_xor_sync(0xffffffffu, a, 2);
+                    a += __shfl_xor_sync(0xffffffffu, a, 1);
+                    if (act && s == 0) dl[ax * N + r] = a;
+                }
+            }
+            cl.sync();
+            for (int e = tid; e < NN; e += nt) {
+                const int row = e - (e / N) * N;
+                dst[e] = cl.map_shared_rank(dl, row / L)[e];
+            }
+        } else {
+            // Kronecker form, per axis with robot mean m of src:
+            //   dst_i = P_dev src_i + (P_mean - P_dev) m   (+ the same with B for b - A xi_bar)
+            const int lane = tid & 31, nw = nt >> 5;
+            for (int pq = tid >> 5; pq < ND * nxi; pq += nw) {
+                const int ax = pq / nxi, c = pq - ax * nxi;
+                T s = T(0);
+                for (int i = lane; i < n; i += 32) s += src[(ax * n + i) * nxi + c];
+#pragma unroll
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) mv[pq] = s * invn;
+            }
+            __syncthreads();
+            for (int e = tid; e < ND * nxi; e += nt) {
+                const int ax = e / nxi, u = e - ax * nxi;
+                T s = T(0);
+                for (int c = 0; c < nxi; ++c) s += Pdif[u * nxi + c] * mv[ax * nxi + c];
+                if (corr_b) s += Bdif[u * 2] * mb[ax * 2] + Bdif[u * 2 + 1] * mb[ax * 2 + 1];
+                pm[e] = s;
+            }
+            __syncthreads();
+            for (int e = tid; e < NN; e += nt) {
+                const int r = e / nxi, u = e - r * nxi, ax = r / n;
+                const T *vr = src + r * nxi;
+                const T *pu = Pdev + u * nxi;
+                T s0 = pm[ax * nxi + u], s1 = T(0);
+                int c = 0;
+                for (; c + 1 < nxi; c += 2) {
+                    s0 += pu[c] * vr[c];
+                    s1 += pu[c + 1] * vr[c + 1];
+                }
+                if (c < nxi) s0 += pu[c] * vr[c];
+                if (corr_b) s1 += Bdev[u * 2] * db[r * 2] + Bdev[u * 2 + 1] * db[r * 2 + 1];
+                dst[e] = s0 + s1;
+            }
+        }
+    }
+
+    // First half of an iteration of T: rows of this CTA's timesteps, partial g into gme.
+    __device__ void rows_and_g(T *gme, T &rp2, T &mx2)
+    {
+        for (int e = tid; e < NN; e += nt) gme[e] = T(0);
+        for (int k0 = k_lo; k0 < k_hi; k0 += hc) {
+            const int hcc = min(hc, k_hi - k0);
+            __syncthreads();
+            positions(k0, hcc, xb);
+            __syncthreads();
+            rows(k0, hcc, rp2, mx2);
+            __syncthreads();
+            wt_acc(k0, hcc, Rb, gme);
+        }
+    }
+
+    // Second half, after the cluster barrier: g = sum over the cluster of gme (fixed order,
+    // the same bits in every CTA), lambda step, correction projection, xi_bar update.
+    // Returns this thread's share of ||z^{l+1} - z^l||^2.
+    __device__ T update(cg::cluster_group &cl, const T *gme, bool corr_b)
+    {
+        T fp = T(0);
+        for (int e = tid; e < NN; e += nt) {
+            T gg = T(0);
+            for (int q = 0; q < C; ++q) gg += cl.map_shared_rank(gme, q)[e];
+            const T ln = lam[e] - rho * gg;
+            const T dlam = ln - lam[e];
+            fp += dlam * dlam;
+            v[e] = xc[e] - xb[e] + ln - rho * gg;
+            lam[e] = ln;
+        }
+        __syncthreads();
+        project(cl, v, dd, corr_b);
+        for (int e = tid; e < NN; e += nt) {
+            const int r = e / nxi, c = e - r * nxi;
+            T xn = xb[e] + dd[e];
+            if (c == 0) xn = bd[r * 2];                  // A xi_bar = b holds exactly
+            else if (c == nxi - 1) xn = bd[r * 2 + 1];
+            const T dx = xn - xb[e];
+            fp += dx * dx;
+            xb[e] = xn;
+        }
+        return fp;
+    }
+};
+
+// Launches n_inst clusters of csize CTAs of `kernel` with `smem` bytes of dynamic shared memory.
+template <typename K, typename Arg>
+inline cudaError_t launch_cluster(K kernel, const Arg &a, int n_inst, int csize, int threads, size_t smem,
+                                  cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_inst * csize), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+}  // namespace sf
