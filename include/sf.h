@@ -88,7 +88,12 @@ typedef struct sf_desc {
     double rho;         /* augmented-Lagrangian penalty (eq. aug_lag), > 0                 */
     int32_t precision;  /* SF_FP64 .. SF_BF16                                              */
     int32_t proj;       /* SF_PROJ_DENSE or SF_PROJ_STRUCTURED                             */
-    int32_t n_refine;   /* extra refinement passes of the reduced-precision projection      */
+    int32_t n_refine;   /* refinement passes of the tensor-core projection (SF_TF32,
+                           SF_BF16X3, SF_BF16; ignored otherwise; 0 .. 8): each pass adds P~(v - H d)
+                           to the projected d, the residual taken in FP32 through the
+                           Kronecker-structured Hessian of eq. batch_comp.  With P~ the
+                           rounded projector the error shrinks by ||I - P~H|| per pass; one
+                           pass brings SF_BF16X3 to FP32 accuracy, two bring SF_TF32       */
     int32_t max_iters;  /* upper bound on `iters` of sf_solve (sizes checkpoint storage)    */
     int32_t ckpt_every; /* > 0: sf_solve keeps (xi_bar, lambda) every ckpt_every iterations
                            so sf_solve_backward can run; 0: no backward                    */

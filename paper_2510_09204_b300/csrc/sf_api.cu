@@ -59,6 +59,8 @@ struct sf_handle {
     DevBuf Wt, Pt, Pbt, St;            // in T (aliases of the FP64 pools when T = double)
     DevBuf ck_x, ck_l;
     DevBuf seg;                        // adjoint: recomputed iterates of a checkpoint segment
+    DevBuf tcA, tcoff;                 // tensor-core chunks of P_eta for the current cluster size
+    int tc_mode = 0, tc_c = 0;
     int n_slots = 0;
     int64_t xi_total = 0;
     // launch configuration
@@ -96,11 +98,11 @@ static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SF_OK : (e == 
         if (e_ != cudaSuccess) return cuda_status(e_); \
     } while (0)
 
-static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
-                     int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out)
+                     int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode)
 {
+    if (proj != SF_PROJ_DENSE) tc_mode = 0;
     Plan p;
     p.threads = threads;
     int minH = H[0];
@@ -113,8 +115,9 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     for (int i = 0; i < n_inst; ++i) {
         const int own = (H[i] + C - 1) / C;
         int hc = own;
+        if (tc_mode && tc_ntiles(n[i] * nxi, C) > 8) return SF_EUNSUPPORTED;   // 8 x 128 rows per CTA at most
         auto bytes = [&](int h, int rows) {
-            return (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz).total * esz;
+            return (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz, tc_mode).total * esz;
         };
         while (hc > 1 && bytes(hc, 0) > (size_t)optin) --hc;
         if (bytes(hc, 0) > (size_t)optin) return SF_EUNSUPPORTED;
@@ -125,7 +128,7 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
         if (r1 > (size_t)optin) return SF_EUNSUPPORTED;
         need_r = std::max(need_r, (size_t)residual_doubles(nd, nxi, H[i], n[i], nobs[i], own) * sizeof(double));
     }
-    if (proj == SF_PROJ_DENSE) {
+    if (proj == SF_PROJ_DENSE && !tc_mode) {
         size_t with_p = 0;
         for (int i = 0; i < n_inst; ++i)
             with_p = std::max(with_p, (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], maxL, esz).total * esz);
@@ -138,7 +141,8 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     p.smem_res = std::min((size_t)optin, need_r);
     size_t need_b = 0;
     for (int i = 0; i < n_inst; ++i)
-        need_b = std::max(need_b, (size_t)backward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], p.p_rows, esz).total * esz);
+        need_b = std::max(need_b,
+                          (size_t)backward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], p.p_rows, esz, tc_mode).total * esz);
     p.smem_bwd = need_b <= (size_t)optin ? need_b : 0;
     *out = p;
     return SF_OK;
@@ -151,7 +155,7 @@ static int validate(const sf_desc *d)
     if (!(d->rho > 0.0) || !isfinite(d->rho) || d->n_inst < 1) return SF_EINVAL;
     if (d->precision < SF_FP64 || d->precision > SF_BF16) return SF_EINVAL;
     if (d->proj != SF_PROJ_DENSE && d->proj != SF_PROJ_STRUCTURED) return SF_EINVAL;
-    if (d->max_iters < 0 || d->ckpt_every < 0 || d->n_refine < 0 || !(d->tol >= 0.0)) return SF_EINVAL;
+    if (d->max_iters < 0 || d->ckpt_every < 0 || d->n_refine < 0 || d->n_refine > 8 || !(d->tol >= 0.0)) return SF_EINVAL;
     for (int i = 0; i < d->n_inst; ++i) {
         const sf_shape &s = d->shapes[i];
         if (s.n < 1 || s.n > 256 || s.n_obs < 0 || s.n_obs > 4096 || s.H < 2 || s.H > 4096) return SF_EINVAL;
@@ -205,7 +209,7 @@ static void destroy_all(sf_handle *h)
             h->ev[k] = nullptr;
         }
     DevBuf *bufs[] = {&h->inst_dev, &h->shapes_dev, &h->order_dev, &h->status_dev, &h->W64, &h->P64,
-                      &h->Pb64, &h->S64, &h->ck_x, &h->ck_l, &h->seg};
+                      &h->Pb64, &h->S64, &h->ck_x, &h->ck_l, &h->seg, &h->tcA, &h->tcoff};
     if (h->esz == 4) {
         h->Wt.release();
         h->Pt.release();
@@ -213,6 +217,29 @@ static void destroy_all(sf_handle *h)
         h->St.release();
     }
     for (DevBuf *b : bufs) b->release();
+}
+
+// (Re)builds the tensor-core chunk pool for the plan's cluster size.
+static int build_tc_pool(sf_handle *h, cudaStream_t st)
+{
+    if (!h->tc_mode || h->tc_c == h->plan.csize) return SF_OK;
+    const int C = h->plan.csize;
+    std::vector<int64_t> off(h->n_shapes);
+    int64_t tot = 0;
+    for (int i = 0; i < h->n_shapes; ++i) {
+        off[i] = tot;
+        tot += tc_pool_bytes(h->tc_mode, h->shapes_h[i].N, C);
+    }
+    SF_TRY(cudaStreamSynchronize(st));
+    h->tcA.release();
+    if (!h->tcoff.p) SF_TRY(h->tcoff.alloc(sizeof(int64_t) * h->n_shapes));
+    SF_TRY(h->tcA.alloc((size_t)tot));
+    SF_TRY(cudaMemcpy(h->tcoff.p, off.data(), sizeof(int64_t) * h->n_shapes, cudaMemcpyHostToDevice));
+    SF_TRY(arrange_tc((const Shape *)h->shapes_dev.p, h->n_shapes, h->shapes_h.data(), (const double *)h->P64.p,
+                      (const int64_t *)h->tcoff.p, off.data(), h->tc_mode, C, (unsigned char *)h->tcA.p, st));
+    SF_TRY(cudaStreamSynchronize(st));
+    h->tc_c = C;
+    return SF_OK;
 }
 
 extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
@@ -227,6 +254,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
     h->shp.assign(desc->shapes, desc->shapes + desc->n_inst);
     h->d.shapes = nullptr;
     h->esz = desc->precision == SF_FP64 ? 8 : 4;
+    h->tc_mode = desc->proj == SF_PROJ_DENSE ? tc_mode_of(desc->precision) : 0;
     const int nd = desc->n_d, nxi = desc->n_xi, B = desc->n_inst;
     cudaStream_t st = (cudaStream_t)desc->stream;
 
@@ -294,9 +322,9 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
             }
         }
         int prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                               h->smem_optin, c0, t0, &h->plan, h->hc.data());
+                               h->smem_optin, c0, t0, &h->plan, h->hc.data(), h->tc_mode);
         if (prc && c0) prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                                          h->smem_optin, 0, kDefaultThreads, &h->plan, h->hc.data());
+                                          h->smem_optin, 0, kDefaultThreads, &h->plan, h->hc.data(), h->tc_mode);
         if (prc) { destroy_all(h); delete h; return prc; }
     }
 
@@ -376,6 +404,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
         convert_pool((double *)h->S64.p, (float *)h->St.p, oS, st);
         if ((r = cuda_status(cudaStreamSynchronize(st)))) { destroy_all(h); delete h; return r; }
     }
+    if ((r = build_tc_pool(h, st))) { destroy_all(h); delete h; return r; }
     // checkpoints
     if (desc->ckpt_every > 0) {
         h->n_slots = desc->max_iters / desc->ckpt_every + 2;   // every c-th iterate, then the final one
@@ -436,6 +465,10 @@ static FwdArgs<T> fwd_args(const sf_handle *h, const void *bnd, const void *obs,
     a.obs = (const T *)obs;
     a.oab = (const T *)oab;
     a.status = (int32_t *)h->status_dev.p;
+    a.tc_mode = h->tc_mode;
+    a.n_refine = h->tc_mode ? h->d.n_refine : 0;
+    a.tcA = (const unsigned char *)h->tcA.p;
+    a.tc_off = (const int64_t *)h->tcoff.p;
     if (h->d.ckpt_every > 0) {
         a.ck_x = (T *)h->ck_x.p;
         a.ck_l = (T *)h->ck_l.p;
@@ -571,11 +604,12 @@ extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
     }
     Plan p;
     int rc = plan_forward(h->d.n_d, h->d.n_xi, h->esz, h->d.proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                          h->smem_optin, cluster, threads ? threads : kDefaultThreads, &p, hc.data());
+                          h->smem_optin, cluster, threads ? threads : kDefaultThreads, &p, hc.data(), h->tc_mode);
     if (rc) return rc;
     SF_TRY(cudaDeviceSynchronize());
     h->plan = p;
     h->hc = hc;
+    if ((rc = build_tc_pool(h, (cudaStream_t)0))) return rc;
     return h->esz == 8 ? upload_instances<double>(h) : upload_instances<float>(h);
 }
 

@@ -23,7 +23,7 @@
 
 namespace sf {
 
-template <typename T, int ND, int MAXT>
+template <typename T, int ND, int MAXT, bool TC>
 __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
 {
     using VP = Vec<T, NDP<ND>::v>;
@@ -34,10 +34,11 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     const int w = blockIdx.x / C;
     const int ii = A.order ? A.order[w] : w;
     const Inst<T> I0 = A.inst[ii];
-    const BwdCarve cv = backward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T));
-    Cta<T, ND> X;
+    const BwdCarve cv = backward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode);
+    Cta<T, ND, TC> X;
     X.init(A, smem_raw, cv.f, ii, cr, C);
     X.load_constants(A, A.p_rows);
+    X.tc_setup(A, smem_raw);
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *xs = sm + cv.xs, *ls = sm + cv.ls, *cs = sm + cv.cs;
     VP *Rs = reinterpret_cast<VP *>(sm + cv.Rs);
@@ -151,6 +152,8 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             if (B.gl0) B.gl0[off + e] = ls[e];
         }
     }
+    if (tid == 0 && X.tc_timed_out()) A.status[ii] = SF_ETIMEOUT;
+    X.tc_teardown();
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
@@ -161,12 +164,22 @@ static cudaError_t launch_backward_t(const BwdArgs<T> &a, int threads, size_t sm
     if (f.n_inst < 1 || f.csize < 1 || f.csize > kMaxCluster) return cudaErrorInvalidValue;
     if (threads > max_threads((int)sizeof(T))) return cudaErrorInvalidValue;
     constexpr int big = sizeof(T) == 8 ? 512 : 1024;
-    if (threads > 512) {
-        if (f.nd == 2) return launch_cluster(k_backward<T, 2, big>, a, f.n_inst, f.csize, threads, smem, s);
-        return launch_cluster(k_backward<T, 3, big>, a, f.n_inst, f.csize, threads, smem, s);
+    constexpr bool tcok = sizeof(T) == 4;
+    const int ni = f.n_inst, cs = f.csize;
+    if (f.tc_mode && tcok) {
+        if (threads > 512) {
+            if (f.nd == 2) return launch_cluster(k_backward<T, 2, big, tcok>, a, ni, cs, threads, smem, s);
+            return launch_cluster(k_backward<T, 3, big, tcok>, a, ni, cs, threads, smem, s);
+        }
+        if (f.nd == 2) return launch_cluster(k_backward<T, 2, 512, tcok>, a, ni, cs, threads, smem, s);
+        return launch_cluster(k_backward<T, 3, 512, tcok>, a, ni, cs, threads, smem, s);
     }
-    if (f.nd == 2) return launch_cluster(k_backward<T, 2, 512>, a, f.n_inst, f.csize, threads, smem, s);
-    return launch_cluster(k_backward<T, 3, 512>, a, f.n_inst, f.csize, threads, smem, s);
+    if (threads > 512) {
+        if (f.nd == 2) return launch_cluster(k_backward<T, 2, big, false>, a, ni, cs, threads, smem, s);
+        return launch_cluster(k_backward<T, 3, big, false>, a, ni, cs, threads, smem, s);
+    }
+    if (f.nd == 2) return launch_cluster(k_backward<T, 2, 512, false>, a, ni, cs, threads, smem, s);
+    return launch_cluster(k_backward<T, 3, 512, false>, a, ni, cs, threads, smem, s);
 }
 
 cudaError_t launch_backward(const BwdArgs<double> &a, int threads, size_t smem, cudaStream_t s)

@@ -11,9 +11,13 @@
 //   H = L L' (Cholesky), Hinv = L^-T L^-1, Y = Hinv A', S = A Y (Schur
 //   complement), P_b = Y S^-1, P_eta = Hinv - P_b Y'.
 // so that argmin = P_eta eta + P_b b.  Every step runs in FP64 on the GPU.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "sf_internal.cuh"
+#include "sf_tc.cuh"
+
+#include <algorithm>
 
 namespace sf {
 
@@ -248,6 +252,62 @@ cudaError_t convert_pool(const double *src, float *dst, int64_t n, cudaStream_t 
     int grid = (int)((n + 255) / 256);
     if (grid > 4096) grid = 4096;
     k_convert<<<grid, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+int64_t tc_pool_bytes(int mode, int N, int C)
+{
+    if (!mode) return 0;
+    return (int64_t)C * tc_ntiles(N, C) * tc_nk(mode, N) * tc_na(mode) * kTcChunkBytes;
+}
+
+// One element of the tensor-core chunk layout per thread: CTA rank cr takes rows
+// [cr L, cr L + L) of P_eta (L = ceil(N / C)) in 128-row tiles; each tile is split into
+// K chunks of 128 bytes per row, stored as core matrices [16 row groups][8 K groups][8][16 B].
+__global__ void k_arrange_tc(const Shape *sh, const double *P64, const int64_t *tc_off, int mode, int C,
+                             unsigned char *out)
+{
+    const Shape S = sh[blockIdx.y];
+    const int N = S.N, L = (N + C - 1) / C, nT = tc_ntiles(N, C), nK = tc_nk(mode, N), na = tc_na(mode);
+    const int es = tc_es(mode), KC = tc_kc(mode);
+    const int64_t tot = (int64_t)C * nT * nK * 128 * KC;
+    unsigned char *base = out + tc_off[blockIdx.y];
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rest = idx;
+        const int kk = (int)(rest % KC); rest /= KC;
+        const int i = (int)(rest % 128); rest /= 128;
+        const int kc = (int)(rest % nK); rest /= nK;
+        const int t = (int)(rest % nT);
+        const int cr = (int)(rest / nT);
+        const int r = cr * L + 128 * t + i, c = kc * KC + kk, rhi = min(N, (cr + 1) * L);
+        const double val = (r < rhi && c < N) ? P64[S.off_P + (int64_t)r * N + c] : 0.0;
+        unsigned char *blk = base + ((((int64_t)cr * nT + t) * nK + kc) * na) * kTcChunkBytes;
+        const int within = ((i >> 3) * 8 + ((kk * es) >> 4)) * 128 + (i & 7) * 16 + ((kk * es) & 15);
+        if (mode == 1) {
+            *reinterpret_cast<float *>(blk + within) = tc::to_tf32((float)val);
+        } else {
+            const __nv_bfloat16 hi = __float2bfloat16_rn((float)val);
+            *reinterpret_cast<__nv_bfloat16 *>(blk + within) = hi;
+            if (na == 2)
+                *reinterpret_cast<__nv_bfloat16 *>(blk + kTcChunkBytes + within) =
+                    __float2bfloat16_rn((float)(val - (double)__bfloat162float(hi)));
+        }
+    }
+}
+
+cudaError_t arrange_tc(const Shape *shapes_dev, int n_shapes, const Shape *shapes_host, const double *P64,
+                       const int64_t *tc_off_dev, const int64_t *tc_off_host, int mode, int C, unsigned char *out,
+                       cudaStream_t s)
+{
+    (void)tc_off_host;
+    if (!mode || n_shapes < 1) return cudaSuccess;
+    int64_t most = 0;
+    for (int i = 0; i < n_shapes; ++i) {
+        const int N = shapes_host[i].N;
+        most = std::max<int64_t>(most, (int64_t)C * tc_ntiles(N, C) * tc_nk(mode, N) * 128 * tc_kc(mode));
+    }
+    const int64_t blocks = std::min<int64_t>(4096, (most + 255) / 256);
+    k_arrange_tc<<<dim3((unsigned)blocks, n_shapes), 256, 0, s>>>(shapes_dev, P64, tc_off_dev, mode, C, out);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@
 
 namespace sf {
 
-template <typename T, int ND, int MAXT>
+template <typename T, int ND, int MAXT, bool TC>
 __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -36,10 +36,11 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
     const int w = blockIdx.x / C;
     const int ii = A.order ? A.order[w] : w;
     const Inst<T> I0 = A.inst[ii];
-    const FwdCarve cv = forward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T));
-    Cta<T, ND> X;
+    const FwdCarve cv = forward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode);
+    Cta<T, ND, TC> X;
     X.init(A, smem_raw, cv, ii, cr, C);
     X.load_constants(A, A.p_rows);
+    X.tc_setup(A, smem_raw);
     const int tid = X.tid, nt = X.nt, NN = X.NN;
     const int64_t off = X.I.off_xi;
     const T *x0g = A.x0 ? A.x0 + off : A.xc + off;
@@ -117,6 +118,8 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
             if (bad) A.status[ii] = SF_ENONFINITE;
         }
     }
+    if (tid == 0 && X.tc_timed_out()) A.status[ii] = SF_ETIMEOUT;
+    X.tc_teardown();
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
@@ -249,12 +252,22 @@ static cudaError_t launch_forward_t(const FwdArgs<T> &a, int threads, size_t sme
     if (a.n_inst < 1 || a.csize < 1 || a.csize > kMaxCluster) return cudaErrorInvalidValue;
     if (threads > max_threads((int)sizeof(T))) return cudaErrorInvalidValue;
     constexpr int big = sizeof(T) == 8 ? 512 : 1024;
-    if (threads > 512) {
-        if (a.nd == 2) return launch_cluster(k_forward<T, 2, big>, a, a.n_inst, a.csize, threads, smem, s);
-        return launch_cluster(k_forward<T, 3, big>, a, a.n_inst, a.csize, threads, smem, s);
+    constexpr bool tcok = sizeof(T) == 4;
+    const int ni = a.n_inst, cs = a.csize;
+    if (a.tc_mode && tcok) {
+        if (threads > 512) {
+            if (a.nd == 2) return launch_cluster(k_forward<T, 2, big, tcok>, a, ni, cs, threads, smem, s);
+            return launch_cluster(k_forward<T, 3, big, tcok>, a, ni, cs, threads, smem, s);
+        }
+        if (a.nd == 2) return launch_cluster(k_forward<T, 2, 512, tcok>, a, ni, cs, threads, smem, s);
+        return launch_cluster(k_forward<T, 3, 512, tcok>, a, ni, cs, threads, smem, s);
     }
-    if (a.nd == 2) return launch_cluster(k_forward<T, 2, 512>, a, a.n_inst, a.csize, threads, smem, s);
-    return launch_cluster(k_forward<T, 3, 512>, a, a.n_inst, a.csize, threads, smem, s);
+    if (threads > 512) {
+        if (a.nd == 2) return launch_cluster(k_forward<T, 2, big, false>, a, ni, cs, threads, smem, s);
+        return launch_cluster(k_forward<T, 3, big, false>, a, ni, cs, threads, smem, s);
+    }
+    if (a.nd == 2) return launch_cluster(k_forward<T, 2, 512, false>, a, ni, cs, threads, smem, s);
+    return launch_cluster(k_forward<T, 3, 512, false>, a, ni, cs, threads, smem, s);
 }
 
 cudaError_t launch_forward(const FwdArgs<double> &a, int threads, size_t smem, cudaStream_t s)

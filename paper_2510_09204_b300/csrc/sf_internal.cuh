@@ -37,10 +37,34 @@ struct Shape {
     int64_t off_S;    // structured form: P_dev, P_mean, B_dev, B_mean (n_xi x n_xi, n_xi x 2 each)
 };
 
+// ---- tensor-core projection (dense P_eta on tcgen05) -----------------------------
+// Modes: 0 none (SIMT), 1 TF32, 2 BF16, 3 BF16 x3 (hi*hi + hi*lo + lo*hi).
+__host__ __device__ inline int tc_mode_of(int precision)
+{
+    return precision == SF_TF32 ? 1 : precision == SF_BF16 ? 2 : precision == SF_BF16X3 ? 3 : 0;
+}
+__host__ __device__ inline int tc_es(int mode) { return mode == 1 ? 4 : 2; }          // operand bytes
+__host__ __device__ inline int tc_kc(int mode) { return 128 / tc_es(mode); }          // K per 128-byte chunk row
+__host__ __device__ inline int tc_nk(int mode, int N) { return (N + tc_kc(mode) - 1) / tc_kc(mode); }
+__host__ __device__ inline int tc_na(int mode) { return mode == 3 ? 2 : 1; }          // A (and B) parts
+__host__ __device__ inline int tc_ntiles(int N, int C) { return (((N + C - 1) / C) + 127) / 128; }
+constexpr int kTcChunkBytes = 128 * 128;   // one 128-row x 128-byte A chunk
+
+// Bytes at the front of shared memory for the tensor-core path: two A ring stages, the B
+// operand, slack after B (so any misread of a descriptor stays inside the allocation),
+// and the mbarriers / tensor-memory address.
+__host__ __device__ inline int64_t tc_smem_bytes(int mode, int N)
+{
+    if (!mode) return 0;
+    const int64_t kpad = (int64_t)tc_nk(mode, N) * tc_kc(mode);
+    const int64_t b = 16 * kpad * tc_es(mode);
+    return 2LL * kTcChunkBytes * tc_na(mode) + b * tc_na(mode) + b + 1024 + 128;
+}
+
 // Shared-memory carve of the forward kernel, in elements of T.  Every region starts on a
 // 32-byte boundary.  Host and kernel both call forward_carve, so they cannot disagree.
 struct FwdCarve {
-    int64_t W, xb, lam, xc, v, gp, dl, dd, pb, Rb, ob, bd, db, sx, red, Ps, total;
+    int64_t W, xb, lam, xc, v, gp, dl, dd, rr, wtw, pb, Rb, ob, bd, db, sx, red, Ps, total;
 };
 
 __host__ __device__ inline int64_t carve_round(int64_t cnt, int esz)
@@ -51,11 +75,12 @@ __host__ __device__ inline int64_t carve_round(int64_t cnt, int esz)
 
 // nd, nxi: dimension and coefficients; H, n, nobs: instance sizes; hc: timesteps per chunk;
 // p_rows: rows of P_eta staged in shared memory (0: read from global memory).
-__host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz)
+__host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
+                                                  int tc_mode = 0)
 {
     const int64_t N = (int64_t)n * nxi, NN = nd * N, ndp = nd == 2 ? 2 : 4;
     FwdCarve c;
-    int64_t o = 0;
+    int64_t o = (tc_smem_bytes(tc_mode, (int)N) + 127) / 128 * 128 / esz;   // tensor-core buffers first
     c.W = o;   o += carve_round((int64_t)H * nxi, esz);
     c.xb = o;  o += carve_round(NN, esz);
     c.lam = o; o += carve_round(NN, esz);
@@ -64,6 +89,8 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n,
     c.gp = o;  o += 2 * carve_round(NN + 4, esz);                 // partial g + stats, two buffers
     c.dl = o;  o += carve_round(NN, esz);                         // projection rows of this CTA
     c.dd = o;  o += carve_round(NN, esz);                         // projection output
+    c.rr = o;  o += carve_round(tc_mode ? NN : 0, esz);           // refinement residual (tensor cores)
+    c.wtw = o; o += carve_round(tc_mode ? (int64_t)nxi * nxi + nd * nxi : 0, esz);   // W'W and robot sums
     const int64_t npad = (n + 3) / 4 * 4, opad = (nobs + 3) / 4 * 4;
     c.pb = o;  o += carve_round(npad * hc * ndp, esz);            // positions [i][k] as vectors (+ far dummies)
     c.Rb = o;  o += carve_round((int64_t)nd * n * hc, esz);       // row sums R [ax][i][k]
@@ -84,10 +111,11 @@ struct BwdCarve {
     int64_t xs, ls, cs, Rs, total;
 };
 
-__host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz)
+__host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
+                                                   int tc_mode = 0)
 {
     BwdCarve b;
-    b.f = forward_carve(nd, nxi, H, n, nobs, hc, p_rows, esz);
+    b.f = forward_carve(nd, nxi, H, n, nobs, hc, p_rows, esz, tc_mode);
     const int64_t NN = (int64_t)nd * n * nxi, npad = (n + 3) / 4 * 4, ndp = nd == 2 ? 2 : 4;
     int64_t o = b.f.total;
     b.xs = o; o += carve_round(NN, esz);
@@ -103,6 +131,10 @@ struct FwdArgs {
     int nd, nxi, iters, n_inst;
     int csize;        // CTAs per instance (thread-block cluster), 1..kMaxCluster
     int p_rows;       // rows of P_eta per CTA staged in shared memory (dense; 0 = global)
+    int tc_mode;      // tensor-core projection: 0 none, 1 TF32, 2 BF16, 3 BF16 x3
+    int n_refine;     // refinement passes of the tensor-core projection
+    const unsigned char *tcA;   // arranged P_eta chunks for the current cluster size
+    const int64_t *tc_off;      // byte offset of each shape's chunks in tcA
     int proj;         // SF_PROJ_DENSE / SF_PROJ_STRUCTURED
     T rho;
     double tol;
@@ -165,7 +197,14 @@ struct Plan {
 // hc_out[i] and the shared-memory sizes.  Returns SF_OK or SF_EUNSUPPORTED when an
 // instance cannot fit in `optin` bytes of shared memory.
 int plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
-                 int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out);
+                 int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode = 0);
+
+// Arranges every shape's P_eta (FP64 pool) into the tensor-core chunk layout for cluster
+// size C: per shape [C][tiles][K chunks][128 x 128 bytes] (x 2 for the BF16 x3 low part).
+cudaError_t arrange_tc(const Shape *shapes_dev, int n_shapes, const Shape *shapes_host, const double *P64,
+                       const int64_t *tc_off_dev, const int64_t *tc_off_host, int mode, int C, unsigned char *out,
+                       cudaStream_t s);
+int64_t tc_pool_bytes(int mode, int N, int C);
 
 // Both launch n_inst clusters of a.csize CTAs (one cluster per instance).
 cudaError_t launch_forward(const FwdArgs<double> &a, int threads, size_t smem, cudaStream_t s);

@@ -10,11 +10,16 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <cuda_bf16.h>
+
 #include "sf_internal.cuh"
+#include "sf_tc.cuh"
 
 namespace sf {
 
 namespace cg = cooperative_groups;
+
+constexpr uint32_t kWaitLimit = 1u << 20;   // polls of a bounded mbarrier wait (tens of ms)
 
 template <typename T> __device__ __forceinline__ T rsq(T x);
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
@@ -116,7 +121,8 @@ __device__ __forceinline__ void block_reduce3_to(T a, T b, T c, T *red)
     }
 }
 
-template <typename T, int ND>
+// TC: compile in the tensor-core projection (FP32 only); other instantiations stay lean.
+template <typename T, int ND, bool TC = false>
 struct Cta {
     using VP = Vec<T, NDP<ND>::v>;
     int tid, nt, C, cr, nxi, n, npad, H, N, NN, nobs, opad, hc, k_lo, k_hi, L, r_lo, r_hi, ii;
@@ -124,14 +130,25 @@ struct Cta {
     T rho, invn;
     Inst<T> I;
     Shape S;
-    T *W, *xb, *lam, *xc, *v, *gp, *dl, *dd, *Rb, *ob, *bd, *db, *sx, *red, *Ps;
+    T *W, *xb, *lam, *xc, *v, *gp, *dl, *dd, *rr, *wtw, *Rb, *ob, *bd, *db, *sx, *red, *Ps;
+    int n_refine, n_obs_;
     VP *P;
     const T *Prow, *Pbg, *obs_g;
     int64_t gstride;
     T *Pdev, *Pdif, *Bdev, *Bdif, *mv, *pm, *mb;
     int need_b;
+    // tensor-core projection (FP32 kernels, dense mode)
+    int tcm, tc_nK, tc_nT, tc_na, tc_es, tc_bbytes, tc_sbo_b;
+    unsigned char *tc_ring, *tc_B;
+    uint64_t *tc_bar;          // full[2], empty[2], done
+    int *tc_flag;              // sticky failure flag
+    uint32_t *tc_slot;         // tensor-memory address written by tcgen05.alloc
+    // per ring stage s: full-barrier phases waited (fw), loads issued (ld), MMA commits (ec);
+    // scalars, not arrays, so that a runtime stage index keeps the object in registers
+    uint32_t tmem_base, tmem_cols, tc_done, tc_fw0, tc_fw1, tc_ld0, tc_ld1, tc_ec0, tc_ec1;
+    const unsigned char *tc_src;
 
-    __device__ void init(const FwdArgs<T> &A, unsigned char *smem_raw, const FwdCarve &cv, int inst, int rank, int csize)
+    __device__ __forceinline__ void init(const FwdArgs<T> &A, unsigned char *smem_raw, const FwdCarve &cv, int inst, int rank, int csize)
     {
         T *sm = reinterpret_cast<T *>(smem_raw);
         tid = threadIdx.x;
@@ -159,7 +176,10 @@ struct Cta {
         r_lo = min(N, cr * L);
         r_hi = min(N, r_lo + L);
         W = sm + cv.W; xb = sm + cv.xb; lam = sm + cv.lam; xc = sm + cv.xc; v = sm + cv.v;
-        gp = sm + cv.gp; dl = sm + cv.dl; dd = sm + cv.dd; Rb = sm + cv.Rb; ob = sm + cv.ob;
+        gp = sm + cv.gp; dl = sm + cv.dl; dd = sm + cv.dd; rr = sm + cv.rr; wtw = sm + cv.wtw;
+        Rb = sm + cv.Rb; ob = sm + cv.ob;
+        n_refine = A.n_refine;
+        n_obs_ = I.n_obs;
         bd = sm + cv.bd; db = sm + cv.db; sx = sm + cv.sx; red = sm + cv.red; Ps = sm + cv.Ps;
         P = reinterpret_cast<VP *>(sm + cv.pb);
         gstride = carve_round(NN + 4, (int)sizeof(T));
@@ -169,10 +189,75 @@ struct Cta {
         mv = Bdif + 2 * nxi; pm = mv + ND * nxi; mb = pm + ND * nxi;
         Prow = nullptr;
         need_b = 0;
+        tcm = 0;
     }
 
+    // Tensor-core projection set-up: barriers, the zeroed B operand and a tensor-memory
+    // accumulator of 16 columns per 128-row tile.  All threads call it.
+    __device__ __forceinline__ void tc_setup(const FwdArgs<T> &A, unsigned char *smem_raw)
+    {
+        if constexpr (TC && sizeof(T) == 4) {
+            tcm = dense ? A.tc_mode : 0;
+            if (!tcm) return;
+            tc_es = sf::tc_es(tcm);
+            tc_nK = tc_nk(tcm, N);
+            tc_nT = tc_ntiles(N, C);
+            tc_na = sf::tc_na(tcm);
+            const int kpad = tc_nK * tc_kc(tcm);
+            tc_bbytes = 16 * kpad * tc_es;
+            tc_sbo_b = (kpad * tc_es / 16) * 128;
+            tc_ring = smem_raw;
+            tc_B = tc_ring + 2 * kTcChunkBytes * tc_na;
+            unsigned char *bars = tc_B + (int64_t)tc_bbytes * tc_na + tc_bbytes + 1024;
+            tc_bar = reinterpret_cast<uint64_t *>(bars);
+            tc_flag = reinterpret_cast<int *>(bars + 40);
+            tc_slot = reinterpret_cast<uint32_t *>(bars + 44);
+            tc_src = A.tcA + A.tc_off[I.shape] + (int64_t)cr * tc_nT * tc_nK * tc_na * kTcChunkBytes;
+            for (int e = tid; e < tc_bbytes * tc_na / 4; e += nt) reinterpret_cast<uint32_t *>(tc_B)[e] = 0u;
+            for (int e = tid; e < nxi * nxi; e += nt) {   // W'W for the refinement's Hessian products
+                const int u = e / nxi, vv = e - u * nxi;
+                float acc = 0.f;
+                for (int k = 0; k < H; ++k) acc += W[k * nxi + u] * W[k * nxi + vv];
+                wtw[e] = acc;
+            }
+            if (tid == 0) {
+                for (int b = 0; b < 5; ++b) tc::mbar_init(tc_bar + b, 1);
+                *tc_flag = 0;
+                tc::fence_barrier_init();
+            }
+            tmem_cols = 32;
+            while (tmem_cols < (uint32_t)(16 * tc_nT)) tmem_cols <<= 1;
+            if ((tid >> 5) == 0) {
+                tc::tmem_alloc(tc_slot, tmem_cols);
+                tc::tmem_relinquish();
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            tmem_base = *tc_slot;
+            tc_done = 0;
+            tc_fw0 = tc_fw1 = tc_ld0 = tc_ld1 = tc_ec0 = tc_ec1 = 0;
+        }
+    }
+
+    // Releases the tensor memory after waiting (bounded) for copies still in flight.
+    __device__ __forceinline__ void tc_teardown()
+    {
+        if constexpr (TC && sizeof(T) == 4) {
+            if (!tcm) return;
+            if (tid == 0) {
+                while (tc_fw0 < tc_ld0 && tc::mbar_wait(tc_bar + 0, tc_fw0 & 1, kWaitLimit)) ++tc_fw0;
+                while (tc_fw1 < tc_ld1 && tc::mbar_wait(tc_bar + 1, tc_fw1 & 1, kWaitLimit)) ++tc_fw1;
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            if ((tid >> 5) == 0) tc::tmem_dealloc(tmem_base, tmem_cols);
+        }
+    }
+
+
     // Basis, candidate, boundary values, obstacle records and projection operators.
-    __device__ void load_constants(const FwdArgs<T> &A, int p_rows)
+    __device__ __forceinline__ void load_constants(const FwdArgs<T> &A, int p_rows)
     {
         const T *Wg = A.W + S.off_W;
         for (int e = tid; e < H * nxi; e += nt) W[e] = Wg[e];
@@ -214,7 +299,7 @@ struct Cta {
 
     // b - A xi_bar for the current xb (nonzero only when it misses the boundary values);
     // sets need_b (block-uniform) and the robot means mb for the structured form.
-    __device__ void boundary_gap()
+    __device__ __forceinline__ void boundary_gap()
     {
         __syncthreads();
         int nb = 0;
@@ -235,7 +320,7 @@ struct Cta {
     }
 
     // out[i][kl][ax] = sum_c W[k0 + kl][c] coeff[ax][i][c] (vector layout, one (ax, i, kl) per thread)
-    __device__ void wvec(int k0, int hcc, const T *coeff, VP *out)
+    __device__ __forceinline__ void wvec(int k0, int hcc, const T *coeff, VP *out)
     {
         T *o = reinterpret_cast<T *>(out);
         for (int e = tid; e < ND * n * hcc; e += nt) {
@@ -255,7 +340,7 @@ struct Cta {
     }
 
     // positions of coeff for the chunk, robots padded with far stand-ins
-    __device__ void positions(int k0, int hcc, const T *coeff)
+    __device__ __forceinline__ void positions(int k0, int hcc, const T *coeff)
     {
         wvec(k0, hcc, coeff, P);
         for (int e = n * hcc + tid; e < npad * hcc; e += nt) {
@@ -267,7 +352,7 @@ struct Cta {
     }
 
     // dst[ax][i][c] += sum_kl W[k0 + kl][c] src[ax][i][kl]
-    __device__ void wt_acc(int k0, int hcc, const T *src, T *dst)
+    __device__ __forceinline__ void wt_acc(int k0, int hcc, const T *src, T *dst)
     {
         for (int e = tid; e < NN; e += nt) {
             const int r = e / nxi, c = e - r * nxi;
@@ -289,7 +374,7 @@ struct Cta {
     // Rows of the items (i, k) of one chunk: R written to Rb[ax][i][kl].  Partners and
     // obstacles are tested four at a time; the warp votes once per block of four and takes
     // the rare active-row path only when one of its lanes needs it.
-    __device__ void rows(int k0, int hcc, T &rp2, T &mx2)
+    __device__ __forceinline__ void rows(int k0, int hcc, T &rp2, T &mx2)
     {
         const int items = n * hcc;
         const T a2 = I.a * I.a, ia2 = I.ia2, kz = (I.a * I.a) * I.ib2;
@@ -393,7 +478,7 @@ struct Cta {
     // p* = sum over active rows of J' (R*_i - R*_j) (pairs), J' R*_i (obstacles) and the
     // box mask times R*_i, to Rb[ax][i][kl].  seed_w > 0 instead differentiates
     // seed_w / 2 * ||r_p||^2: y = seed_w r_1 on every active row and seed_w (u+ - l+) on the box.
-    __device__ void rows_adjoint(int k0, int hcc, const VP *Rs, T seed_w)
+    __device__ __forceinline__ void rows_adjoint(int k0, int hcc, const VP *Rs, T seed_w)
     {
         const bool seed = seed_w != T(0);
         const int items = n * hcc;
@@ -484,11 +569,170 @@ struct Cta {
         }
     }
 
+    // Rows [r_lo, r_hi) of P_eta src on the tensor cores into dl: B = src (axes as rows,
+    // converted to TF32 / BF16 [+ BF16 residual]); the CTA's A chunks stream through a
+    // two-stage ring by bulk copies; one thread issues tcgen05.mma into tensor memory;
+    // warps 0-3 read the 128-row tiles back.  A wait that runs out sets the sticky flag
+    // and the instance's status; the control flow of every thread stays the same.
+    __device__ __forceinline__ void tc_rows(const T *src, bool corr_b)
+    {
+        if constexpr (TC && sizeof(T) == 4) {
+            const int es = tc_es, na = tc_na;
+            for (int e = tid; e < ND * N; e += nt) {
+                const int ax = e / N, c = e - ax * N;
+                const float x = src[ax * N + c];
+                const int off = ((c * es) >> 4) * 128 + ax * 16 + ((c * es) & 15);
+                if (tcm == 1) {
+                    *reinterpret_cast<float *>(tc_B + off) = tc::to_tf32(x);
+                } else {
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                    *reinterpret_cast<__nv_bfloat16 *>(tc_B + off) = hi;
+                    if (na == 2)
+                        *reinterpret_cast<__nv_bfloat16 *>(tc_B + tc_bbytes + off) =
+                            __float2bfloat16_rn(x - __bfloat162float(hi));
+                }
+            }
+            tc::fence_async_shared();
+            __syncthreads();
+            const bool failed = *tc_flag != 0;
+            if (!failed && tid == 0) {
+                const int items = tc_nT * tc_nK;
+                const uint32_t stage_bytes = (uint32_t)(na * kTcChunkBytes);
+                const uint32_t idesc = tc::instr_desc(tcm == 1 ? 2u : 1u, 128, 16);
+                const uint32_t ring0 = tc::smem_u32(tc_ring), b0 = tc::smem_u32(tc_B);
+                bool bad = false;
+                for (int w = 0; w < items && w < 2; ++w) {
+                    tc::mbar_arrive_expect_tx(tc_bar + w, stage_bytes);
+                    tc::bulk_g2s(tc_ring + w * stage_bytes, tc_src + (int64_t)w * stage_bytes, stage_bytes, tc_bar + w);
+                    if (w) ++tc_ld1; else ++tc_ld0;
+                }
+                for (int w = 0; w < items; ++w) {
+                    const int st = w & 1;
+                    const uint32_t fw = st ? tc_fw1 : tc_fw0;
+                    if (!tc::mbar_wait(tc_bar + st, fw & 1, kWaitLimit)) {
+                        bad = true;
+                        break;
+                    }
+                    if (st) ++tc_fw1; else ++tc_fw0;
+                    tc::fence_after_sync();
+                    const int t = w / tc_nK, kc = w - t * tc_nK;
+                    const uint32_t d_tmem = tmem_base + 16u * t;
+                    const uint32_t a_hi = ring0 + st * stage_bytes, a_lo = a_hi + kTcChunkBytes;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint64_t ad = tc::smem_desc(a_hi + 256u * j, 128, 1024);
+                        const uint32_t boff = (uint32_t)((kc * 8 + 2 * j) * 128);
+                        const uint64_t bd_ = tc::smem_desc(b0 + boff, 128, tc_sbo_b);
+                        const uint32_t acc = (kc > 0 || j > 0) ? 1u : 0u;
+                        if (tcm == 1) {
+                            tc::mma_tf32(d_tmem, ad, bd_, idesc, acc);
+                        } else {
+                            tc::mma_bf16(d_tmem, ad, bd_, idesc, acc);
+                            if (na == 2) {
+                                const uint64_t bl = tc::smem_desc(b0 + tc_bbytes + boff, 128, tc_sbo_b);
+                                const uint64_t al = tc::smem_desc(a_lo + 256u * j, 128, 1024);
+                                tc::mma_bf16(d_tmem, ad, bl, idesc, 1u);
+                                tc::mma_bf16(d_tmem, al, bd_, idesc, 1u);
+                            }
+                        }
+                    }
+                    tc::mma_commit(tc_bar + 2 + st);
+                    if (st) ++tc_ec1; else ++tc_ec0;
+                    if (w + 2 < items) {
+                        const uint32_t ec = st ? tc_ec1 : tc_ec0;
+                        if (!tc::mbar_wait(tc_bar + 2 + st, (ec - 1) & 1, kWaitLimit)) {
+                            bad = true;
+                            break;
+                        }
+                        tc::mbar_arrive_expect_tx(tc_bar + st, stage_bytes);
+                        tc::bulk_g2s(tc_ring + st * stage_bytes, tc_src + (int64_t)(w + 2) * stage_bytes, stage_bytes,
+                                     tc_bar + st);
+                        if (st) ++tc_ld1; else ++tc_ld0;
+                    }
+                }
+                tc::mma_commit(tc_bar + 4);
+                if (bad) *tc_flag = 1;
+            }
+            bool ok = !failed;
+            if (!failed) {
+                ok = tc::mbar_wait(tc_bar + 4, tc_done & 1, kWaitLimit);
+                ++tc_done;
+            }
+            ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+            tc::fence_after_sync();
+            const int wp = tid >> 5, lane = tid & 31;
+            if (wp < 4) {
+                for (int t = 0; t < tc_nT; ++t) {
+                    float dv[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (ok) tc::tmem_ld_x4(tmem_base + ((uint32_t)(32 * wp) << 16) + 16u * t, dv);
+                    const int row = r_lo + 128 * t + 32 * wp + lane;
+                    if (row < r_hi) {
+#pragma unroll
+                        for (int ax = 0; ax < ND; ++ax) {
+                            T a = (T)dv[ax];
+                            if (corr_b)
+                                for (int q = 0; q < 2 * n; ++q)
+                                    a += Pbg[(int64_t)row * 2 * n + q] * db[(ax * n + (q >> 1)) * 2 + (q & 1)];
+                            dl[ax * N + row] = a;
+                        }
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+        }
+    }
+
+    // true when a bounded wait of the tensor-core pipeline ran out in this CTA
+    __device__ __forceinline__ bool tc_timed_out() const
+    {
+        if constexpr (TC && sizeof(T) == 4) return tcm && *tc_flag != 0;
+        return false;
+    }
+
     // dst = P_eta src (+ P_b db when corr_b); dst[e] is valid for the elements e this
     // thread owns (e = tid + j nt).  src and dst must differ from each other and from dl.
-    __device__ void project(cg::cluster_group &cl, const T *src, T *dst, bool corr_b)
+    __device__ __forceinline__ void project(cg::cluster_group &cl, const T *src, T *dst, bool corr_b)
     {
-        if (dense) {
+        if (TC && dense && tcm) {
+            tc_rows(src, corr_b);
+            cl.sync();
+            for (int e = tid; e < NN; e += nt) {
+                const int row = e - (e / N) * N;
+                dst[e] = cl.map_shared_rank(dl, row / L)[e];
+            }
+            // refinement: dst += P~ (src - H dst) on the interior coefficients, the residual in
+            // FP32 through H = I + rho ((n + n_obs + 2) I - 11') (x) W'W
+            for (int pass = 0; pass < n_refine; ++pass) {
+                __syncthreads();
+                T *sums = wtw + nxi * nxi;   // [ND][nxi] robot sums of dst
+                const int lane = tid & 31, nw = nt >> 5;
+                for (int pq = tid >> 5; pq < ND * nxi; pq += nw) {
+                    const int ax = pq / nxi, c = pq - ax * nxi;
+                    T sacc = T(0);
+                    for (int i = lane; i < n; i += 32) sacc += dst[(ax * n + i) * nxi + c];
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                    if (lane == 0) sums[pq] = sacc;
+                }
+                __syncthreads();
+                const T cn = T(n + n_obs_ + 2);
+                for (int e = tid; e < NN; e += nt) {
+                    const int r = e / nxi, u = e - r * nxi, ax = r / n;
+                    T hv = T(0);
+                    for (int c = 0; c < nxi; ++c) hv += wtw[u * nxi + c] * (cn * dst[r * nxi + c] - sums[ax * nxi + c]);
+                    const T res = src[e] - (dst[e] + rho * hv);
+                    rr[e] = (u == 0 || u == nxi - 1) ? T(0) : res;
+                }
+                __syncthreads();
+                tc_rows(rr, false);
+                cl.sync();
+                for (int e = tid; e < NN; e += nt) {
+                    const int row = e - (e / N) * N;
+                    dst[e] += cl.map_shared_rank(dl, row / L)[e];
+                }
+            }
+        } else if (dense) {
             // rows [r_lo, r_hi) of P_eta src: 8 lanes per row, interleaved columns; the trip
             // count is the same for every thread, so whole warps take part in the shuffles
             const int seg = 8, rows = r_hi - r_lo;
@@ -566,7 +810,7 @@ struct Cta {
     }
 
     // First half of an iteration of T: rows of this CTA's timesteps, partial g into gme.
-    __device__ void rows_and_g(T *gme, T &rp2, T &mx2)
+    __device__ __forceinline__ void rows_and_g(T *gme, T &rp2, T &mx2)
     {
         for (int e = tid; e < NN; e += nt) gme[e] = T(0);
         for (int k0 = k_lo; k0 < k_hi; k0 += hc) {
@@ -583,7 +827,7 @@ struct Cta {
     // Second half, after the cluster barrier: g = sum over the cluster of gme (fixed order,
     // the same bits in every CTA), lambda step, correction projection, xi_bar update.
     // Returns this thread's share of ||z^{l+1} - z^l||^2.
-    __device__ T update(cg::cluster_group &cl, const T *gme, bool corr_b)
+    __device__ __forceinline__ T update(cg::cluster_group &cl, const T *gme, bool corr_b)
     {
         T fp = T(0);
         for (int e = tid; e < NN; e += nt) {

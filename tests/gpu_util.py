@@ -11,9 +11,10 @@ def pack_list(solver, arrays):
 
 
 def gpu_solve(insts, iters, precision="fp64", proj="dense", rho=0.3, xi0=None, lam0=None, ckpt_every=0,
-              tol=1e-3, max_iters=None, cluster=None, threads=0):
+              tol=1e-3, max_iters=None, cluster=None, threads=0, n_refine=0):
     s = SFSolver(insts, insts[0]["n_d"], insts[0]["n_xi"], rho=rho, precision=precision, proj=proj,
-                 max_iters=max(iters, 1) if max_iters is None else max_iters, ckpt_every=ckpt_every, tol=tol)
+                 max_iters=max(iters, 1) if max_iters is None else max_iters, ckpt_every=ckpt_every, tol=tol,
+                 n_refine=n_refine)
     if cluster is not None:
         s.set_launch(cluster, threads)
     data = s.pack(insts)
