@@ -1,12 +1,18 @@
 #!/usr/bin/env python
-"""Benchmark of the batched Safety-Filter solve.
+"""Benchmark of the batched, differentiable Safety-Filter solve.
 
-One step = one full SF solve of a batch (every iteration of T on every instance,
-plus the FP64 residual check of the result).  Default workload: 32 instances of
-16 disc robots in a 15 x 15 m 2D map with 20 obstacles, horizon 100, 200
-iterations (seeded synthetic instances from ``sfgen``).  Prints one JSON line.
+One step = the whole hot path on one batch: sf_solve (every iteration of T on every
+instance, checkpoints every c iterations), the FP64 residual check of the result and
+sf_solve_backward (the adjoint of all the iterations, seeded with a fixed cotangent).
+Default workload: 32 instances of 16 disc robots in a 15 x 15 m 2D map with 20
+obstacles, horizon 100, 200 iterations (seeded synthetic instances from ``sfgen``).
+Beside it: the plain FP64 GPU path and the other precisions / projections on the same
+batch (time and error against FP64), a CUDA-graph replay of the step, the end-to-end
+call from pinned host memory and the FP64 oracle on the host cores.  Prints one JSON
+line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config C] [--precision P] [--proj dense|structured] [--forward-only]
 
 Under torchrun each rank solves its own batch (seeds offset by rank): weak scaling,
 no collective on the data path; the step time is the max over ranks.
@@ -43,9 +49,12 @@ def args_():
     p.add_argument("--config", type=int, default=2)
     p.add_argument("--precision", default="fp32")
     p.add_argument("--proj", default="dense")
+    p.add_argument("--n-refine", type=int, default=0)
+    p.add_argument("--ckpt-every", type=int, default=10)
+    p.add_argument("--forward-only", action="store_true", help="time sf_solve + residual check without the adjoint")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--compare-fp64", action="store_true", help="also time the plain FP64 GPU solve")
+    p.add_argument("--no-compare", action="store_true", help="skip the FP64 and tensor-core comparison solves")
     p.add_argument("--no-autotune", action="store_true")
     return p.parse_args()
 
@@ -61,19 +70,37 @@ def workload(cid, rank=0):
     return cfg, insts, pairs, obs
 
 
-def algorithmic_flops(insts, iters, proj):
-    """FP32 operations of one forward launch counted at the algorithmic minimum:
-    per pair or obstacle row 2 n_d + 1 (line of sight, scaled squared norm), per
-    (robot, timestep) 2 n_d box tests, positions and W' aggregation 2 n_d n H n_xi each,
-    lambda / correction 6 n_d N, projection 2 n_d N^2 (dense) or 4 n_d n n_xi^2."""
+def _per_iter(i, proj):
+    """Algorithmic FP32 operations of one forward iteration of one instance: per pair or
+    obstacle row 2 n_d + 1 (line of sight, scaled squared norm), per (robot, timestep)
+    2 n_d box tests, positions and W' aggregation 2 n_d n H n_xi each, lambda and the
+    correction 6 n_d N, projection 2 n_d N^2 (dense) or 4 n_d n n_xi^2 (structured)."""
+    nd, n, H, nxi, no = i["n_d"], i["n"], i["H"], i["n_xi"], i["n_obs"]
+    N = n * nxi
+    rows = (n * (n - 1) // 2 + n * no) * H
+    per = rows * (2 * nd + 1) + 2 * nd * n * H + 4 * nd * n * H * nxi + 6 * nd * N
+    proj_f = 2 * nd * N * N if proj == "dense" else 4 * nd * n * nxi * nxi
+    return per + proj_f, rows, proj_f
+
+
+def algorithmic_flops(insts, iters, proj, kernel="k_forward"):
+    """Operations of one launch of ``kernel`` at the algorithmic minimum.
+    k_forward: iters forward iterations.  k_backward: the recomputation (iters forward
+    iterations) plus the reverse sweep, per iteration the activity test of every row
+    (2 n_d + 1) and box entry (2 n_d), positions, R* = W g* and W' p* (2 n_d n H n_xi
+    each), the projection and 8 n_d N elementwise.  k_residual: one FP64 pass over the
+    rows and the positions."""
     tot = 0.0
     for i in insts:
-        nd, n, H, nxi, no = i["n_d"], i["n"], i["H"], i["n_xi"], i["n_obs"]
-        N = n * nxi
-        rows = (n * (n - 1) // 2 + n * no) * H
-        per = rows * (2 * nd + 1) + 2 * nd * n * H + 4 * nd * n * H * nxi + 6 * nd * N
-        per += 2 * nd * N * N if proj == "dense" else 4 * nd * n * nxi * nxi
-        tot += per * iters
+        fwd, rows, proj_f = _per_iter(i, proj)
+        nd, n, H, nxi = i["n_d"], i["n"], i["H"], i["n_xi"]
+        if kernel == "k_forward":
+            tot += fwd * iters
+        elif kernel == "k_backward":
+            rev = rows * (2 * nd + 1) + 2 * nd * n * H + 6 * nd * n * H * nxi + proj_f + 8 * nd * n * nxi
+            tot += (fwd + rev) * iters
+        else:
+            tot += rows * (2 * nd + 1) + 2 * nd * n * H + 2 * nd * n * H * nxi
     return tot
 
 
@@ -149,23 +176,68 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(insts, iters, budget_s=15.0):
-    """The FP64 oracle, as it stands, on the host cores over a bounded sample of the batch."""
+def _oracle_step(sample, iters, seeds, forward_only, pool):
+    """One step of the oracle on ``sample``: the FP64 solve (OpenMP over instances) or,
+    for the differentiable step, per instance (threads over instances) the solve, the
+    residual check and the reverse pass (which recomputes the forward, as the adjoint
+    kernel does)."""
+    import oracle
+    if forward_only:
+        oracle.solve_batch(sample, iters, rho=RHO)
+        return
+
+    def one(k):
+        inst = sample[k]
+        xo = oracle.solve(inst, iters, rho=RHO)["xi"]
+        oracle.residual(inst, xo, rho=RHO)
+        oracle.solve_backward(inst, iters, g_xi_out=seeds[k], g_rp2=1.0, rho=RHO)
+
+    list(pool.map(one, range(len(sample))))
+
+
+def _oracle_sample(insts, iters, forward_only, budget_s):
+    """A bounded sample of the batch sized to about ``budget_s`` of host work per step."""
+    import concurrent.futures
     import oracle
     oracle.load()
     cores = os.cpu_count() or 1
-    # grow the sample until it costs about budget_s (never more than the whole batch)
+    pool = concurrent.futures.ThreadPoolExecutor(max_workers=cores)
+    seeds = [np.random.default_rng(100 + k).normal(size=i["xi"].shape) * 1e-2 for k, i in enumerate(insts)]
     t0 = time.perf_counter()
-    oracle.solve_batch(insts[:1], iters, rho=RHO)
+    _oracle_step(insts[:1], iters, seeds, forward_only, pool)
     one = max(time.perf_counter() - t0, 1e-3)
     k = int(max(1, min(len(insts), budget_s / one * cores * 0.7)))
-    sample = insts[:k]
+    return insts[:k], seeds[:k], pool, cores
+
+
+def _oracle_desc(k, B, iters, forward_only, dt=None):
+    what = ("FP64 solve, OpenMP over instances" if forward_only else
+            "FP64 solve + residual + reverse pass per instance, threads over instances")
+    d = "%d of %d instances x %d iterations, %s" % (k, B, iters, what)
+    return d + (" (%.1f s)" % dt if dt is not None else "")
+
+
+def cpu_baseline(insts, iters, forward_only, budget_s=15.0):
+    """The FP64 oracle, as it stands, on the host cores over a bounded sample of the batch."""
+    sample, seeds, pool, cores = _oracle_sample(insts, iters, forward_only, budget_s)
     t0 = time.perf_counter()
-    oracle.solve_batch(sample, iters, rho=RHO)
+    _oracle_step(sample, iters, seeds, forward_only, pool)
     dt = time.perf_counter() - t0
     pairs, _ = sfgen.batch_stats(sample)
     return {"value": pairs * iters / dt, "unit": "pair-timestep updates/s", "cores": cores, "kind": "oracle",
-            "sample": "%d of %d instances x %d iterations, FP64, OpenMP over instances (%.1f s)" % (k, len(insts), iters, dt)}
+            "sample": _oracle_desc(len(sample), len(insts), iters, forward_only, dt)}
+
+
+METRIC = "SF ms/batch & pair-timestep updates/s, chosen vs plain FP64, residual≤1e-3 m"
+
+
+def _config(cfg, insts, iters, a, extra=None):
+    c = {"workload": cfg.name, "instances": len(insts), "robots": cfg.n[0], "obstacles": cfg.n_obs[0],
+         "horizon": cfg.H[0], "iterations": iters, "n_d": cfg.n_d, "n_xi": 11, "rho": RHO,
+         "step": ("sf_solve + FP64 residual check" if a.forward_only else
+                  "sf_solve (checkpoints every %d) + FP64 residual check + sf_solve_backward" % a.ckpt_every)}
+    c.update(extra or {})
+    return c
 
 
 def run_reference(a):
@@ -173,38 +245,114 @@ def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    cfg, insts, pairs_all, _ = workload(a.config)
+    cfg, insts, _, _ = workload(a.config)
     iters = cfg.iters
-    oracle.load()
-    t0 = time.perf_counter()
-    oracle.solve_batch(insts[:1], iters, rho=RHO)
-    one = max(time.perf_counter() - t0, 1e-3)
-    cores = os.cpu_count() or 1
-    k = int(max(1, min(len(insts), 4.0 / one * cores * 0.7)))  # about 4 s of CPU work per step
-    sample = insts[:k]
+    sample, seeds, pool, cores = _oracle_sample(insts, iters, a.forward_only, 4.0)   # ~4 s of host work per step
     pairs, _ = sfgen.batch_stats(sample)
     for _ in range(a.warmup):
-        oracle.solve_batch(sample, iters, rho=RHO)
+        _oracle_step(sample, iters, seeds, a.forward_only, pool)
     times = []
     for _ in range(a.steps):
         t0 = time.perf_counter()
-        oracle.solve_batch(sample, iters, rho=RHO)
+        _oracle_step(sample, iters, seeds, a.forward_only, pool)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = pairs * iters * a.steps / tot
-    desc = "%d of %d instances x %d iterations per step, FP64 oracle, OpenMP over instances" % (k, len(insts), iters)
-    line = {"impl": "reference", "metric": "SF pair-timestep updates/s", "value": value,
+    desc = _oracle_desc(len(sample), len(insts), iters, a.forward_only) + " per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "pair-timestep updates/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": 1e3 * tot / a.steps * len(insts) / k, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg.name, "instances": len(insts), "robots": cfg.n[0], "obstacles": cfg.n_obs[0],
-                       "horizon": cfg.H[0], "iterations": iters, "n_d": cfg.n_d},
+            "ms_per_step": 1e3 * tot / a.steps * len(insts) / len(sample), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(cfg, insts, iters, a, {"precision": "fp64 (oracle)"}),
             "cpu_baseline": {"value": value, "unit": "pair-timestep updates/s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "pair-timestep updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+class Step:
+    """Buffers and calls of one bench step on one solver: the solve with the FP64 residual
+    check and, unless forward-only, the adjoint seeded with a fixed cotangent on xi_out
+    and d/d||r_p||^2 = 1 (the work of the reverse pass does not depend on the seed values)."""
+
+    def __init__(self, solver, data, iters, forward_only, stream):
+        import torch
+        self.s, self.data, self.iters, self.fo, self.stream = solver, data, iters, forward_only, stream
+        x = data["xi"]
+        self.xo, self.lo = torch.empty_like(x), torch.empty_like(x)
+        self.res = torch.empty((solver.B, 4), dtype=torch.float64, device=x.device)
+        g = np.random.default_rng(7).normal(size=x.numel()) * 1e-2
+        self.gxo = torch.as_tensor(g, dtype=x.dtype, device=x.device)
+        self.grp2 = torch.ones(solver.B, dtype=torch.float64, device=x.device)
+        self.g = (torch.empty_like(x), torch.empty_like(x), torch.empty_like(x))
+
+    def __call__(self):
+        self.s.solve(self.data, self.data["xi"], self.iters, xi_out=self.xo, lam_out=self.lo, resid=self.res,
+                     stream=self.stream)
+        if not self.fo:
+            self.s.backward(self.gxo, None, self.grp2, out=self.g, stream=self.stream)
+
+    def launches(self):
+        return 2 if self.fo else 3
+
+
+def _time_steps(step, n, stream, flush=None, per_kernel=None):
+    import torch
+    times, kt = [], []
+    for _ in range(n):
+        if flush is not None:
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        if per_kernel is not None:
+            kt.append(per_kernel())
+    return times, kt
+
+
+def _positions(solver, flat, insts):
+    import torch
+    out = []
+    for k in range(len(insts)):
+        W = torch.as_tensor(solver.operator(k, 0), device=flat.device, dtype=torch.float64)
+        out.append(torch.einsum("hc,anc->anh", W, solver.unpack(flat, k).double()))
+    return out
+
+
+def _max_pos_err(pa, pb):
+    return max(float((a - b).norm(dim=0).max()) for a, b in zip(pa, pb))
+
+
+def _variant(insts, nd, iters, a, precision, proj, n_refine, dev, stream, flush, ref_pos, ref_res, reps=10):
+    """Times the step of another precision / projection and reports its error against
+    the FP64 GPU solve of the same batch."""
+    import torch
+
+    from paper_2510_09204_b300 import SFSolver
+    s = SFSolver(insts, nd, 11, rho=RHO, precision=precision, proj=proj, max_iters=iters,
+                 ckpt_every=0 if a.forward_only else a.ckpt_every, n_refine=n_refine)
+    d = s.pack(insts, device=dev)
+    if not a.no_autotune:
+        s.autotune(d, d["xi"], iters, reps=1, stream=stream)
+    st = Step(s, d, iters, a.forward_only, stream)
+    for _ in range(2):
+        st()
+    torch.cuda.synchronize()
+    times, _ = _time_steps(st, reps, stream, flush)
+    r = st.res.cpu().numpy()
+    out = {"precision": precision, "projection": proj, "n_refine": n_refine, "ms_per_step": statistics.median(times),
+           "launch": list(s.launch()[:2]), "status_ok": bool((s.status() == 0).all())}
+    if ref_pos is not None:
+        out["max_position_error_vs_fp64_m"] = _max_pos_err(_positions(s, st.xo, insts), ref_pos)
+        out["max_final_residual_diff_vs_fp64_m"] = float(np.abs(r[:, 1] - ref_res[:, 1]).max())
+    out["_pos"], out["_res"] = _positions(s, st.xo, insts), r
+    s.close()
+    return out
 
 
 def main():
@@ -225,22 +373,18 @@ def main():
     cfg, insts, pairs, obs = workload(a.config, rank)
     iters = cfg.iters
     nd = cfg.n_d
-    solver = SFSolver(insts, nd, 11, rho=RHO, precision=a.precision, proj=a.proj, max_iters=iters)
-    data = solver.pack(insts, device=dev)
-    xo = torch.empty_like(data["xi"])
-    lo = torch.empty_like(data["xi"])
-    res = torch.empty((len(insts), 4), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+    solver = SFSolver(insts, nd, 11, rho=RHO, precision=a.precision, proj=a.proj, max_iters=iters,
+                      ckpt_every=0 if a.forward_only else a.ckpt_every, n_refine=a.n_refine)
+    data = solver.pack(insts, device=dev)
     tune = None
     if not a.no_autotune:
         t0 = time.perf_counter()
-        c, t, ms = solver.autotune(data, data["xi"], iters, reps=2)
-        tune = {"cluster": c, "threads": t, "best_ms": ms, "tuning_s": time.perf_counter() - t0}
+        c, t, ms = solver.autotune(data, data["xi"], iters, reps=2, stream=stream)
+        tune = {"cluster": c, "threads": t, "best_forward_ms": ms, "tuning_s": time.perf_counter() - t0}
     solver.profile(True)
-
-    def step():
-        solver.solve(data, data["xi"], iters, xi_out=xo, lam_out=lo, resid=res, stream=stream)
+    step = Step(solver, data, iters, a.forward_only, stream)
 
     try:
         gsel = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -252,7 +396,7 @@ def main():
     for _ in range(max(a.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    assert (solver.status() == 0).all(), "non-finite iterates"
+    assert (solver.status() == 0).all(), "non-finite iterates or a timed-out wait"
 
     def barrier():
         if world > 1:
@@ -261,17 +405,7 @@ def main():
 
     barrier()
     t_start = time.time()
-    times, fwd_ms = [], []
-    for _ in range(a.steps):
-        flush.zero_()  # L2 flush between timed steps (outside the events)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        fwd_ms.append(solver.kernel_times()[0])
+    times, kts = _time_steps(step, a.steps, stream, flush, solver.kernel_times)
     barrier()
     clocks.window(t_start, time.time())
     clk = clocks.stop()
@@ -282,19 +416,57 @@ def main():
         tot_ms = float(t.item())
     ms_step = tot_ms / a.steps
     value = pairs * iters * world / (ms_step * 1e-3)
+    r = step.res.cpu().numpy()
+    chosen_pos = _positions(solver, step.xo, insts)
 
-    # end to end through the public API from pinned host memory
+    # the same step replayed from a CUDA graph
+    graph = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            gstep = Step(solver, data, iters, a.forward_only, side)
+            gstep()
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            gstep.stream = torch.cuda.current_stream()
+            gstep()
+        gt, _ = _time_steps(g.replay, a.steps, stream, flush)
+        graph = {"ms_per_step": statistics.median(gt),
+                 "bitwise_equal_to_eager": bool(torch.equal(gstep.xo, step.xo) and
+                                                (a.forward_only or torch.equal(gstep.g[0], step.g[0])))}
+    except Exception as e:  # reported, never hidden
+        graph = {"error": str(e)[:200]}
+
+    # end to end through the public API from pinned host memory: inputs (and the
+    # cotangent) in, xi_out, the residuals and d/dxi_cand out
     e2e = None
     if not a.no_e2e:
         host = {k: v.cpu().pin_memory() for k, v in data.items()}
-        outp = (torch.empty(xo.shape, dtype=xo.dtype, pin_memory=True),
-                torch.empty(res.shape, dtype=res.dtype, pin_memory=True))
+        hg = step.gxo.cpu().pin_memory()
+        outs = [torch.empty(step.xo.shape, dtype=step.xo.dtype, pin_memory=True),
+                torch.empty(step.res.shape, dtype=step.res.dtype, pin_memory=True)]
+        if not a.forward_only:
+            outs.append(torch.empty(step.xo.shape, dtype=step.xo.dtype, pin_memory=True))
+
+        def e2e_step():
+            d = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+            xo, _, res = solver.solve(d, d["xi"], iters, stream=stream)
+            outs[0].copy_(xo, non_blocking=True)
+            outs[1].copy_(res, non_blocking=True)
+            if not a.forward_only:
+                gx, _, _ = solver.backward(hg.to(dev, non_blocking=True), None, step.grp2, stream=stream)
+                outs[2].copy_(gx, non_blocking=True)
+            stream.synchronize()
+
         for _ in range(2):
-            solver.solve_host(host, iters, outp)
+            e2e_step()
         barrier()
         t0 = time.perf_counter()
         for _ in range(a.steps):
-            solver.solve_host(host, iters, outp)
+            e2e_step()
         barrier()
         e2e_s = (time.perf_counter() - t0) / a.steps
         if world > 1:
@@ -302,54 +474,63 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         h2d = sum(v.numel() * v.element_size() for v in host.values())
-        d2h = outp[0].numel() * outp[0].element_size() + outp[1].numel() * outp[1].element_size()
+        h2d += 0 if a.forward_only else hg.numel() * hg.element_size()
+        d2h = sum(o.numel() * o.element_size() for o in outs)
         e2e = {"value": pairs * iters * world / e2e_s, "unit": "pair-timestep updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
-    # plain FP64 GPU solve of the same batch (the comparison the metric names)
-    fp64 = None
-    if a.compare_fp64 and rank == 0:
-        s64 = SFSolver(insts, nd, 11, rho=RHO, precision="fp64", proj="dense", max_iters=iters)
-        d64 = s64.pack(insts, device=dev)
-        if not a.no_autotune:
-            s64.autotune(d64, d64["xi"], iters, reps=1)
-        s64.solve(d64, d64["xi"], iters)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, _, r64 = s64.solve(d64, d64["xi"], iters, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        r32 = res.cpu().numpy()
-        r64 = r64.cpu().numpy()
-        fp64 = {"ms_per_batch": ms64, "value": pairs * iters / (ms64 * 1e-3), "launch": s64.launch(),
-                "max_abs_final_residual_diff_m": float(np.abs(r32[:, 1] - r64[:, 1]).max()),
-                "frac_instances_resid_le_1e-3": float(np.mean(r64[:, 1] <= 1e-3))}
+    # plain FP64 GPU solve of the same step, and the tensor-core / structured variants
+    fp64, variants = None, []
+    if not a.no_compare and rank == 0:
+        v64 = _variant(insts, nd, iters, a, "fp64", "dense", 0, dev, stream, flush, None, None, reps=5)
+        p64, r64 = v64.pop("_pos"), v64.pop("_res")
+        fp64 = dict(v64, value=pairs * iters / (v64["ms_per_step"] * 1e-3),
+                    chosen_max_position_error_m=_max_pos_err(chosen_pos, p64),
+                    chosen_max_final_residual_diff_m=float(np.abs(r[:, 1] - r64[:, 1]).max()),
+                    frac_instances_resid_le_1e3=float(np.mean(r64[:, 1] <= 1e-3)),
+                    chosen_speedup=v64["ms_per_step"] / ms_step)
+        for prec, proj, nr in [("fp32", "structured" if a.proj == "dense" else "dense", 0), ("tf32", "dense", 2),
+                               ("bf16x3", "dense", 1), ("bf16", "dense", 3)]:
+            if (prec, proj, nr) == (a.precision, a.proj, a.n_refine):
+                continue
+            v = _variant(insts, nd, iters, a, prec, proj, nr, dev, stream, flush, p64, r64)
+            v.pop("_pos"), v.pop("_res")
+            variants.append(v)
 
     if rank == 0:
         peaks = measured_peaks()
         sm_max = float(peaks.get("sm_max_mhz", 2032.0))
         peak_alu = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        fwd_avg = statistics.mean(fwd_ms)
-        ach = algorithmic_flops(insts, iters, a.proj) / (fwd_avg * 1e-3) / 1e12
-        r = res.cpu().numpy()
+        names = ["k_forward", "k_residual", "k_backward"]
+        kernels = {}
+        for k, nm in enumerate(names):
+            if a.forward_only and nm == "k_backward":
+                continue
+            ms = statistics.mean(x[k] for x in kts)
+            fl = algorithmic_flops(insts, iters, a.proj, nm)
+            ach = fl / (ms * 1e-3) / 1e12
+            kernels[nm] = {"ms": ms, "share": ms / ms_step, "algorithmic_gflop": fl / 1e9, "achieved_tflops": ach,
+                           "frac": ach / peak_alu}
+        dom = max(kernels, key=lambda k: kernels[k]["ms"])
         line = {
-            "metric": "SF pair-timestep updates/s (ms/batch in ms_per_step)",
+            "metric": METRIC,
             "value": value, "unit": "pair-timestep updates/s", "n_gpus": world, "steps": a.steps,
             "warmup": max(a.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": cfg.name, "instances": len(insts), "robots": cfg.n[0], "obstacles": cfg.n_obs[0],
-                       "horizon": cfg.H[0], "iterations": iters, "n_d": nd, "n_xi": 11, "rho": RHO,
-                       "precision": a.precision, "projection": a.proj, "l2": "flushed between steps (256 MB write)",
-                       "cluster_ctas_per_instance": solver.launch()[0], "threads_per_cta": solver.launch()[1],
-                       "autotune": tune,
-                       "parallelism": "instances sharded by rank" if world > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
-                         "traffic": None, "kernel": "k_forward", "kernel_ms": fwd_avg,
-                         "peak_source": "148 SMs x 128 FP32 lanes x 2 x sm_max_mhz %.0f (derived)" % sm_max},
+            "config": _config(cfg, insts, iters, a, {
+                "precision": a.precision, "projection": a.proj, "n_refine": a.n_refine,
+                "l2": "flushed between steps (256 MB write)",
+                "cluster_ctas_per_instance": solver.launch()[0], "threads_per_cta": solver.launch()[1],
+                "autotune": tune,
+                "parallelism": "instances sharded by rank" if world > 1 else "single GPU"}),
+            "roofline": {"bound": "alu", "achieved": kernels[dom]["achieved_tflops"], "peak": peak_alu,
+                         "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": None, "kernel": dom,
+                         "kernel_ms": kernels[dom]["ms"],
+                         "peak_source": "148 SMs x 128 FP32 lanes x 2 x sm_max_mhz %.0f (derived ALU peak)" % sm_max},
+            "kernels": kernels,
             "clocks": clk,
-            "gpu_launches": 2 * a.steps,
+            "gpu_launches": step.launches() * a.steps,
+            "graph": graph,
             "result": {"final_max_residual_m_median": float(np.median(r[:, 1])),
                        "frac_instances_resid_le_1e-3": float(np.mean(r[:, 1] <= 1e-3))},
         }
@@ -357,8 +538,10 @@ def main():
             line["e2e"] = e2e
         if fp64:
             line["fp64_gpu"] = fp64
+        if variants:
+            line["variants"] = variants
         if not a.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(insts, iters)
+            line["cpu_baseline"] = cpu_baseline(insts, iters, a.forward_only)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

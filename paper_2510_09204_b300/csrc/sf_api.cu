@@ -112,6 +112,8 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     p.csize = C;
     size_t need = 0, need_r = 0;
     int maxL = 0;
+    bool res_ok = tc_mode != 0;
+    std::vector<int> hc_res(n_inst, 1);
     for (int i = 0; i < n_inst; ++i) {
         const int own = (H[i] + C - 1) / C;
         int hc = own;
@@ -121,6 +123,17 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
         };
         while (hc > 1 && bytes(hc, 0) > (size_t)optin) --hc;
         if (bytes(hc, 0) > (size_t)optin) return SF_EUNSUPPORTED;
+        if (tc_mode) {   // resident projector chunks, if they fit with a chunk of at least 8 timesteps
+            const int st = tc_stages(tc_mode, n[i] * nxi, C, 1);
+            int hr = own;
+            auto rbytes = [&](int h) {
+                return (size_t)std::max(forward_carve(nd, nxi, H[i], n[i], nobs[i], h, 0, esz, tc_mode, st).total,
+                                        backward_carve(nd, nxi, H[i], n[i], nobs[i], h, 0, esz, tc_mode, st).total) * esz;
+            };
+            while (hr > 1 && rbytes(hr) > (size_t)optin) --hr;
+            if (rbytes(hr) > (size_t)optin || hr < std::min(own, 8)) res_ok = false;
+            hc_res[i] = hr;
+        }
         hc_out[i] = hc;
         need = std::max(need, bytes(hc, 0));
         maxL = std::max(maxL, (n[i] * nxi + C - 1) / C);
@@ -137,12 +150,21 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
             need = with_p;
         }
     }
+    if (res_ok) {
+        p.tc_res = 1;
+        need = 0;
+        for (int i = 0; i < n_inst; ++i) {
+            hc_out[i] = hc_res[i];
+            need = std::max(need, (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], 0, esz, tc_mode,
+                                                        tc_stages(tc_mode, n[i] * nxi, C, 1)).total * esz);
+        }
+    }
     p.smem_fwd = need;
     p.smem_res = std::min((size_t)optin, need_r);
     size_t need_b = 0;
     for (int i = 0; i < n_inst; ++i)
-        need_b = std::max(need_b,
-                          (size_t)backward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], p.p_rows, esz, tc_mode).total * esz);
+        need_b = std::max(need_b, (size_t)backward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], p.p_rows, esz, tc_mode,
+                                                         tc_stages(tc_mode, n[i] * nxi, C, p.tc_res)).total * esz);
     p.smem_bwd = need_b <= (size_t)optin ? need_b : 0;
     *out = p;
     return SF_OK;
@@ -217,6 +239,31 @@ static void destroy_all(sf_handle *h)
         h->St.release();
     }
     for (DevBuf *b : bufs) b->release();
+}
+
+// Sizes the adjoint's segment scratch (a segment of recomputed iterates per cluster CTA)
+// for the current plan, so that sf_solve_backward never allocates and can be captured
+// in a CUDA graph.  Only grows.
+static int ensure_seg(sf_handle *h)
+{
+    if (h->d.ckpt_every <= 0) return SF_OK;
+    const size_t need = (size_t)h->xi_total * h->plan.csize * h->d.ckpt_every * h->esz;
+    if (h->seg.bytes >= need) return SF_OK;
+    SF_TRY(cudaDeviceSynchronize());
+    h->seg.release();
+    SF_TRY(h->seg.alloc(need));
+    return SF_OK;
+}
+
+// Event records are skipped while the stream is being captured into a graph.
+static bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return cs != cudaStreamCaptureStatusNone;
 }
 
 // (Re)builds the tensor-core chunk pool for the plan's cluster size.
@@ -415,6 +462,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
             return r;
         }
     }
+    if ((r = ensure_seg(h))) { destroy_all(h); delete h; return r; }
     *out = h;
     return SF_OK;
 }
@@ -466,6 +514,7 @@ static FwdArgs<T> fwd_args(const sf_handle *h, const void *bnd, const void *obs,
     a.oab = (const T *)oab;
     a.status = (int32_t *)h->status_dev.p;
     a.tc_mode = h->tc_mode;
+    a.tc_res = h->plan.tc_res;
     a.n_refine = h->tc_mode ? h->d.n_refine : 0;
     a.tcA = (const unsigned char *)h->tcA.p;
     a.tc_off = (const int64_t *)h->tcoff.p;
@@ -488,10 +537,12 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
     a.lo = (T *)lo;
     a.resid = resid;
     a.its = its;
-    for (int k = 0; k < SF_NKT; ++k) h->ev_used[k] = false;
-    if (h->profile) SF_TRY(cudaEventRecord(h->ev[0], st));
+    const bool prof = h->profile && !capturing(st);
+    if (prof)
+        for (int k = 0; k < SF_NKT; ++k) h->ev_used[k] = false;
+    if (prof) SF_TRY(cudaEventRecord(h->ev[0], st));
     SF_TRY(launch_forward(a, h->plan.threads, h->plan.smem_fwd, st));
-    if (h->profile) {
+    if (prof) {
         SF_TRY(cudaEventRecord(h->ev[1], st));
         h->ev_used[SF_KT_FORWARD] = true;
     }
@@ -514,9 +565,9 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
         r.status = a.status;
         r.smem_doubles = (int64_t)(h->plan.smem_res / sizeof(double));
         r.csize = h->plan.csize;
-        if (h->profile) SF_TRY(cudaEventRecord(h->ev[2], st));
+        if (prof) SF_TRY(cudaEventRecord(h->ev[2], st));
         SF_TRY(launch_residual(r, std::min(h->plan.threads, 512), h->plan.smem_res, st));
-        if (h->profile) {
+        if (prof) {
             SF_TRY(cudaEventRecord(h->ev[3], st));
             h->ev_used[SF_KT_RESIDUAL] = true;
         }
@@ -556,11 +607,8 @@ extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void 
     if (!h->plan.smem_bwd) return SF_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t seg_bytes = (size_t)h->xi_total * h->plan.csize * h->d.ckpt_every * h->esz;
-    if (h->seg.bytes < seg_bytes) {
-        SF_TRY(cudaStreamSynchronize(st));
-        h->seg.release();
-        SF_TRY(h->seg.alloc(seg_bytes));
-    }
+    if (h->seg.bytes < seg_bytes) return SF_ESTATE;   // sized whenever the plan changes
+    const bool prof = h->profile && !capturing(st);
     const SolveRecord &R = h->last;
     int rc;
     auto go = [&](auto tag) -> int {
@@ -576,9 +624,9 @@ extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void 
         b.gl0 = (T *)g_lam0;
         b.seg = (T *)h->seg.p;
         b.x0_null = R.x0 == nullptr;
-        if (h->profile) SF_TRY(cudaEventRecord(h->ev[2 * SF_KT_BACKWARD], st));
+        if (prof) SF_TRY(cudaEventRecord(h->ev[2 * SF_KT_BACKWARD], st));
         SF_TRY(launch_backward(b, h->plan.threads, h->plan.smem_bwd, st));
-        if (h->profile) {
+        if (prof) {
             SF_TRY(cudaEventRecord(h->ev[2 * SF_KT_BACKWARD + 1], st));
             h->ev_used[SF_KT_BACKWARD] = true;
         }
@@ -610,6 +658,7 @@ extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
     h->plan = p;
     h->hc = hc;
     if ((rc = build_tc_pool(h, (cudaStream_t)0))) return rc;
+    if ((rc = ensure_seg(h))) return rc;
     return h->esz == 8 ? upload_instances<double>(h) : upload_instances<float>(h);
 }
 

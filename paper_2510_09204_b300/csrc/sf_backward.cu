@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     const int w = blockIdx.x / C;
     const int ii = A.order ? A.order[w] : w;
     const Inst<T> I0 = A.inst[ii];
-    const BwdCarve cv = backward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode);
+    const BwdCarve cv = backward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
+                                    tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res));
     Cta<T, ND, TC> X;
     X.init(A, smem_raw, cv.f, ii, cr, C);
     X.load_constants(A, A.p_rows);

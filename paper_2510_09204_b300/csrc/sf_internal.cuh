@@ -50,15 +50,22 @@ __host__ __device__ inline int tc_na(int mode) { return mode == 3 ? 2 : 1; }    
 __host__ __device__ inline int tc_ntiles(int N, int C) { return (((N + C - 1) / C) + 127) / 128; }
 constexpr int kTcChunkBytes = 128 * 128;   // one 128-row x 128-byte A chunk
 
-// Bytes at the front of shared memory for the tensor-core path: two A ring stages, the B
+// A ring stages of a CTA: every chunk of its rows when they stay resident in shared
+// memory for the whole launch (res), else two stages that stream from global memory.
+__host__ __device__ inline int tc_stages(int mode, int N, int C, int res)
+{
+    return res ? tc_ntiles(N, C) * tc_nk(mode, N) : 2;
+}
+
+// Bytes at the front of shared memory for the tensor-core path: the A ring, the B
 // operand, slack after B (so any misread of a descriptor stays inside the allocation),
 // and the mbarriers / tensor-memory address.
-__host__ __device__ inline int64_t tc_smem_bytes(int mode, int N)
+__host__ __device__ inline int64_t tc_smem_bytes(int mode, int N, int stages)
 {
     if (!mode) return 0;
     const int64_t kpad = (int64_t)tc_nk(mode, N) * tc_kc(mode);
     const int64_t b = 16 * kpad * tc_es(mode);
-    return 2LL * kTcChunkBytes * tc_na(mode) + b * tc_na(mode) + b + 1024 + 128;
+    return (int64_t)stages * kTcChunkBytes * tc_na(mode) + b * tc_na(mode) + b + 1024 + 128;
 }
 
 // Shared-memory carve of the forward kernel, in elements of T.  Every region starts on a
@@ -74,13 +81,14 @@ __host__ __device__ inline int64_t carve_round(int64_t cnt, int esz)
 }
 
 // nd, nxi: dimension and coefficients; H, n, nobs: instance sizes; hc: timesteps per chunk;
-// p_rows: rows of P_eta staged in shared memory (0: read from global memory).
+// p_rows: rows of P_eta staged in shared memory (0: read from global memory); tc_mode,
+// tc_st: tensor-core projection mode and A ring stages.
 __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
-                                                  int tc_mode = 0)
+                                                  int tc_mode = 0, int tc_st = 2)
 {
     const int64_t N = (int64_t)n * nxi, NN = nd * N, ndp = nd == 2 ? 2 : 4;
     FwdCarve c;
-    int64_t o = (tc_smem_bytes(tc_mode, (int)N) + 127) / 128 * 128 / esz;   // tensor-core buffers first
+    int64_t o = (tc_smem_bytes(tc_mode, (int)N, tc_st) + 127) / 128 * 128 / esz;   // tensor-core buffers first
     c.W = o;   o += carve_round((int64_t)H * nxi, esz);
     c.xb = o;  o += carve_round(NN, esz);
     c.lam = o; o += carve_round(NN, esz);
@@ -112,10 +120,10 @@ struct BwdCarve {
 };
 
 __host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
-                                                   int tc_mode = 0)
+                                                   int tc_mode = 0, int tc_st = 2)
 {
     BwdCarve b;
-    b.f = forward_carve(nd, nxi, H, n, nobs, hc, p_rows, esz, tc_mode);
+    b.f = forward_carve(nd, nxi, H, n, nobs, hc, p_rows, esz, tc_mode, tc_st);
     const int64_t NN = (int64_t)nd * n * nxi, npad = (n + 3) / 4 * 4, ndp = nd == 2 ? 2 : 4;
     int64_t o = b.f.total;
     b.xs = o; o += carve_round(NN, esz);
@@ -132,6 +140,7 @@ struct FwdArgs {
     int csize;        // CTAs per instance (thread-block cluster), 1..kMaxCluster
     int p_rows;       // rows of P_eta per CTA staged in shared memory (dense; 0 = global)
     int tc_mode;      // tensor-core projection: 0 none, 1 TF32, 2 BF16, 3 BF16 x3
+    int tc_res;       // the CTA's projector chunks stay resident in shared memory
     int n_refine;     // refinement passes of the tensor-core projection
     const unsigned char *tcA;   // arranged P_eta chunks for the current cluster size
     const int64_t *tc_off;      // byte offset of each shape's chunks in tcA
@@ -188,6 +197,7 @@ struct Plan {
     int csize = 1;        // CTAs per instance
     int threads = kDefaultThreads;
     int p_rows = 0;       // rows of P_eta staged per CTA (dense projection), 0 = read from global
+    int tc_res = 0;       // tensor-core projector chunks resident in shared memory
     size_t smem_fwd = 0;  // dynamic shared memory of the forward launch
     size_t smem_res = 0;  // and of the residual launch
     size_t smem_bwd = 0;  // and of the adjoint launch (0: does not fit)

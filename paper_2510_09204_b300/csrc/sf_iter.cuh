@@ -138,7 +138,7 @@ struct Cta {
     T *Pdev, *Pdif, *Bdev, *Bdif, *mv, *pm, *mb;
     int need_b;
     // tensor-core projection (FP32 kernels, dense mode)
-    int tcm, tc_nK, tc_nT, tc_na, tc_es, tc_bbytes, tc_sbo_b;
+    int tcm, tc_nK, tc_nT, tc_na, tc_es, tc_bbytes, tc_sbo_b, tc_res;
     unsigned char *tc_ring, *tc_B;
     uint64_t *tc_bar;          // full[2], empty[2], done
     int *tc_flag;              // sticky failure flag
@@ -206,8 +206,9 @@ struct Cta {
             const int kpad = tc_nK * tc_kc(tcm);
             tc_bbytes = 16 * kpad * tc_es;
             tc_sbo_b = (kpad * tc_es / 16) * 128;
+            tc_res = A.tc_res;
             tc_ring = smem_raw;
-            tc_B = tc_ring + 2 * kTcChunkBytes * tc_na;
+            tc_B = tc_ring + (int64_t)tc_stages(tcm, N, C, tc_res) * kTcChunkBytes * tc_na;
             unsigned char *bars = tc_B + (int64_t)tc_bbytes * tc_na + tc_bbytes + 1024;
             tc_bar = reinterpret_cast<uint64_t *>(bars);
             tc_flag = reinterpret_cast<int *>(bars + 40);
@@ -220,10 +221,22 @@ struct Cta {
                 for (int k = 0; k < H; ++k) acc += W[k * nxi + u] * W[k * nxi + vv];
                 wtw[e] = acc;
             }
+            tc_fw0 = tc_fw1 = tc_ld0 = tc_ld1 = tc_ec0 = tc_ec1 = 0;
             if (tid == 0) {
                 for (int b = 0; b < 5; ++b) tc::mbar_init(tc_bar + b, 1);
                 *tc_flag = 0;
                 tc::fence_barrier_init();
+                if (tc_res) {   // every chunk of this CTA's rows, once, on barrier 0
+                    const int items = tc_nT * tc_nK;
+                    const uint32_t stage_bytes = (uint32_t)(tc_na * kTcChunkBytes);
+                    tc::mbar_arrive_expect_tx(tc_bar, (uint32_t)items * stage_bytes);
+                    for (int w = 0; w < items; ++w)
+                        tc::bulk_g2s(tc_ring + (int64_t)w * stage_bytes, tc_src + (int64_t)w * stage_bytes, stage_bytes,
+                                     tc_bar);
+                    tc_ld0 = 1;
+                    if (tc::mbar_wait(tc_bar, 0, kWaitLimit)) tc_fw0 = 1;
+                    else *tc_flag = 1;
+                }
             }
             tmem_cols = 32;
             while (tmem_cols < (uint32_t)(16 * tc_nT)) tmem_cols <<= 1;
@@ -236,7 +249,6 @@ struct Cta {
             tc::fence_after_sync();
             tmem_base = *tc_slot;
             tc_done = 0;
-            tc_fw0 = tc_fw1 = tc_ld0 = tc_ld1 = tc_ec0 = tc_ec1 = 0;
         }
     }
 
@@ -601,23 +613,9 @@ struct Cta {
                 const uint32_t idesc = tc::instr_desc(tcm == 1 ? 2u : 1u, 128, 16);
                 const uint32_t ring0 = tc::smem_u32(tc_ring), b0 = tc::smem_u32(tc_B);
                 bool bad = false;
-                for (int w = 0; w < items && w < 2; ++w) {
-                    tc::mbar_arrive_expect_tx(tc_bar + w, stage_bytes);
-                    tc::bulk_g2s(tc_ring + w * stage_bytes, tc_src + (int64_t)w * stage_bytes, stage_bytes, tc_bar + w);
-                    if (w) ++tc_ld1; else ++tc_ld0;
-                }
-                for (int w = 0; w < items; ++w) {
-                    const int st = w & 1;
-                    const uint32_t fw = st ? tc_fw1 : tc_fw0;
-                    if (!tc::mbar_wait(tc_bar + st, fw & 1, kWaitLimit)) {
-                        bad = true;
-                        break;
-                    }
-                    if (st) ++tc_fw1; else ++tc_fw0;
-                    tc::fence_after_sync();
-                    const int t = w / tc_nK, kc = w - t * tc_nK;
-                    const uint32_t d_tmem = tmem_base + 16u * t;
-                    const uint32_t a_hi = ring0 + st * stage_bytes, a_lo = a_hi + kTcChunkBytes;
+                // one k-chunk of one 128-row tile: 4 MMAs of K = 32 bytes (x3 for BF16 x3)
+                auto issue = [&](uint32_t a_hi, int t, int kc) {
+                    const uint32_t d_tmem = tmem_base + 16u * t, a_lo = a_hi + kTcChunkBytes;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const uint64_t ad = tc::smem_desc(a_hi + 256u * j, 128, 1024);
@@ -636,6 +634,30 @@ struct Cta {
                             }
                         }
                     }
+                };
+                if (tc_res) {   // resident chunks: no waits between the MMAs
+                    tc::fence_after_sync();
+                    for (int w = 0; w < items; ++w) {
+                        const int t = w / tc_nK;
+                        issue(ring0 + (uint32_t)w * stage_bytes, t, w - t * tc_nK);
+                    }
+                }
+                for (int w = 0; w < items && w < 2 && !tc_res; ++w) {
+                    tc::mbar_arrive_expect_tx(tc_bar + w, stage_bytes);
+                    tc::bulk_g2s(tc_ring + w * stage_bytes, tc_src + (int64_t)w * stage_bytes, stage_bytes, tc_bar + w);
+                    if (w) ++tc_ld1; else ++tc_ld0;
+                }
+                for (int w = 0; w < items && !tc_res; ++w) {
+                    const int st = w & 1;
+                    const uint32_t fw = st ? tc_fw1 : tc_fw0;
+                    if (!tc::mbar_wait(tc_bar + st, fw & 1, kWaitLimit)) {
+                        bad = true;
+                        break;
+                    }
+                    if (st) ++tc_fw1; else ++tc_fw0;
+                    tc::fence_after_sync();
+                    const int t = w / tc_nK;
+                    issue(ring0 + st * stage_bytes, t, w - t * tc_nK);
                     tc::mma_commit(tc_bar + 2 + st);
                     if (st) ++tc_ec1; else ++tc_ec0;
                     if (w + 2 < items) {

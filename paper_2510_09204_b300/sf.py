@@ -192,12 +192,16 @@ class SFSolver:
         self._keep = (data, xi_cand, xi0, lam0)
         return xi_out, lam_out, (resid if want_resid else None)
 
-    def backward(self, g_xi_out, g_lam_out=None, g_rp2=None, want_xi0=True, want_lam0=True, stream=None):
-        """sf_solve_backward: returns (g_xi_cand, g_xi0, g_lam0)."""
+    def backward(self, g_xi_out, g_lam_out=None, g_rp2=None, want_xi0=True, want_lam0=True, out=None, stream=None):
+        """sf_solve_backward: returns (g_xi_cand, g_xi0, g_lam0).  ``out``: optional
+        preallocated (g_xi_cand, g_xi0, g_lam0) tensors (None entries are skipped)."""
         ref = g_xi_out
-        g_xc = torch.empty_like(ref)
-        g_x0 = torch.empty_like(ref) if want_xi0 else None
-        g_l0 = torch.empty_like(ref) if want_lam0 else None
+        if out is not None:
+            g_xc, g_x0, g_l0 = out
+        else:
+            g_xc = torch.empty_like(ref)
+            g_x0 = torch.empty_like(ref) if want_xi0 else None
+            g_l0 = torch.empty_like(ref) if want_lam0 else None
         _check(lib().sf_solve_backward(self.h, _ptr(g_xi_out), _ptr(g_lam_out), _ptr(g_rp2), _ptr(g_xc),
                                        _ptr(g_x0), _ptr(g_l0), _stream(stream)), "sf_solve_backward")
         return g_xc, g_x0, g_l0
