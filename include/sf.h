@@ -203,7 +203,8 @@ int sf_shape_operator(const sf_handle *h, int32_t inst, int32_t which, double *h
  *  cluster   CTAs that share one instance (a thread-block cluster, each CTA taking a
  *            contiguous share of the timesteps), 1..8, or 0 for the automatic choice
  *            (enough clusters to cover the SMs)
- *  threads   threads per CTA, a multiple of 32 in 64..512, or 0 for 512
+ *  threads   threads per CTA, a multiple of 32 in 64..512 (SF_FP64) or 64..1024 (the
+ *            FP32-based precisions), or 0 for 512
  * Results do not depend on the geometry beyond rounding order.  Errors: SF_EINVAL,
  * SF_EUNSUPPORTED (an instance does not fit in shared memory with this geometry).
  */
@@ -211,7 +212,7 @@ int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads);
 
 /*
  * sf_autotune — time each candidate launch geometry (cluster 1, 2, 4, 8 x threads
- * 128, 256, 512 that fit) on this handle's own batch with `iters` iterations of
+ * 128, 256, 512, 1024 that fit) on this handle's own batch with `iters` iterations of
  * sf_solve (CUDA events on `stream`, best of `reps` runs), keep the fastest and
  * return it.  Allocates and frees temporary output buffers; results of later solves
  * do not depend on the choice beyond rounding order.  The choice is also remembered
@@ -225,6 +226,27 @@ int sf_autotune(sf_handle *h, const sf_instance_data *data, const void *xi_cand,
 
 /* sf_get_launch — the geometry in use: cluster, threads, staged projection rows. */
 int sf_get_launch(const sf_handle *h, int32_t *cluster, int32_t *threads, int32_t *p_rows);
+
+/* Options of sf_set_option / sf_get_option */
+enum {
+    SF_OPT_CULL = 1   /* row culling: 1 (default) loops, per chunk of timesteps, over the
+                         partners and obstacles whose bounding boxes come within the
+                         activity threshold of the robot's box (steps alpha..d of the
+                         iteration, and their adjoint); 0 loops over all of them.  The
+                         two give identical bits: a culled row is inactive throughout
+                         the chunk and contributes nothing.  Culling is dropped silently
+                         when its lists do not fit in shared memory.                   */
+};
+
+/*
+ * sf_set_option — set an option (SF_OPT_*) and re-plan the launch with the current
+ * geometry (synchronises the device).  Errors: SF_EINVAL (unknown option or value),
+ * SF_EUNSUPPORTED (the re-plan does not fit).
+ * sf_get_option — the option's effective value in the current plan (for SF_OPT_CULL,
+ * 0 when culling was requested but does not fit).
+ */
+int sf_set_option(sf_handle *h, int32_t option, int32_t value);
+int sf_get_option(const sf_handle *h, int32_t option, int32_t *value);
 
 /* Kernel timing slots of sf_kernel_times */
 enum { SF_KT_FORWARD = 0, SF_KT_RESIDUAL = 1, SF_KT_BACKWARD = 2, SF_NKT = 3 };

@@ -61,6 +61,7 @@ struct sf_handle {
     DevBuf seg;                        // adjoint: recomputed iterates of a checkpoint segment
     DevBuf tcA, tcoff;                 // tensor-core chunks of P_eta for the current cluster size
     int tc_mode = 0, tc_c = 0;
+    int cull_req = 1;                  // culled row loops (sf_set_option SF_OPT_CULL)
     int n_slots = 0;
     int64_t xi_total = 0;
     // launch configuration
@@ -100,7 +101,8 @@ static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SF_OK : (e == 
 
 
 int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
-                     int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode)
+                     int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode,
+                     int cull_req)
 {
     if (proj != SF_PROJ_DENSE) tc_mode = 0;
     Plan p;
@@ -110,6 +112,15 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     int C = csize_req > 0 ? csize_req : std::max(1, num_sms / std::max(1, n_inst));
     C = std::max(1, std::min(std::min(C, kMaxCluster), minH));
     p.csize = C;
+    // culled row loops when the candidate lists fit beside a chunk of at least 8 timesteps
+    int cull = cull_req ? 1 : 0;
+    for (int i = 0; i < n_inst && cull; ++i) {
+        const int h8 = std::min((H[i] + C - 1) / C, 8);
+        const size_t b = (size_t)std::max(forward_carve(nd, nxi, H[i], n[i], nobs[i], h8, 0, esz, tc_mode, 2, 1).total,
+                                          backward_carve(nd, nxi, H[i], n[i], nobs[i], h8, 0, esz, tc_mode, 2, 1).total) * esz;
+        if (b > (size_t)optin || n[i] > 65535 - 8 || nobs[i] > 65535 - 8) cull = 0;
+    }
+    p.cull = cull;
     size_t need = 0, need_r = 0;
     int maxL = 0;
     bool res_ok = tc_mode != 0;
@@ -119,7 +130,7 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
         int hc = own;
         if (tc_mode && tc_ntiles(n[i] * nxi, C) > 8) return SF_EUNSUPPORTED;   // 8 x 128 rows per CTA at most
         auto bytes = [&](int h, int rows) {
-            return (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz, tc_mode).total * esz;
+            return (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total * esz;
         };
         while (hc > 1 && bytes(hc, 0) > (size_t)optin) --hc;
         if (bytes(hc, 0) > (size_t)optin) return SF_EUNSUPPORTED;
@@ -127,8 +138,8 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
             const int st = tc_stages(tc_mode, n[i] * nxi, C, 1);
             int hr = own;
             auto rbytes = [&](int h) {
-                return (size_t)std::max(forward_carve(nd, nxi, H[i], n[i], nobs[i], h, 0, esz, tc_mode, st).total,
-                                        backward_carve(nd, nxi, H[i], n[i], nobs[i], h, 0, esz, tc_mode, st).total) * esz;
+                return (size_t)std::max(forward_carve(nd, nxi, H[i], n[i], nobs[i], h, 0, esz, tc_mode, st, cull).total,
+                                        backward_carve(nd, nxi, H[i], n[i], nobs[i], h, 0, esz, tc_mode, st, cull).total) * esz;
             };
             while (hr > 1 && rbytes(hr) > (size_t)optin) --hr;
             if (rbytes(hr) > (size_t)optin || hr < std::min(own, 8)) res_ok = false;
@@ -144,7 +155,7 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     if (proj == SF_PROJ_DENSE && !tc_mode) {
         size_t with_p = 0;
         for (int i = 0; i < n_inst; ++i)
-            with_p = std::max(with_p, (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], maxL, esz).total * esz);
+            with_p = std::max(with_p, (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], maxL, esz, 0, 2, cull).total * esz);
         if (with_p <= (size_t)optin) {
             p.p_rows = maxL;
             need = with_p;
@@ -156,7 +167,7 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
         for (int i = 0; i < n_inst; ++i) {
             hc_out[i] = hc_res[i];
             need = std::max(need, (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], 0, esz, tc_mode,
-                                                        tc_stages(tc_mode, n[i] * nxi, C, 1)).total * esz);
+                                                        tc_stages(tc_mode, n[i] * nxi, C, 1), cull).total * esz);
         }
     }
     p.smem_fwd = need;
@@ -164,7 +175,7 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     size_t need_b = 0;
     for (int i = 0; i < n_inst; ++i)
         need_b = std::max(need_b, (size_t)backward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], p.p_rows, esz, tc_mode,
-                                                         tc_stages(tc_mode, n[i] * nxi, C, p.tc_res)).total * esz);
+                                                         tc_stages(tc_mode, n[i] * nxi, C, p.tc_res), cull).total * esz);
     p.smem_bwd = need_b <= (size_t)optin ? need_b : 0;
     *out = p;
     return SF_OK;
@@ -369,9 +380,9 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
             }
         }
         int prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                               h->smem_optin, c0, t0, &h->plan, h->hc.data(), h->tc_mode);
+                               h->smem_optin, c0, t0, &h->plan, h->hc.data(), h->tc_mode, h->cull_req);
         if (prc && c0) prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                                          h->smem_optin, 0, kDefaultThreads, &h->plan, h->hc.data(), h->tc_mode);
+                                          h->smem_optin, 0, kDefaultThreads, &h->plan, h->hc.data(), h->tc_mode, h->cull_req);
         if (prc) { destroy_all(h); delete h; return prc; }
     }
 
@@ -515,6 +526,7 @@ static FwdArgs<T> fwd_args(const sf_handle *h, const void *bnd, const void *obs,
     a.status = (int32_t *)h->status_dev.p;
     a.tc_mode = h->tc_mode;
     a.tc_res = h->plan.tc_res;
+    a.cull = h->plan.cull;
     a.n_refine = h->tc_mode ? h->d.n_refine : 0;
     a.tcA = (const unsigned char *)h->tcA.p;
     a.tc_off = (const int64_t *)h->tcoff.p;
@@ -652,7 +664,7 @@ extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
     }
     Plan p;
     int rc = plan_forward(h->d.n_d, h->d.n_xi, h->esz, h->d.proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                          h->smem_optin, cluster, threads ? threads : kDefaultThreads, &p, hc.data(), h->tc_mode);
+                          h->smem_optin, cluster, threads ? threads : kDefaultThreads, &p, hc.data(), h->tc_mode, h->cull_req);
     if (rc) return rc;
     SF_TRY(cudaDeviceSynchronize());
     h->plan = p;
@@ -737,6 +749,30 @@ extern "C" int sf_get_launch(const sf_handle *h, int32_t *cluster, int32_t *thre
     if (threads) *threads = h->plan.threads;
     if (p_rows) *p_rows = h->plan.p_rows;
     return SF_OK;
+}
+
+extern "C" int sf_set_option(sf_handle *h, int32_t option, int32_t value)
+{
+    if (!h) return SF_EINVAL;
+    if (option == SF_OPT_CULL) {
+        if (value != 0 && value != 1) return SF_EINVAL;
+        const int keep = h->cull_req;
+        h->cull_req = value;
+        const int rc = sf_set_launch(h, h->plan.csize, h->plan.threads);
+        if (rc) h->cull_req = keep;
+        return rc;
+    }
+    return SF_EINVAL;
+}
+
+extern "C" int sf_get_option(const sf_handle *h, int32_t option, int32_t *value)
+{
+    if (!h || !value) return SF_EINVAL;
+    if (option == SF_OPT_CULL) {
+        *value = h->plan.cull;
+        return SF_OK;
+    }
+    return SF_EINVAL;
 }
 
 extern "C" int sf_profile(sf_handle *h, int32_t enable)

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     const int ii = A.order ? A.order[w] : w;
     const Inst<T> I0 = A.inst[ii];
     const BwdCarve cv = backward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
-                                    tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res));
+                                    tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
     Cta<T, ND, TC> X;
     X.init(A, smem_raw, cv.f, ii, cr, C);
     X.load_constants(A, A.p_rows);
@@ -65,8 +65,10 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
         for (int k0 = X.k_lo; k0 < X.k_hi; k0 += X.hc) {
             const int hcc = min(X.hc, X.k_hi - k0);
             __syncthreads();
+            X.begin_chunk();
             X.positions(k0, hcc, X.xb);
-            __syncthreads();
+            X.sync_lists();
+            X.cull_lists(k0, hcc);
             X.rows_adjoint(k0, hcc, Rs, wseed);
             __syncthreads();
             X.wt_acc(k0, hcc, X.Rb, gme);
@@ -131,9 +133,11 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             for (int k0 = X.k_lo; k0 < X.k_hi; k0 += X.hc) {
                 const int hcc = min(X.hc, X.k_hi - k0);
                 __syncthreads();
+                X.begin_chunk();
                 X.positions(k0, hcc, xl);
                 X.wvec(k0, hcc, gs, Rs);
-                __syncthreads();
+                X.sync_lists();
+                X.cull_lists(k0, hcc);
                 X.rows_adjoint(k0, hcc, Rs, T(0));
                 __syncthreads();
                 X.wt_acc(k0, hcc, X.Rb, gme);

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
     const int ii = A.order ? A.order[w] : w;
     const Inst<T> I0 = A.inst[ii];
     const FwdCarve cv = forward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
-                                    tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res));
+                                    tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
     Cta<T, ND, TC> X;
     X.init(A, smem_raw, cv, ii, cr, C);
     X.load_constants(A, A.p_rows);

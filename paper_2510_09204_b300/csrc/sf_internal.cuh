@@ -71,8 +71,13 @@ __host__ __device__ inline int64_t tc_smem_bytes(int mode, int N, int stages)
 // Shared-memory carve of the forward kernel, in elements of T.  Every region starts on a
 // 32-byte boundary.  Host and kernel both call forward_carve, so they cannot disagree.
 struct FwdCarve {
-    int64_t W, xb, lam, xc, v, gp, dl, dd, rr, wtw, pb, Rb, ob, bd, db, sx, red, Ps, total;
+    int64_t W, xb, lam, xc, v, gp, dl, dd, rr, wtw, pb, Rb, ob, bd, db, sx, red, Ps, bb, os, lp, lo, lc, total;
 };
+
+// Candidate lists of the culled row loops: per robot, the partners and obstacles whose
+// bounding boxes over the chunk come within reach, padded to a multiple of four.
+__host__ __device__ inline int cull_lp(int n) { return (n + 3) / 4 * 4 + 4; }          // partner list stride
+__host__ __device__ inline int cull_lo(int nobs) { return (nobs + 3) / 4 * 4 + 4; }    // obstacle list stride
 
 __host__ __device__ inline int64_t carve_round(int64_t cnt, int esz)
 {
@@ -84,7 +89,7 @@ __host__ __device__ inline int64_t carve_round(int64_t cnt, int esz)
 // p_rows: rows of P_eta staged in shared memory (0: read from global memory); tc_mode,
 // tc_st: tensor-core projection mode and A ring stages.
 __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
-                                                  int tc_mode = 0, int tc_st = 2)
+                                                  int tc_mode = 0, int tc_st = 2, int cull = 0)
 {
     const int64_t N = (int64_t)n * nxi, NN = nd * N, ndp = nd == 2 ? 2 : 4;
     FwdCarve c;
@@ -100,14 +105,23 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n,
     c.rr = o;  o += carve_round(tc_mode ? NN : 0, esz);           // refinement residual (tensor cores)
     c.wtw = o; o += carve_round(tc_mode ? (int64_t)nxi * nxi + nd * nxi : 0, esz);   // W'W and robot sums
     const int64_t npad = (n + 3) / 4 * 4, opad = (nobs + 3) / 4 * 4;
-    c.pb = o;  o += carve_round(npad * hc * ndp, esz);            // positions [i][k] as vectors (+ far dummies)
+    c.pb = o;  o += carve_round((npad + 4) * hc * ndp, esz);      // positions [i][k] as vectors (+ far dummies)
     c.Rb = o;  o += carve_round((int64_t)nd * n * hc, esz);       // row sums R [ax][i][k]
-    c.ob = o;  o += carve_round(opad * 8, esz);                   // obstacle records (+ dummies)
+    c.ob = o;  o += carve_round((opad + 4) * 8, esz);             // obstacle records (+ dummies)
     c.bd = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b
     c.db = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b - A xi_bar^0
     c.sx = o;  o += carve_round(2 * (int64_t)nxi * nxi + 4 * nxi + 2 * (int64_t)nd * nxi + 2 * nd, esz);
     c.red = o; o += carve_round(4 * 32, esz);
     c.Ps = o;  o += carve_round((int64_t)p_rows * N, esz);
+    // culling, per segment of at most 32 timesteps: boxes [ax][lo, hi][segment][robot |
+    // dynamic obstacle], obstacle columns [x, y, z, a_o^2, kz_o][m] (both read one entry
+    // per lane), lists [segment][robot] (16-bit), counts
+    const int64_t ns = (hc + 31) / 32;                            // culling segments of a chunk
+    c.bb = o;  o += carve_round(cull ? ns * (n + nobs) * nd * 2 : 0, esz);
+    c.os = o;  o += carve_round(cull ? (int64_t)nobs * 5 : 0, esz);
+    c.lp = o;  o += carve_round(cull ? (ns * n * cull_lp(n) * 2 + esz - 1) / esz : 0, esz);
+    c.lo = o;  o += carve_round(cull ? (ns * n * cull_lo(nobs) * 2 + esz - 1) / esz : 0, esz);
+    c.lc = o;  o += carve_round(cull ? (ns * n * 2 * 4 + esz - 1) / esz : 0, esz);
     c.total = o;
     return c;
 }
@@ -120,16 +134,16 @@ struct BwdCarve {
 };
 
 __host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
-                                                   int tc_mode = 0, int tc_st = 2)
+                                                   int tc_mode = 0, int tc_st = 2, int cull = 0)
 {
     BwdCarve b;
-    b.f = forward_carve(nd, nxi, H, n, nobs, hc, p_rows, esz, tc_mode, tc_st);
+    b.f = forward_carve(nd, nxi, H, n, nobs, hc, p_rows, esz, tc_mode, tc_st, cull);
     const int64_t NN = (int64_t)nd * n * nxi, npad = (n + 3) / 4 * 4, ndp = nd == 2 ? 2 : 4;
     int64_t o = b.f.total;
     b.xs = o; o += carve_round(NN, esz);
     b.ls = o; o += carve_round(NN, esz);
     b.cs = o; o += carve_round(NN, esz);
-    b.Rs = o; o += carve_round(npad * hc * ndp, esz);
+    b.Rs = o; o += carve_round((npad + 4) * hc * ndp, esz);
     b.total = o;
     return b;
 }
@@ -141,6 +155,7 @@ struct FwdArgs {
     int p_rows;       // rows of P_eta per CTA staged in shared memory (dense; 0 = global)
     int tc_mode;      // tensor-core projection: 0 none, 1 TF32, 2 BF16, 3 BF16 x3
     int tc_res;       // the CTA's projector chunks stay resident in shared memory
+    int cull;         // row loops over per-chunk candidate lists (bounding-box culling)
     int n_refine;     // refinement passes of the tensor-core projection
     const unsigned char *tcA;   // arranged P_eta chunks for the current cluster size
     const int64_t *tc_off;      // byte offset of each shape's chunks in tcA
@@ -198,6 +213,7 @@ struct Plan {
     int threads = kDefaultThreads;
     int p_rows = 0;       // rows of P_eta staged per CTA (dense projection), 0 = read from global
     int tc_res = 0;       // tensor-core projector chunks resident in shared memory
+    int cull = 0;         // culled row loops (the candidate lists fit in shared memory)
     size_t smem_fwd = 0;  // dynamic shared memory of the forward launch
     size_t smem_res = 0;  // and of the residual launch
     size_t smem_bwd = 0;  // and of the adjoint launch (0: does not fit)
@@ -207,7 +223,8 @@ struct Plan {
 // hc_out[i] and the shared-memory sizes.  Returns SF_OK or SF_EUNSUPPORTED when an
 // instance cannot fit in `optin` bytes of shared memory.
 int plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
-                 int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode = 0);
+                 int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode = 0,
+                 int cull_req = 1);
 
 // Arranges every shape's P_eta (FP64 pool) into the tensor-core chunk layout for cluster
 // size C: per shape [C][tiles][K chunks][128 x 128 bytes] (x 2 for the BF16 x3 low part).

@@ -137,6 +137,14 @@ struct Cta {
     int64_t gstride;
     T *Pdev, *Pdif, *Bdev, *Bdif, *mv, *pm, *mb;
     int need_b;
+    // culled row loops: boxes, candidate lists (partners, obstacles) and their counts
+    T *bbx, *osa;
+    unsigned short *lpl, *lol;
+    int *lcn;
+    int cull, LPs, LOs, NBX;
+    int lv, need;     // lists valid for the current chunk; rebuild asked (block-uniform)
+    bool esc;         // this thread saw a position outside its robot's inflated box
+    T cdel;           // inflation of the robots' boxes
     // tensor-core projection (FP32 kernels, dense mode)
     int tcm, tc_nK, tc_nT, tc_na, tc_es, tc_bbytes, tc_sbo_b, tc_res;
     unsigned char *tc_ring, *tc_B;
@@ -180,6 +188,19 @@ struct Cta {
         Rb = sm + cv.Rb; ob = sm + cv.ob;
         n_refine = A.n_refine;
         n_obs_ = I.n_obs;
+        cull = A.cull;
+        bbx = sm + cv.bb;
+        osa = sm + cv.os;
+        lpl = reinterpret_cast<unsigned short *>(sm + cv.lp);
+        lol = reinterpret_cast<unsigned short *>(sm + cv.lo);
+        lcn = reinterpret_cast<int *>(sm + cv.lc);
+        LPs = cull_lp(n);
+        LOs = cull_lo(nobs);
+        NBX = n + nobs;
+        lv = 0;
+        need = 0;
+        esc = false;
+        cdel = T(0.5) * fmax(I.a, I.b);
         bd = sm + cv.bd; db = sm + cv.db; sx = sm + cv.sx; red = sm + cv.red; Ps = sm + cv.Ps;
         P = reinterpret_cast<VP *>(sm + cv.pb);
         gstride = carve_round(NN + 4, (int)sizeof(T));
@@ -276,7 +297,7 @@ struct Cta {
         const T *xcg = A.xc + I.off_xi;
         for (int e = tid; e < NN; e += nt) xc[e] = xcg[e];
         for (int e = tid; e < ND * n * 2; e += nt) bd[e] = A.bnd[I.off_bnd + e];
-        for (int m = nobs + tid; m < opad; m += nt) {   // padding records: far away, zero radius
+        for (int m = nobs + tid; m < opad + 4; m += nt) {   // padding records: far away, zero radius
             T *o = ob + 8 * m;
             for (int q = 0; q < 8; ++q) o[q] = T(0);
             for (int ax = 0; ax < ND; ++ax) o[ax] = Far<T>::v;
@@ -291,6 +312,11 @@ struct Cta {
             o[5] = T(1) / (ao * ao);
             o[6] = ao;
             o[7] = bo;
+            if (cull) {
+                for (int ax = 0; ax < 3; ++ax) osa[ax * nobs + m] = o[ax];
+                osa[3 * nobs + m] = o[3];
+                osa[4 * nobs + m] = o[4];
+            }
         }
         const T *Pg = A.P + S.off_P;
         if (dense && p_rows > 0)
@@ -331,10 +357,12 @@ struct Cta {
         __syncthreads();
     }
 
-    // out[i][kl][ax] = sum_c W[k0 + kl][c] coeff[ax][i][c] (vector layout, one (ax, i, kl) per thread)
-    __device__ __forceinline__ void wvec(int k0, int hcc, const T *coeff, VP *out)
+    // out[i][kl][ax] = sum_c W[k0 + kl][c] coeff[ax][i][c] (vector layout, one (ax, i, kl) per
+    // thread).  chk: also note in esc whether a value leaves its robot's inflated box.
+    __device__ __forceinline__ void wvec(int k0, int hcc, const T *coeff, VP *out, bool chk = false)
     {
         T *o = reinterpret_cast<T *>(out);
+        const int S = seg_len(hcc), ns = nseg_of(hcc);
         for (int e = tid; e < ND * n * hcc; e += nt) {
             const int r = e / hcc, kl = e - r * hcc, ax = r / n, i = r - ax * n;
             const T *wr = W + (k0 + kl) * nxi;
@@ -347,15 +375,43 @@ struct Cta {
                 s2 += wr[c + 2] * xr[c + 2];
             }
             for (; c < nxi; ++c) s0 += wr[c] * xr[c];
-            o[(i * hcc + kl) * NDP<ND>::v + ax] = (s0 + s1) + s2;
+            const T val = (s0 + s1) + s2;
+            o[(i * hcc + kl) * NDP<ND>::v + ax] = val;
+            if (chk) {
+                const int sg = kl / S;
+                if (!(val >= bbx[((2 * ax) * ns + sg) * NBX + i] && val <= bbx[((2 * ax + 1) * ns + sg) * NBX + i]))
+                    esc = true;
+            }
+        }
+    }
+
+    // Segments of a chunk for the culling boxes: at most 32 timesteps each.
+    __device__ __forceinline__ static int nseg_of(int hcc) { return (hcc + 31) >> 5; }
+    __device__ __forceinline__ static int seg_len(int hcc) { return (hcc + nseg_of(hcc) - 1) / nseg_of(hcc); }
+
+    // Call before positions() of each chunk: lists of another chunk are not reused.
+    __device__ __forceinline__ void begin_chunk()
+    {
+        if (k_hi - k_lo > hc) lv = 0;
+    }
+
+    // The barrier after positions(); with culling it also decides (block-uniformly)
+    // whether the candidate lists must be rebuilt: none yet, or a position left its box.
+    __device__ __forceinline__ void sync_lists()
+    {
+        if (cull) {
+            need = __syncthreads_or(esc || !lv);
+            esc = false;
+        } else {
+            __syncthreads();
         }
     }
 
     // positions of coeff for the chunk, robots padded with far stand-ins
     __device__ __forceinline__ void positions(int k0, int hcc, const T *coeff)
     {
-        wvec(k0, hcc, coeff, P);
-        for (int e = n * hcc + tid; e < npad * hcc; e += nt) {
+        wvec(k0, hcc, coeff, P, cull && lv);
+        for (int e = n * hcc + tid; e < (npad + 4) * hcc; e += nt) {
             VP p;
 #pragma unroll
             for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = Far<T>::v;
@@ -383,12 +439,149 @@ struct Cta {
         }
     }
 
+    // Candidate lists of the chunk [k0, k0 + hcc), rebuilt after sync_lists() asked for it.
+    // The chunk is cut into segments of at most 32 timesteps.  Per segment, each robot's
+    // bounding box over the segment, inflated by cdel on every axis, and each dynamic
+    // obstacle's box; then per (segment, robot), in ascending order, the partners j != i
+    // and obstacles m whose boxes come within the activity threshold (relative margin
+    // 1e-5).  While every position stays inside its robot's inflated box (checked by
+    // positions()), a row that is not listed is inactive at every timestep of its segment:
+    // the culled loops add the same terms in the same order as the full ones.  Lists are
+    // padded to a multiple of four with the far stand-ins npad (robots) and opad
+    // (obstacles).  Ends with a barrier when it rebuilds.
+    __device__ __forceinline__ void cull_lists(int k0, int hcc)
+    {
+        if (!cull || !need) return;
+        const int lane = tid & 31, wp = tid >> 5, nw = nt >> 5;
+        const int nbox = n + (I.dyn ? nobs : 0), ns = nseg_of(hcc), S = seg_len(hcc);
+        // boxes: groups of 8 lanes per (segment, box), lane s8 taking timesteps s8, s8 + 8, ...
+        const int tasks = ns * nbox;
+        for (int base = wp * 4; base < tasks; base += nw * 4) {   // warp-uniform: full-mask shuffles
+            const int t = base + (lane >> 3), s8 = lane & 7;
+            const int sg = t / nbox, b = t - sg * nbox;
+            const int kb = sg * S, ke = min(hcc, kb + S);
+            T lo[ND], hi[ND];
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) {
+                lo[ax] = T(1e30);
+                hi[ax] = T(-1e30);
+            }
+            if (t < tasks)
+                for (int kl = kb + s8; kl < ke; kl += 8) {
+                    T x[ND];
+                    if (b < n) {
+                        const VP pv = P[b * hcc + kl];
+#pragma unroll
+                        for (int ax = 0; ax < ND; ++ax) x[ax] = pv.v[ax];
+                    } else {
+                        const T *c = obs_g + ((int64_t)(b - n) * H + k0 + kl) * ND;
+#pragma unroll
+                        for (int ax = 0; ax < ND; ++ax) x[ax] = c[ax];
+                    }
+#pragma unroll
+                    for (int ax = 0; ax < ND; ++ax) {
+                        lo[ax] = fmin(lo[ax], x[ax]);
+                        hi[ax] = fmax(hi[ax], x[ax]);
+                    }
+                }
+#pragma unroll
+            for (int o = 4; o; o >>= 1)
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax) {
+                    lo[ax] = fmin(lo[ax], __shfl_xor_sync(0xffffffffu, lo[ax], o));
+                    hi[ax] = fmax(hi[ax], __shfl_xor_sync(0xffffffffu, hi[ax], o));
+                }
+            if (s8 == 0 && t < tasks) {
+                const T dl = b < n ? cdel : T(0);
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax) {
+                    bbx[((2 * ax) * ns + sg) * NBX + b] = lo[ax] - dl;
+                    bbx[((2 * ax + 1) * ns + sg) * NBX + b] = hi[ax] + dl;
+                }
+            }
+        }
+        __syncthreads();
+        const T a2c = I.a * I.a * T(1.00001), kz = (I.a * I.a) * I.ib2;
+        for (int task = wp; task < ns * n; task += nw) {
+            const int sg = task / n, i = task - sg * n;
+            const T *bl = bbx + sg * NBX, *bh = bbx + (ns + sg) * NBX;   // axis ax at + 2 ax ns NBX
+            T lo[ND], hi[ND];
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) {
+                lo[ax] = bl[2 * ax * ns * NBX + i];
+                hi[ax] = bh[2 * ax * ns * NBX + i];
+            }
+            unsigned short *L = lpl + task * LPs;
+            int cp = 0;
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                const int j = j0 + lane;
+                bool c = false;
+                if (j < n && j != i) {
+                    T g[ND];
+#pragma unroll
+                    for (int ax = 0; ax < ND; ++ax)
+                        g[ax] = fmax(T(0), fmax(bl[2 * ax * ns * NBX + j] - hi[ax], lo[ax] - bh[2 * ax * ns * NBX + j]));
+                    c = qdist<T, ND>(g, kz) <= a2c;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, c);
+                if (c) L[cp + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)j;
+                cp += __popc(bal);
+            }
+            for (int u = cp + lane; u < ((cp + 3) & ~3); u += 32) L[u] = (unsigned short)npad;
+            unsigned short *M = lol + task * LOs;
+            int co = 0;
+            for (int m0 = 0; m0 < nobs; m0 += 32) {
+                const int m = m0 + lane;
+                bool c = false;
+                if (m < nobs) {
+                    T g[ND];
+#pragma unroll
+                    for (int ax = 0; ax < ND; ++ax) {
+                        T cl, ch;
+                        if (I.dyn) {
+                            cl = bl[2 * ax * ns * NBX + n + m];
+                            ch = bh[2 * ax * ns * NBX + n + m];
+                        } else {
+                            cl = ch = osa[ax * nobs + m];
+                        }
+                        g[ax] = fmax(T(0), fmax(cl - hi[ax], lo[ax] - ch));
+                    }
+                    T q = g[0] * g[0] + g[1] * g[1];
+                    if (ND == 3) q += osa[4 * nobs + m] * g[ND - 1] * g[ND - 1];
+                    c = q <= osa[3 * nobs + m] * T(1.00001);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, c);
+                if (c) M[co + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)m;
+                co += __popc(bal);
+            }
+            for (int u = co + lane; u < ((co + 3) & ~3); u += 32) M[u] = (unsigned short)opad;
+            if (lane == 0) {
+                lcn[2 * task] = cp;
+                lcn[2 * task + 1] = co;
+            }
+        }
+        __syncthreads();
+        lv = 1;
+    }
+
+    // Four partner (or obstacle) indices of block b of robot i's loop: the full loop's
+    // b*4 .. b*4+3, or the culled loop's list entries (far stand-ins past the count).
+    __device__ __forceinline__ void block_ids(const unsigned short *list, int cnt, int b4, int stand_in, int (&id)[4]) const
+    {
+        if (b4 < cnt) {
+            const ushort4 q = *reinterpret_cast<const ushort4 *>(list + b4);
+            id[0] = q.x; id[1] = q.y; id[2] = q.z; id[3] = q.w;
+        } else {
+            id[0] = id[1] = id[2] = id[3] = stand_in;
+        }
+    }
+
     // Rows of the items (i, k) of one chunk: R written to Rb[ax][i][kl].  Partners and
     // obstacles are tested four at a time; the warp votes once per block of four and takes
     // the rare active-row path only when one of its lanes needs it.
     __device__ __forceinline__ void rows(int k0, int hcc, T &rp2, T &mx2)
     {
-        const int items = n * hcc;
+        const int items = n * hcc, segS = seg_len(hcc);
         const T a2 = I.a * I.a, ia2 = I.ia2, kz = (I.a * I.a) * I.ib2;
         T tie_f[ND], tie_b[ND];   // r_1 of a coincident pair seen from the row's first / second robot
 #pragma unroll
@@ -408,13 +601,20 @@ struct Cta {
             T R[ND];
 #pragma unroll
             for (int ax = 0; ax < ND; ++ax) R[ax] = T(0);
+            const int task = (kl / segS) * n + i;   // culling lists of (segment, robot)
+            const int cp4 = cull ? (lcn[2 * task] + 3) & ~3 : 0, co4 = cull ? (lcn[2 * task + 1] + 3) & ~3 : 0;
+            const int jend = cull ? __reduce_max_sync(0xffffffffu, cp4) : npad;
+            const int mend = cull ? __reduce_max_sync(0xffffffffu, co4) : opad;
             // robot pairs: the row of pair (min(i,j), max(i,j)); j == i (q = 0) is excluded in
             // the slow path
-            for (int j0 = 0; j0 < npad; j0 += 4) {
+            for (int j0 = 0; j0 < jend; j0 += 4) {
+                int jj[4];
+                if (cull) block_ids(lpl + task * LPs, cp4, j0, npad, jj);
+                else { jj[0] = j0; jj[1] = j0 + 1; jj[2] = j0 + 2; jj[3] = j0 + 3; }
                 T d[4][ND], q[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const VP pj = P[(j0 + u) * hcc + kl];
+                    const VP pj = P[jj[u] * hcc + kl];
 #pragma unroll
                     for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - pj.v[ax];
                     q[u] = qdist<T, ND>(d[u], kz);
@@ -423,7 +623,7 @@ struct Cta {
                 if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int j = j0 + u;
+                        const int j = jj[u];
                         if (q[u] <= a2 && j != i) {
                             if (j > i) row_active<T, ND>(d[u], q[u], ia2, tie_f, R, rp2, mx2, true);
                             else row_active<T, ND>(d[u], q[u], ia2, tie_b, R, rp2, mx2, false);
@@ -432,11 +632,14 @@ struct Cta {
                 }
             }
             // obstacles
-            for (int m0 = 0; m0 < opad; m0 += 4) {
+            for (int m0 = 0; m0 < mend; m0 += 4) {
+                int mm[4];
+                if (cull) block_ids(lol + task * LOs, co4, m0, opad, mm);
+                else { mm[0] = m0; mm[1] = m0 + 1; mm[2] = m0 + 2; mm[3] = m0 + 3; }
                 T d[4][ND], q[4], lim[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int m = m0 + u;
+                    const int m = mm[u];
                     const Vec<T, 4> r0 = reinterpret_cast<const Vec<T, 4> *>(ob)[2 * m];
                     if (I.dyn && m < nobs) {
                         const T *c = obs_g + ((int64_t)m * H + k) * ND;
@@ -455,7 +658,7 @@ struct Cta {
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         if (q[u] <= lim[u]) {
-                            const int m = m0 + u;
+                            const int m = mm[u];
                             T tie[ND];
 #pragma unroll
                             for (int ax = 0; ax < ND; ++ax) tie[ax] = T(0);
@@ -493,7 +696,7 @@ struct Cta {
     __device__ __forceinline__ void rows_adjoint(int k0, int hcc, const VP *Rs, T seed_w)
     {
         const bool seed = seed_w != T(0);
-        const int items = n * hcc;
+        const int items = n * hcc, segS = seg_len(hcc);
         const T a2 = I.a * I.a, ia2 = I.ia2, ib2 = I.ib2, kz = (I.a * I.a) * I.ib2;
         for (int e0 = 0; e0 < items; e0 += nt) {
             const int e = e0 + tid;
@@ -511,11 +714,18 @@ struct Cta {
                 Ri[ax] = seed ? T(0) : Rs[i * hcc + kl].v[ax];
                 ps[ax] = T(0);
             }
-            for (int j0 = 0; j0 < npad; j0 += 4) {
+            const int task = (kl / segS) * n + i;   // culling lists of (segment, robot)
+            const int cp4 = cull ? (lcn[2 * task] + 3) & ~3 : 0, co4 = cull ? (lcn[2 * task + 1] + 3) & ~3 : 0;
+            const int jend = cull ? __reduce_max_sync(0xffffffffu, cp4) : npad;
+            const int mend = cull ? __reduce_max_sync(0xffffffffu, co4) : opad;
+            for (int j0 = 0; j0 < jend; j0 += 4) {
+                int jj[4];
+                if (cull) block_ids(lpl + task * LPs, cp4, j0, npad, jj);
+                else { jj[0] = j0; jj[1] = j0 + 1; jj[2] = j0 + 2; jj[3] = j0 + 3; }
                 T d[4][ND], q[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const VP pj = P[(j0 + u) * hcc + kl];
+                    const VP pj = P[jj[u] * hcc + kl];
 #pragma unroll
                     for (int ax = 0; ax < ND; ++ax) d[u][ax] = pi.v[ax] - pj.v[ax];
                     q[u] = qdist<T, ND>(d[u], kz);
@@ -524,7 +734,7 @@ struct Cta {
                 if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int j = j0 + u;
+                        const int j = jj[u];
                         if (q[u] <= a2 && j != i) {
                             T y[ND];
 #pragma unroll
@@ -534,11 +744,14 @@ struct Cta {
                     }
                 }
             }
-            for (int m0 = 0; m0 < opad; m0 += 4) {
+            for (int m0 = 0; m0 < mend; m0 += 4) {
+                int mm[4];
+                if (cull) block_ids(lol + task * LOs, co4, m0, opad, mm);
+                else { mm[0] = m0; mm[1] = m0 + 1; mm[2] = m0 + 2; mm[3] = m0 + 3; }
                 T d[4][ND], q[4], lim[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int m = m0 + u;
+                    const int m = mm[u];
                     const Vec<T, 4> r0 = reinterpret_cast<const Vec<T, 4> *>(ob)[2 * m];
                     if (I.dyn && m < nobs) {
                         const T *c = obs_g + ((int64_t)m * H + k) * ND;
@@ -557,7 +770,7 @@ struct Cta {
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         if (q[u] <= lim[u]) {
-                            const int m = m0 + u;
+                            const int m = mm[u];
                             const T iao = ob[8 * m + 5], ibo = ob[8 * m + 4] * ob[8 * m + 5];
                             row_adjoint<T, ND>(d[u], q[u], iao, ibo, Ri, seed_w, seed, ps);
                         }
@@ -838,8 +1051,10 @@ struct Cta {
         for (int k0 = k_lo; k0 < k_hi; k0 += hc) {
             const int hcc = min(hc, k_hi - k0);
             __syncthreads();
+            begin_chunk();
             positions(k0, hcc, xb);
-            __syncthreads();
+            sync_lists();
+            cull_lists(k0, hcc);
             rows(k0, hcc, rp2, mx2);
             __syncthreads();
             wt_acc(k0, hcc, Rb, gme);

@@ -218,6 +218,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
     a.n_inst = n_inst;
     a.csize = plan.csize;
     a.p_rows = 0;
+    a.cull = plan.cull;
     a.proj = SF_PROJ_STRUCTURED;
     a.rho = (float)rho;
     a.tol = 1e-3;

@@ -28,7 +28,8 @@ PROJECTIONS = {"dense": SF_PROJ_DENSE, "structured": SF_PROJ_STRUCTURED}
 # every symbol declared in include/sf.h
 EXPORTS = ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
            "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch",
-           "sf_get_launch", "sf_autotune", "sf_strerror", "sf_version")
+           "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_strerror", "sf_version")
+SF_OPT_CULL = 1
 SF_KT_FORWARD, SF_KT_RESIDUAL, SF_KT_BACKWARD, SF_NKT = range(4)
 
 
@@ -81,11 +82,13 @@ def lib(path: str | None = None):
         L.sf_autotune.argtypes = [vp, ct.POINTER(sf_instance_data), vp, i32, i32, vp, ct.POINTER(i32),
                                   ct.POINTER(i32), ct.POINTER(ct.c_float)]
         L.sf_get_launch.argtypes = [vp, ct.POINTER(i32), ct.POINTER(i32), ct.POINTER(i32)]
+        L.sf_set_option.argtypes = [vp, i32, i32]
+        L.sf_get_option.argtypes = [vp, i32, ct.POINTER(i32)]
         L.sf_strerror.argtypes = [i32]
         L.sf_strerror.restype = ct.c_char_p
         L.sf_version.restype = i32
         for f in ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
-                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch", "sf_autotune"):
+                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -217,6 +220,16 @@ class SFSolver:
         _check(lib().sf_autotune(self.h, ct.byref(dd), _ptr(xi_cand), int(iters), int(reps), _stream(stream),
                                  ct.byref(c), ct.byref(t), ct.byref(ms)), "sf_autotune")
         return c.value, t.value, ms.value
+
+    def set_option(self, option, value):
+        """sf_set_option (re-plans with the current geometry)."""
+        _check(lib().sf_set_option(self.h, int(option), int(value)), "sf_set_option")
+
+    def option(self, option):
+        """sf_get_option: the option's effective value in the current plan."""
+        v = ct.c_int32()
+        _check(lib().sf_get_option(self.h, int(option), ct.byref(v)), "sf_get_option")
+        return v.value
 
     def launch(self):
         """(cluster, threads, staged projection rows) in use."""
