@@ -1,6 +1,7 @@
 """Build the SF solver's shared library (``libsf.so``) in-tree with nvcc for sm_103a."""
 from __future__ import annotations
 
+import concurrent.futures
 import glob
 import os
 import subprocess
@@ -30,20 +31,37 @@ def stale(out: str = LIB) -> bool:
     return any(os.path.getmtime(f) > t for f in sources() + headers())
 
 
+def _run(cmd):
+    return subprocess.run(cmd, capture_output=True, text=True)
+
+
 def build(force: bool = False, verbose: bool = False, out: str = LIB, extra=()) -> str:
-    """Compile every .cu under csrc/ into one shared library; returns its path."""
+    """Compile every .cu under csrc/ (one object per file, in parallel) and link them into
+    one shared library; returns its path."""
     if not force and not stale(out):
         return out
-    cmd = [NVCC, "-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC", "-shared",
-           "-I", INCLUDE, "-I", CSRC, "-o", out, *sources(), *extra]
+    objdir = os.path.join(PKG, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    flags = [NVCC, "-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC, *extra]
     if verbose:
-        cmd += ["-Xptxas", "-v"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+        flags += ["-Xptxas", "-v"]
+    objs, cmds = [], []
+    for src in sources():
+        obj = os.path.join(objdir, os.path.splitext(os.path.basename(src))[0] + ".o")
+        objs.append(obj)
+        cmds.append(flags + ["-c", src, "-o", obj])
+    with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(_run, cmds))
+    for r in results:
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout + r.stderr)
+            raise RuntimeError("nvcc failed building %s" % out)
+        if verbose:
+            sys.stderr.write(r.stderr)
+    r = _run([NVCC, *ARCH, "-shared", "-o", out, *objs])
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building %s" % out)
-    if verbose:
-        sys.stderr.write(r.stderr)
+        raise RuntimeError("nvcc failed linking %s" % out)
     return out
 
 

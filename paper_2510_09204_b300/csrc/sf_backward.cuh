@@ -19,11 +19,12 @@
 // with J = dr_1/dDelta = (1 - s) I + s^3 Delta (M^-2 Delta)' on active rows and 0 on
 // inactive ones (derivative conventions of the kinks: the clamped branch counts as
 // active, Delta = 0 has zero derivative).
+#pragma once
 #include "sf_iter.cuh"
 
 namespace sf {
 
-template <typename T, int ND, int MAXT, bool TC>
+template <typename T, int ND, int MAXT, bool TC, int NXI>
 __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
 {
     using VP = Vec<T, NDP<ND>::v>;
@@ -34,9 +35,9 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     const int w = blockIdx.x / C;
     const int ii = A.order ? A.order[w] : w;
     const Inst<T> I0 = A.inst[ii];
-    const BwdCarve cv = backward_carve(ND, A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
+    const BwdCarve cv = backward_carve(ND, NXI > 0 ? NXI : A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
                                     tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
-    Cta<T, ND, TC> X;
+    Cta<T, ND, TC, NXI> X;
     X.init(A, smem_raw, cv.f, ii, cr, C);
     X.load_constants(A, A.p_rows);
     X.tc_setup(A, smem_raw);
@@ -162,38 +163,45 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
+// n_xi = 11 (the default basis) runs a specialisation with the coefficient count fixed at
+// compile time (FP32 kernels); other sizes, and FP64, the generic kernel.
+template <typename T, int ND, int MAXT, bool TC>
+static cudaError_t go_backward(const BwdArgs<T> &a, int nxi, int ni, int cs, int threads, size_t smem, cudaStream_t s)
+{
+    if (sizeof(T) == 4 && nxi == 11) return launch_cluster(k_backward<T, ND, MAXT, TC, sizeof(T) == 4 ? 11 : 0>, a, ni, cs, threads, smem, s);
+    return launch_cluster(k_backward<T, ND, MAXT, TC, 0>, a, ni, cs, threads, smem, s);
+}
+
+// Launch for one dimension: tensor-core projection or not, 512- or 1024-thread CTAs.
+template <typename T, int ND>
+cudaError_t launch_backward_nd(const BwdArgs<T> &a, int threads, size_t smem, cudaStream_t s)
+{
+    const FwdArgs<T> &f = a.f;
+    constexpr int big = sizeof(T) == 8 ? 512 : 1024;
+    constexpr bool tcok = sizeof(T) == 4;
+    const int ni = f.n_inst, cs = f.csize, nx = f.nxi;
+    if (f.tc_mode && tcok) {
+        if (threads > 512) return go_backward<T, ND, big, tcok>(a, nx, ni, cs, threads, smem, s);
+        return go_backward<T, ND, 512, tcok>(a, nx, ni, cs, threads, smem, s);
+    }
+    if (threads > 512) return go_backward<T, ND, big, false>(a, nx, ni, cs, threads, smem, s);
+    return go_backward<T, ND, 512, false>(a, nx, ni, cs, threads, smem, s);
+}
+
+// Each (precision, dimension) is instantiated in a translation unit of its own.
+extern template cudaError_t launch_backward_nd<float, 2>(const BwdArgs<float> &, int, size_t, cudaStream_t);
+extern template cudaError_t launch_backward_nd<float, 3>(const BwdArgs<float> &, int, size_t, cudaStream_t);
+extern template cudaError_t launch_backward_nd<double, 2>(const BwdArgs<double> &, int, size_t, cudaStream_t);
+extern template cudaError_t launch_backward_nd<double, 3>(const BwdArgs<double> &, int, size_t, cudaStream_t);
+
 template <typename T>
 static cudaError_t launch_backward_t(const BwdArgs<T> &a, int threads, size_t smem, cudaStream_t s)
 {
     const FwdArgs<T> &f = a.f;
     if (f.n_inst < 1 || f.csize < 1 || f.csize > kMaxCluster) return cudaErrorInvalidValue;
     if (threads > max_threads((int)sizeof(T))) return cudaErrorInvalidValue;
-    constexpr int big = sizeof(T) == 8 ? 512 : 1024;
-    constexpr bool tcok = sizeof(T) == 4;
-    const int ni = f.n_inst, cs = f.csize;
-    if (f.tc_mode && tcok) {
-        if (threads > 512) {
-            if (f.nd == 2) return launch_cluster(k_backward<T, 2, big, tcok>, a, ni, cs, threads, smem, s);
-            return launch_cluster(k_backward<T, 3, big, tcok>, a, ni, cs, threads, smem, s);
-        }
-        if (f.nd == 2) return launch_cluster(k_backward<T, 2, 512, tcok>, a, ni, cs, threads, smem, s);
-        return launch_cluster(k_backward<T, 3, 512, tcok>, a, ni, cs, threads, smem, s);
-    }
-    if (threads > 512) {
-        if (f.nd == 2) return launch_cluster(k_backward<T, 2, big, false>, a, ni, cs, threads, smem, s);
-        return launch_cluster(k_backward<T, 3, big, false>, a, ni, cs, threads, smem, s);
-    }
-    if (f.nd == 2) return launch_cluster(k_backward<T, 2, 512, false>, a, ni, cs, threads, smem, s);
-    return launch_cluster(k_backward<T, 3, 512, false>, a, ni, cs, threads, smem, s);
-}
-
-cudaError_t launch_backward(const BwdArgs<double> &a, int threads, size_t smem, cudaStream_t s)
-{
-    return launch_backward_t(a, threads, smem, s);
-}
-cudaError_t launch_backward(const BwdArgs<float> &a, int threads, size_t smem, cudaStream_t s)
-{
-    return launch_backward_t(a, threads, smem, s);
+    if (f.nd == 2) return launch_backward_nd<T, 2>(a, threads, smem, s);
+    return launch_backward_nd<T, 3>(a, threads, smem, s);
 }
 
 }  // namespace sf

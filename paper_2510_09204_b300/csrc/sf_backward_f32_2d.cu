@@ -1,0 +1,9 @@
+// Backward kernels, FP32, 2D (one translation unit per precision and dimension, so
+// that the library builds in parallel).
+#include "sf_backward.cuh"
+
+namespace sf {
+
+template cudaError_t launch_backward_nd<float, 2>(const BwdArgs<float> &, int, size_t, cudaStream_t);
+
+}  // namespace sf

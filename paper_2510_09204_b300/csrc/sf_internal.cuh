@@ -99,7 +99,7 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n,
     c.lam = o; o += carve_round(NN, esz);
     c.xc = o;  o += carve_round(NN, esz);
     c.v = o;   o += carve_round(NN, esz);
-    c.gp = o;  o += 2 * carve_round(NN + 4, esz);                 // partial g + stats, two buffers
+    c.gp = o;  o += 2 * carve_round(NN + 4 + 3 * 32, esz);        // partial g + per-warp stats, two buffers
     c.dl = o;  o += carve_round(NN, esz);                         // projection rows of this CTA
     c.dd = o;  o += carve_round(NN, esz);                         // projection output
     c.rr = o;  o += carve_round(tc_mode ? NN : 0, esz);           // refinement residual (tensor cores)

@@ -81,6 +81,25 @@ __device__ __forceinline__ void row_adjoint(const T (&d)[ND], T q, T ia2, T ib2,
     for (int ax = 0; ax < ND; ++ax) out[ax] += f * y[ax] + s3dy * d[ax] * (ax == 2 ? ib2 : ia2);
 }
 
+// e / d for 0 <= e < 2^22 and 1 <= d < 2^22 without an integer division: e times the
+// rounded reciprocal of d is within 2^22 * 2^-23 < 1 of the quotient, so its truncation
+// is off by at most one, which the remainder test corrects.
+struct FDiv {
+    int d;
+    float r;
+    __device__ __forceinline__ void set(int dd)
+    {
+        d = dd;
+        r = 1.0f / (float)dd;
+    }
+    __device__ __forceinline__ int q(int e) const
+    {
+        const int x = __float2int_rz((float)e * r);
+        const int m = e - x * d;
+        return x + (m >= d ? 1 : 0) - (m < 0 ? 1 : 0);
+    }
+};
+
 // squared scaled distance: dx^2 + dy^2 + kz dz^2 with kz = a^2 / b^2
 template <typename T, int ND>
 __device__ __forceinline__ T qdist(const T (&d)[ND], T kz)
@@ -122,7 +141,9 @@ __device__ __forceinline__ void block_reduce3_to(T a, T b, T c, T *red)
 }
 
 // TC: compile in the tensor-core projection (FP32 only); other instantiations stay lean.
-template <typename T, int ND, bool TC = false>
+// NXI > 0: the coefficient count fixed at compile time (loops over it unroll, divisions by
+// it become multiplications); 0: taken from the arguments.
+template <typename T, int ND, bool TC = false, int NXI = 0>
 struct Cta {
     using VP = Vec<T, NDP<ND>::v>;
     int tid, nt, C, cr, nxi, n, npad, H, N, NN, nobs, opad, hc, k_lo, k_hi, L, r_lo, r_hi, ii;
@@ -142,6 +163,7 @@ struct Cta {
     unsigned short *lpl, *lol;
     int *lcn;
     int cull, LPs, LOs, NBX;
+    FDiv fn, fN, fL;  // divisions by n, N and L
     int lv, need;     // lists valid for the current chunk; rebuild asked (block-uniform)
     bool esc;         // this thread saw a position outside its robot's inflated box
     T cdel;           // inflation of the robots' boxes
@@ -164,7 +186,7 @@ struct Cta {
         C = csize;
         cr = rank;
         ii = inst;
-        nxi = A.nxi;
+        nxi = NXI > 0 ? NXI : A.nxi;   // a compile-time constant in the specialised kernels
         I = A.inst[ii];
         S = A.shapes[I.shape];
         n = I.n;
@@ -197,13 +219,16 @@ struct Cta {
         LPs = cull_lp(n);
         LOs = cull_lo(nobs);
         NBX = n + nobs;
+        fn.set(n);
+        fN.set(N);
+        fL.set(L);
         lv = 0;
         need = 0;
         esc = false;
         cdel = T(0.5) * fmax(I.a, I.b);
         bd = sm + cv.bd; db = sm + cv.db; sx = sm + cv.sx; red = sm + cv.red; Ps = sm + cv.Ps;
         P = reinterpret_cast<VP *>(sm + cv.pb);
-        gstride = carve_round(NN + 4, (int)sizeof(T));
+        gstride = carve_round(NN + 4 + 3 * 32, (int)sizeof(T));
         Pbg = A.Pb + S.off_Pb;
         obs_g = A.obs + I.off_obs;
         Pdev = sx; Pdif = sx + nxi * nxi; Bdev = sx + 2 * nxi * nxi; Bdif = Bdev + 2 * nxi;
@@ -363,8 +388,11 @@ struct Cta {
     {
         T *o = reinterpret_cast<T *>(out);
         const int S = seg_len(hcc), ns = nseg_of(hcc);
+        FDiv fh, fS;
+        fh.set(hcc);
+        fS.set(S);
         for (int e = tid; e < ND * n * hcc; e += nt) {
-            const int r = e / hcc, kl = e - r * hcc, ax = r / n, i = r - ax * n;
+            const int r = fh.q(e), kl = e - r * hcc, ax = fn.q(r), i = r - ax * n;
             const T *wr = W + (k0 + kl) * nxi;
             const T *xr = coeff + r * nxi;
             T s0 = T(0), s1 = T(0), s2 = T(0);
@@ -378,7 +406,7 @@ struct Cta {
             const T val = (s0 + s1) + s2;
             o[(i * hcc + kl) * NDP<ND>::v + ax] = val;
             if (chk) {
-                const int sg = kl / S;
+                const int sg = fS.q(kl);
                 if (!(val >= bbx[((2 * ax) * ns + sg) * NBX + i] && val <= bbx[((2 * ax + 1) * ns + sg) * NBX + i]))
                     esc = true;
             }
@@ -582,6 +610,9 @@ struct Cta {
     __device__ __forceinline__ void rows(int k0, int hcc, T &rp2, T &mx2)
     {
         const int items = n * hcc, segS = seg_len(hcc);
+        FDiv fh, fS;
+        fh.set(hcc);
+        fS.set(segS);
         const T a2 = I.a * I.a, ia2 = I.ia2, kz = (I.a * I.a) * I.ib2;
         T tie_f[ND], tie_b[ND];   // r_1 of a coincident pair seen from the row's first / second robot
 #pragma unroll
@@ -593,7 +624,7 @@ struct Cta {
             const bool valid = e < items;
             if (__all_sync(0xffffffffu, !valid)) continue;   // a whole warp without items skips the round
             const int ee = valid ? e : 0;
-            const int i = ee / hcc, kl = ee - i * hcc, k = k0 + kl;
+            const int i = fh.q(ee), kl = ee - i * hcc, k = k0 + kl;
             VP pi = P[i * hcc + kl];
             if (!valid)
 #pragma unroll
@@ -601,7 +632,7 @@ struct Cta {
             T R[ND];
 #pragma unroll
             for (int ax = 0; ax < ND; ++ax) R[ax] = T(0);
-            const int task = (kl / segS) * n + i;   // culling lists of (segment, robot)
+            const int task = fS.q(kl) * n + i;   // culling lists of (segment, robot)
             const int cp4 = cull ? (lcn[2 * task] + 3) & ~3 : 0, co4 = cull ? (lcn[2 * task + 1] + 3) & ~3 : 0;
             const int jend = cull ? __reduce_max_sync(0xffffffffu, cp4) : npad;
             const int mend = cull ? __reduce_max_sync(0xffffffffu, co4) : opad;
@@ -697,13 +728,16 @@ struct Cta {
     {
         const bool seed = seed_w != T(0);
         const int items = n * hcc, segS = seg_len(hcc);
+        FDiv fh, fS;
+        fh.set(hcc);
+        fS.set(segS);
         const T a2 = I.a * I.a, ia2 = I.ia2, ib2 = I.ib2, kz = (I.a * I.a) * I.ib2;
         for (int e0 = 0; e0 < items; e0 += nt) {
             const int e = e0 + tid;
             const bool valid = e < items;
             if (__all_sync(0xffffffffu, !valid)) continue;
             const int ee = valid ? e : 0;
-            const int i = ee / hcc, kl = ee - i * hcc, k = k0 + kl;
+            const int i = fh.q(ee), kl = ee - i * hcc, k = k0 + kl;
             VP pi = P[i * hcc + kl];
             if (!valid)
 #pragma unroll
@@ -714,7 +748,7 @@ struct Cta {
                 Ri[ax] = seed ? T(0) : Rs[i * hcc + kl].v[ax];
                 ps[ax] = T(0);
             }
-            const int task = (kl / segS) * n + i;   // culling lists of (segment, robot)
+            const int task = fS.q(kl) * n + i;   // culling lists of (segment, robot)
             const int cp4 = cull ? (lcn[2 * task] + 3) & ~3 : 0, co4 = cull ? (lcn[2 * task + 1] + 3) & ~3 : 0;
             const int jend = cull ? __reduce_max_sync(0xffffffffu, cp4) : npad;
             const int mend = cull ? __reduce_max_sync(0xffffffffu, co4) : opad;
@@ -933,8 +967,8 @@ struct Cta {
             tc_rows(src, corr_b);
             cl.sync();
             for (int e = tid; e < NN; e += nt) {
-                const int row = e - (e / N) * N;
-                dst[e] = cl.map_shared_rank(dl, row / L)[e];
+                const int row = e - fN.q(e) * N;
+                dst[e] = cl.map_shared_rank(dl, fL.q(row))[e];
             }
             // refinement: dst += P~ (src - H dst) on the interior coefficients, the residual in
             // FP32 through H = I + rho ((n + n_obs + 2) I - 11') (x) W'W
@@ -953,7 +987,7 @@ struct Cta {
                 __syncthreads();
                 const T cn = T(n + n_obs_ + 2);
                 for (int e = tid; e < NN; e += nt) {
-                    const int r = e / nxi, u = e - r * nxi, ax = r / n;
+                    const int r = e / nxi, u = e - r * nxi, ax = fn.q(r);
                     T hv = T(0);
                     for (int c = 0; c < nxi; ++c) hv += wtw[u * nxi + c] * (cn * dst[r * nxi + c] - sums[ax * nxi + c]);
                     const T res = src[e] - (dst[e] + rho * hv);
@@ -963,8 +997,8 @@ struct Cta {
                 tc_rows(rr, false);
                 cl.sync();
                 for (int e = tid; e < NN; e += nt) {
-                    const int row = e - (e / N) * N;
-                    dst[e] += cl.map_shared_rank(dl, row / L)[e];
+                    const int row = e - fN.q(e) * N;
+                    dst[e] += cl.map_shared_rank(dl, fL.q(row))[e];
                 }
             }
         } else if (dense) {
@@ -1003,8 +1037,8 @@ struct Cta {
             }
             cl.sync();
             for (int e = tid; e < NN; e += nt) {
-                const int row = e - (e / N) * N;
-                dst[e] = cl.map_shared_rank(dl, row / L)[e];
+                const int row = e - fN.q(e) * N;
+                dst[e] = cl.map_shared_rank(dl, fL.q(row))[e];
             }
         } else {
             // Kronecker form, per axis with robot mean m of src:
@@ -1028,7 +1062,7 @@ struct Cta {
             }
             __syncthreads();
             for (int e = tid; e < NN; e += nt) {
-                const int r = e / nxi, u = e - r * nxi, ax = r / n;
+                const int r = e / nxi, u = e - r * nxi, ax = fn.q(r);
                 const T *vr = src + r * nxi;
                 const T *pu = Pdev + u * nxi;
                 T s0 = pm[ax * nxi + u], s1 = T(0);
@@ -1061,10 +1095,64 @@ struct Cta {
         }
     }
 
+    // update() without side work (the adjoint's recomputation of the iterates)
+    __device__ __forceinline__ T update(cg::cluster_group &cl, const T *gme, bool corr_b)
+    {
+        return update(cl, gme, corr_b, [] {});
+    }
+
+    // Per-warp partial statistics into gme[NN + 4 + 3 w + (0, 1, 2)]: sum of rp2, max of mx2,
+    // sum of fp over the warp's lanes.
+    __device__ __forceinline__ void warp_partials(T *gme, T rp2, T mx2, T fp) const
+    {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            rp2 += __shfl_xor_sync(0xffffffffu, rp2, o);
+            mx2 = fmax(mx2, __shfl_xor_sync(0xffffffffu, mx2, o));
+            fp += __shfl_xor_sync(0xffffffffu, fp, o);
+        }
+        if ((tid & 31) == 0) {
+            T *g = gme + NN + 4 + 3 * (tid >> 5);
+            g[0] = rp2;
+            g[1] = mx2;
+            g[2] = fp;
+        }
+    }
+
+    // Cluster statistics from every CTA's per-warp partials (after the cluster barrier that
+    // follows warp_partials): the sum of rp2 and the max of mx2 over the cluster, the sum of
+    // fp over this CTA (each CTA updates the whole iterate).  Called by one full warp, in a
+    // fixed order; the results are valid in every lane.
+    __device__ __forceinline__ void cluster_stats(cg::cluster_group &cl, const T *gme, T &s_rp2, T &s_mx2,
+                                                  T &s_fp) const
+    {
+        const int lane = tid & 31, nw = nt >> 5;
+        T a = T(0), b = T(0), c = T(0);
+        for (int idx = lane; idx < C * nw; idx += 32) {
+            const int q = idx / nw, w = idx - q * nw;
+            const T *g = cl.map_shared_rank(gme, q) + NN + 4 + 3 * w;
+            a += g[0];
+            b = fmax(b, g[1]);
+            if (q == cr) c += g[2];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        s_rp2 = a;
+        s_mx2 = b;
+        s_fp = c;
+    }
+
     // Second half, after the cluster barrier: g = sum over the cluster of gme (fixed order,
     // the same bits in every CTA), lambda step, correction projection, xi_bar update.
     // Returns this thread's share of ||z^{l+1} - z^l||^2.
-    __device__ __forceinline__ T update(cg::cluster_group &cl, const T *gme, bool corr_b)
+    // side(): work for the CTA's last warp after its share of the g gather (the cluster
+    // statistics of the forward), overlapped with the other warps' gathers.
+    template <typename F>
+    __device__ __forceinline__ T update(cg::cluster_group &cl, const T *gme, bool corr_b, F &&side)
     {
         T fp = T(0);
         for (int e = tid; e < NN; e += nt) {
@@ -1076,6 +1164,7 @@ struct Cta {
             v[e] = xc[e] - xb[e] + ln - rho * gg;
             lam[e] = ln;
         }
+        if (tid >> 5 == (nt >> 5) - 1) side();
         __syncthreads();
         project(cl, v, dd, corr_b);
         for (int e = tid; e < NN; e += nt) {
