@@ -48,7 +48,7 @@ def args_():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", type=int, default=2)
     p.add_argument("--precision", default="fp32")
-    p.add_argument("--proj", default="dense")
+    p.add_argument("--proj", default="structured")
     p.add_argument("--n-refine", type=int, default=0)
     p.add_argument("--ckpt-every", type=int, default=10)
     p.add_argument("--forward-only", action="store_true", help="time sf_solve + residual check without the adjoint")
@@ -166,6 +166,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
                 "power_w_max": max(r[3] for r in inside), "reasons": reasons, "samples": len(inside),
                 "sampling": how}
+
+
+def profiled_traffic(kernel, workload, precision, proj):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary of this workload,
+    or None when there is none or the kernel sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "%s_%s_%s_%s.md" % (kernel, workload, precision, proj))
+    try:
+        with open(path) as f:
+            kv = dict(line.split(":", 1) for line in f.read().splitlines()
+                      if line.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
+    except OSError:
+        return None, None
+    sys.path.insert(0, os.path.join(ROOT, "paper_2510_09204_b300"))
+    import build as _build
+    if kv.get("source_sha256", "").strip() != _build.source_digest():
+        return None, os.path.relpath(path, ROOT) + " (stale: kernel sources changed since the capture)"
+    return int(kv["traffic_bytes_per_launch"]), os.path.relpath(path, ROOT)
 
 
 def measured_peaks():
@@ -512,6 +529,7 @@ def main():
             kernels[nm] = {"ms": ms, "share": ms / ms_step, "algorithmic_gflop": fl / 1e9, "achieved_tflops": ach,
                            "frac": ach / peak_alu}
         dom = max(kernels, key=lambda k: kernels[k]["ms"])
+        traffic, traffic_src = profiled_traffic(dom, cfg.name, a.precision, a.proj)
         line = {
             "metric": METRIC,
             "value": value, "unit": "pair-timestep updates/s", "n_gpus": world, "steps": a.steps,
@@ -524,7 +542,8 @@ def main():
                 "autotune": tune,
                 "parallelism": "instances sharded by rank" if world > 1 else "single GPU"}),
             "roofline": {"bound": "alu", "achieved": kernels[dom]["achieved_tflops"], "peak": peak_alu,
-                         "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": None, "kernel": dom,
+                         "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": traffic,
+                         "traffic_source": traffic_src, "kernel": dom,
                          "kernel_ms": kernels[dom]["ms"],
                          "peak_source": "148 SMs x 128 FP32 lanes x 2 x sm_max_mhz %.0f (derived ALU peak)" % sm_max},
             "kernels": kernels,

@@ -24,6 +24,18 @@ def headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
+def source_digest() -> str:
+    """SHA-256 over the kernel sources (csrc/ and include/, names and contents): a profile
+    summary records it, and its counters apply only while the sources are unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sources() + headers():
+        h.update(os.path.relpath(f, ROOT).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def stale(out: str = LIB) -> bool:
     if not os.path.exists(out):
         return True
