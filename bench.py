@@ -381,6 +381,7 @@ def main():
     import torch.distributed as dist
 
     from paper_2510_09204_b300 import SFSolver
+    from paper_2510_09204_b300.shard import max_over_ranks
 
     rank, world, local = dist_env()
     if world > 1:
@@ -426,11 +427,7 @@ def main():
     barrier()
     clocks.window(t_start, time.time())
     clk = clocks.stop()
-    tot_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(times), dev)
     ms_step = tot_ms / a.steps
     value = pairs * iters * world / (ms_step * 1e-3)
     r = step.res.cpu().numpy()
@@ -485,11 +482,7 @@ def main():
         for _ in range(a.steps):
             e2e_step()
         barrier()
-        e2e_s = (time.perf_counter() - t0) / a.steps
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / a.steps, dev)
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         h2d += 0 if a.forward_only else hg.numel() * hg.element_size()
         d2h = sum(o.numel() * o.element_size() for o in outs)
