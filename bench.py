@@ -50,7 +50,8 @@ def args_():
     p.add_argument("--precision", default="fp32")
     p.add_argument("--proj", default="structured")
     p.add_argument("--n-refine", type=int, default=0)
-    p.add_argument("--ckpt-every", type=int, default=10)
+    p.add_argument("--ckpt-every", type=int, default=1,
+                   help="checkpoint interval of the differentiable step (1: the adjoint recomputes nothing)")
     p.add_argument("--forward-only", action="store_true", help="time sf_solve + residual check without the adjoint")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -83,13 +84,15 @@ def _per_iter(i, proj):
     return per + proj_f, rows, proj_f
 
 
-def algorithmic_flops(insts, iters, proj, kernel="k_forward"):
+def algorithmic_flops(insts, iters, proj, kernel="k_forward", ckpt_every=1):
     """Operations of one launch of ``kernel`` at the algorithmic minimum.
-    k_forward: iters forward iterations.  k_backward: the recomputation (iters forward
-    iterations) plus the reverse sweep, per iteration the activity test of every row
-    (2 n_d + 1) and box entry (2 n_d), positions, R* = W g* and W' p* (2 n_d n H n_xi
-    each), the projection and 8 n_d N elementwise.  k_residual: one FP64 pass over the
-    rows and the positions."""
+    k_forward: iters forward iterations.  k_backward: the recomputation inside the
+    checkpoint segments (c - 1 forward iterations per segment of c) plus the reverse
+    sweep, per iteration the activity test of every row (2 n_d + 1) and box entry
+    (2 n_d), positions, R* = W g* and W' p* (2 n_d n H n_xi each), the projection and
+    8 n_d N elementwise.  k_residual: one FP64 pass over the rows and the positions."""
+    c = max(1, ckpt_every)
+    recompute = iters - (iters + c - 1) // c
     tot = 0.0
     for i in insts:
         fwd, rows, proj_f = _per_iter(i, proj)
@@ -98,7 +101,7 @@ def algorithmic_flops(insts, iters, proj, kernel="k_forward"):
             tot += fwd * iters
         elif kernel == "k_backward":
             rev = rows * (2 * nd + 1) + 2 * nd * n * H + 6 * nd * n * H * nxi + proj_f + 8 * nd * n * nxi
-            tot += (fwd + rev) * iters
+            tot += fwd * recompute + rev * iters
         else:
             tot += rows * (2 * nd + 1) + 2 * nd * n * H + 2 * nd * n * H * nxi
     return tot
@@ -517,7 +520,7 @@ def main():
             if a.forward_only and nm == "k_backward":
                 continue
             ms = statistics.mean(x[k] for x in kts)
-            fl = algorithmic_flops(insts, iters, a.proj, nm)
+            fl = algorithmic_flops(insts, iters, a.proj, nm, a.ckpt_every)
             ach = fl / (ms * 1e-3) / 1e12
             kernels[nm] = {"ms": ms, "share": ms / ms_step, "algorithmic_gflop": fl / 1e9, "achieved_tflops": ach,
                            "frac": ach / peak_alu}

@@ -91,9 +91,12 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             X.lam[e] = A.ck_l[(int64_t)sg * A.ck_slot + off + e];
         }
         if (sg == 0) X.boundary_gap();   // b - A xi_bar^0 for the first step's P_b term
-        // recompute the segment's iterates with the forward's code
+        // recompute the segment's iterates x^l0 .. x^(l1-1) with the forward's code (the
+        // reverse sweep needs the iterate each step started from, so x^l1 is not computed;
+        // with a checkpoint every iteration nothing is recomputed)
         for (int l = l0; l < l1; ++l) {
             for (int e = tid; e < NN; e += nt) seg[(int64_t)(l - l0) * NN + e] = X.xb[e];
+            if (l + 1 == l1) break;
             T *gme = X.gp + (step & 1) * X.gstride;
             ++step;
             T rp2 = T(0), mx2 = T(0);
