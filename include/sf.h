@@ -96,7 +96,9 @@ typedef struct sf_desc {
                            pass brings SF_BF16X3 to FP32 accuracy, two bring SF_TF32       */
     int32_t max_iters;  /* upper bound on `iters` of sf_solve (sizes checkpoint storage)    */
     int32_t ckpt_every; /* > 0: sf_solve keeps (xi_bar, lambda) every ckpt_every iterations
-                           so sf_solve_backward can run; 0: no backward                    */
+                           so sf_solve_backward can run, and every launch plan leaves room
+                           for the adjoint kernel; 1: the adjoint recomputes nothing;
+                           0: no backward                                                  */
     double tol;         /* residual threshold in metres for iterations-to-tolerance        */
     int32_t n_inst;     /* number of instances, >= 1                                       */
     const sf_shape *shapes; /* host array [n_inst], copied by sf_create                    */
@@ -213,8 +215,8 @@ int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads);
 /*
  * sf_autotune — time each candidate launch geometry (cluster 1, 2, 4, 8 x threads
  * 128, 256, 512, 1024 that fit) on this handle's own batch with `iters` iterations of
- * sf_solve (CUDA events on `stream`, best of `reps` runs), keep the fastest and
- * return it.  Allocates and frees temporary output buffers; results of later solves
+ * sf_solve, followed by sf_solve_backward when the handle keeps checkpoints (CUDA
+ * events on `stream`, best of `reps` runs), keep the fastest and return it.  Allocates and frees temporary output buffers; results of later solves
  * do not depend on the choice beyond rounding order.  The choice is also remembered
  * for the batch's shape signature, and sf_create of a later handle with the same
  * signature starts from it.

@@ -81,7 +81,7 @@ static std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;
 
 static std::vector<int64_t> tune_key(const sf_desc &d, const std::vector<sf_shape> &shp)
 {
-    std::vector<int64_t> k = {d.n_d, d.n_xi, d.precision, d.proj, d.n_inst};
+    std::vector<int64_t> k = {d.n_d, d.n_xi, d.precision, d.proj, d.n_inst, d.ckpt_every > 0};
     for (const sf_shape &s : shp) {
         k.push_back(s.n);
         k.push_back(s.n_obs);
@@ -102,7 +102,7 @@ static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SF_OK : (e == 
 
 int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
                      int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode,
-                     int cull_req)
+                     int cull_req, int need_bwd)
 {
     if (proj != SF_PROJ_DENSE) tc_mode = 0;
     Plan p;
@@ -129,8 +129,11 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
         const int own = (H[i] + C - 1) / C;
         int hc = own;
         if (tc_mode && tc_ntiles(n[i] * nxi, C) > 8) return SF_EUNSUPPORTED;   // 8 x 128 rows per CTA at most
+        // the forward's carve, or the larger adjoint carve when the handle keeps checkpoints
         auto bytes = [&](int h, int rows) {
-            return (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total * esz;
+            const int64_t f = forward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total;
+            const int64_t b = need_bwd ? backward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total : 0;
+            return (size_t)std::max(f, b) * esz;
         };
         while (hc > 1 && bytes(hc, 0) > (size_t)optin) --hc;
         if (bytes(hc, 0) > (size_t)optin) return SF_EUNSUPPORTED;
@@ -154,8 +157,11 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     }
     if (proj == SF_PROJ_DENSE && !tc_mode) {
         size_t with_p = 0;
-        for (int i = 0; i < n_inst; ++i)
+        for (int i = 0; i < n_inst; ++i) {
             with_p = std::max(with_p, (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], maxL, esz, 0, 2, cull).total * esz);
+            if (need_bwd)
+                with_p = std::max(with_p, (size_t)backward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], maxL, esz, 0, 2, cull).total * esz);
+        }
         if (with_p <= (size_t)optin) {
             p.p_rows = maxL;
             need = with_p;
@@ -380,9 +386,9 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
             }
         }
         int prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                               h->smem_optin, c0, t0, &h->plan, h->hc.data(), h->tc_mode, h->cull_req);
+                               h->smem_optin, c0, t0, &h->plan, h->hc.data(), h->tc_mode, h->cull_req, h->d.ckpt_every > 0);
         if (prc && c0) prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                                          h->smem_optin, 0, kDefaultThreads, &h->plan, h->hc.data(), h->tc_mode, h->cull_req);
+                                          h->smem_optin, 0, kDefaultThreads, &h->plan, h->hc.data(), h->tc_mode, h->cull_req, h->d.ckpt_every > 0);
         if (prc) { destroy_all(h); delete h; return prc; }
     }
 
@@ -567,7 +573,7 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
         r.tol = a.tol;
         r.inst = a.inst;
         r.shapes = a.shapes;
-        r.W = a.W;
+        r.W = (const double *)h->W64.p;
         r.x = (const T *)xo;
         r.obs = a.obs;
         r.oab = a.oab;
@@ -664,7 +670,7 @@ extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
     }
     Plan p;
     int rc = plan_forward(h->d.n_d, h->d.n_xi, h->esz, h->d.proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                          h->smem_optin, cluster, threads ? threads : kDefaultThreads, &p, hc.data(), h->tc_mode, h->cull_req);
+                          h->smem_optin, cluster, threads ? threads : kDefaultThreads, &p, hc.data(), h->tc_mode, h->cull_req, h->d.ckpt_every > 0);
     if (rc) return rc;
     SF_TRY(cudaDeviceSynchronize());
     h->plan = p;
@@ -680,11 +686,22 @@ extern "C" int sf_autotune(sf_handle *h, const sf_instance_data *data, const voi
     if (!h || !data || !xi_cand || iters < 1 || iters > h->d.max_iters || reps < 1) return SF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)h->xi_total * h->esz;
-    DevBuf xo, lo;
+    const bool bwd = h->d.ckpt_every > 0;   // a differentiable handle: time forward + adjoint
+    DevBuf xo, lo, gxo, gxc;
     int r;
-    if ((r = cuda_status(xo.alloc(bytes))) || (r = cuda_status(lo.alloc(bytes)))) {
+    if ((r = cuda_status(xo.alloc(bytes))) || (r = cuda_status(lo.alloc(bytes))) ||
+        (bwd && ((r = cuda_status(gxo.alloc(bytes))) || (r = cuda_status(gxc.alloc(bytes)))))) {
         xo.release();
         lo.release();
+        gxo.release();
+        gxc.release();
+        return r;
+    }
+    if (bwd && (r = cuda_status(cudaMemsetAsync(gxo.p, 0, bytes, st)))) {
+        xo.release();
+        lo.release();
+        gxo.release();
+        gxc.release();
         return r;
     }
     const Plan keep = h->plan;
@@ -707,6 +724,8 @@ extern "C" int sf_autotune(sf_handle *h, const sf_instance_data *data, const voi
             for (int q = 0; q <= reps && ok; ++q) {   // the first run warms up
                 cudaEventRecord(e0, st);
                 ok = sf_solve(h, data, xi_cand, nullptr, nullptr, iters, xo.p, lo.p, nullptr, nullptr, st) == SF_OK;
+                if (ok && bwd)
+                    ok = sf_solve_backward(h, gxo.p, nullptr, nullptr, gxc.p, nullptr, nullptr, st) == SF_OK;
                 cudaEventRecord(e1, st);
                 if (ok && cudaEventSynchronize(e1) == cudaSuccess && q > 0) {
                     float ms = 0.f;
@@ -724,6 +743,8 @@ extern "C" int sf_autotune(sf_handle *h, const sf_instance_data *data, const voi
     cudaEventDestroy(e1);
     xo.release();
     lo.release();
+    gxo.release();
+    gxc.release();
     h->profile = keep_prof;
     h->last = keep_last;
     r = sf_set_launch(h, bc, bt);

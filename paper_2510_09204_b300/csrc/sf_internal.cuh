@@ -195,7 +195,7 @@ struct ResArgs {
     double tol;
     const Inst<T> *inst;
     const Shape *shapes;
-    const T *W;
+    const double *W;            // the FP64 basis, whatever the solve precision
     const T *x;                 // coefficients to evaluate (packed xi)
     const T *obs, *oab;
     double *resid;              // [n_inst][SF_NRES]
@@ -224,7 +224,7 @@ struct Plan {
 // instance cannot fit in `optin` bytes of shared memory.
 int plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
                  int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode = 0,
-                 int cull_req = 1);
+                 int cull_req = 1, int need_bwd = 0);
 
 // Arranges every shape's P_eta (FP64 pool) into the tensor-core chunk layout for cluster
 // size C: per shape [C][tiles][K chunks][128 x 128 bytes] (x 2 for the BF16 x3 low part).

@@ -245,7 +245,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
         r.tol = 1e-3;
         r.inst = S->inst;
         r.shapes = &S->shape;
-        r.W = S->W32;
+        r.W = S->W64;
         r.x = xi_out;
         r.obs = obs_c;
         r.oab = obs_ab;

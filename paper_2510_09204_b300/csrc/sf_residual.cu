@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(512) k_residual(ResArgs<T> A)
     Id.a = (double)I.a; Id.b = (double)I.b;
     Id.ia2 = 1.0 / (Id.a * Id.a); Id.ib2 = 1.0 / (Id.b * Id.b);
     for (int ax = 0; ax < 3; ++ax) { Id.pmin[ax] = (double)I.pmin[ax]; Id.pmax[ax] = (double)I.pmax[ax]; }
-    for (int e = tid; e < H * nxi; e += nt) W[e] = (double)A.W[S.off_W + e];
+    for (int e = tid; e < H * nxi; e += nt) W[e] = A.W[S.off_W + e];
     for (int e = tid; e < NN; e += nt) xb[e] = (double)A.x[I.off_xi + e];
     for (int m = tid; m < nobs; m += nt) {
         const double ao = (double)A.oab[I.off_oab + 2 * m], bo = (double)A.oab[I.off_oab + 2 * m + 1];
