@@ -238,14 +238,22 @@ def _oracle_desc(k, B, iters, forward_only, dt=None):
 
 
 def cpu_baseline(insts, iters, forward_only, budget_s=15.0):
-    """The FP64 oracle, as it stands, on the host cores over a bounded sample of the batch."""
+    """The FP64 oracle, as it stands, on the host cores over a bounded sample of the batch,
+    and on one core (one instance's step)."""
     sample, seeds, pool, cores = _oracle_sample(insts, iters, forward_only, budget_s)
     t0 = time.perf_counter()
     _oracle_step(sample, iters, seeds, forward_only, pool)
     dt = time.perf_counter() - t0
     pairs, _ = sfgen.batch_stats(sample)
+    import concurrent.futures
+    one = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+    t1 = time.perf_counter()
+    _oracle_step(insts[:1], iters, seeds[:1], forward_only, one)   # one instance: one thread either way
+    dt1 = time.perf_counter() - t1
+    p1, _ = sfgen.batch_stats(insts[:1])
     return {"value": pairs * iters / dt, "unit": "pair-timestep updates/s", "cores": cores, "kind": "oracle",
-            "sample": _oracle_desc(len(sample), len(insts), iters, forward_only, dt)}
+            "sample": _oracle_desc(len(sample), len(insts), iters, forward_only, dt),
+            "single_thread": {"value": p1 * iters / dt1, "sample": "1 instance on one thread (%.2f s)" % dt1}}
 
 
 METRIC = "SF ms/batch & pair-timestep updates/s, chosen vs plain FP64, residual≤1e-3 m"
@@ -396,8 +404,12 @@ def main():
     nd = cfg.n_d
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
     solver = SFSolver(insts, nd, 11, rho=RHO, precision=a.precision, proj=a.proj, max_iters=iters,
                       ckpt_every=0 if a.forward_only else a.ckpt_every, n_refine=a.n_refine)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t_setup)
     data = solver.pack(insts, device=dev)
     tune = None
     if not a.no_autotune:
@@ -547,7 +559,11 @@ def main():
             "gpu_launches": step.launches() * a.steps,
             "graph": graph,
             "result": {"final_max_residual_m_median": float(np.median(r[:, 1])),
-                       "frac_instances_resid_le_1e-3": float(np.mean(r[:, 1] <= 1e-3))},
+                       "frac_instances_resid_le_1e-3": float(np.mean(r[:, 1] <= 1e-3)),
+                       "iterations_to_1e-3": [int(x) for x in r[:, 3]]},
+            "setup": {"sf_create_ms": setup_ms,
+                      "what": "one-time per batch: FP64 factorisation of every distinct shape on the GPU, "
+                              "launch plan, FP32 copies (outside the timed step)"},
         }
         if e2e:
             line["e2e"] = e2e

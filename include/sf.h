@@ -310,6 +310,25 @@ int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_shape *shap
                      int32_t iters, float *xi_out, float *lam_out, double *resid_out, void *stream);
 
 /* sf_strerror — static description of a status code. */
+/*
+ * sf_fit_positions — least-squares Bernstein coefficients of sampled trajectories, with
+ * the end coefficients pinned to the first and last sample (eq. poly, p = W xi; the
+ * boundary rows A xi = b fix coefficients 0 and n_xi - 1, which the basis interpolates).
+ * For every instance, robot and axis, xi minimises ||W xi - p||^2 subject to
+ * xi_0 = p_0 and xi_{n_xi-1} = p_{H-1}.  A helper for building candidates from sampled
+ * positions; not part of the solve.
+ *  n_d, n_xi      2..3, 3..32
+ *  n_inst         instances; n[k], H[k] (HOST arrays): robots and timesteps of
+ *                 instance k, with n_xi <= H[k] <= 2^20
+ *  pos            DEVICE, FP64, instance after instance, [n_d][n][H]
+ *  xi_out         DEVICE, FP64, instance after instance, [n_d][n][n_xi] (the packing of
+ *                 SF_LAYOUT_XI)
+ * Allocates and frees its scratch on `stream` and synchronises it before returning.
+ * Errors: SF_EINVAL (bad sizes, singular fit), SF_ENOMEM, SF_ECUDA.
+ */
+int sf_fit_positions(int32_t n_d, int32_t n_xi, int32_t n_inst, const int32_t *n, const int32_t *H,
+                     const double *pos, double *xi_out, void *stream);
+
 const char *sf_strerror(int32_t code);
 
 /* sf_version — library version as an integer (major * 10000 + minor * 100 + patch). */

@@ -219,6 +219,24 @@ def solve_batch(insts, iters, rho=DEFAULT_RHO, ws_hess=True, threads=None, lib=N
     return outs, resid
 
 
+def fit_positions(pos, n_xi, lib=None):
+    """Endpoint-pinned least-squares coefficients of sampled trajectories (eq. poly, p = W xi,
+    with the boundary rows fixing coefficients 0 and n_xi - 1): pos [n_d][n][H] ->
+    xi [n_d][n][n_xi] with xi_0 = p_0, xi_last = p_{H-1} and the interior the least-squares
+    solution (numpy lstsq) against the samples minus the two endpoint columns."""
+    pos = np.asarray(pos, dtype=np.float64)
+    nd, n, H = pos.shape
+    W = basis(H, n_xi, lib)
+    p0, p1 = pos[..., 0], pos[..., -1]
+    r = pos - W[:, 0] * p0[..., None] - W[:, -1] * p1[..., None]
+    sol = np.linalg.lstsq(W[:, 1:-1], r.reshape(-1, H).T, rcond=None)[0]   # [n_xi - 2][rows]
+    xi = np.empty((nd, n, n_xi))
+    xi[..., 0] = p0
+    xi[..., -1] = p1
+    xi[..., 1:-1] = sol.T.reshape(nd, n, n_xi - 2)
+    return xi
+
+
 def positions(xi_bar, H, lib=None):
     """p = W xi_bar for every axis and robot: [n_d][n][H]."""
     W = basis(H, xi_bar.shape[-1], lib)

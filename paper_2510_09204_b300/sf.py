@@ -28,7 +28,8 @@ PROJECTIONS = {"dense": SF_PROJ_DENSE, "structured": SF_PROJ_STRUCTURED}
 # every symbol declared in include/sf.h
 EXPORTS = ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
            "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch",
-           "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_strerror", "sf_version")
+           "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions", "sf_strerror",
+           "sf_version")
 SF_OPT_CULL = 1
 SF_KT_FORWARD, SF_KT_RESIDUAL, SF_KT_BACKWARD, SF_NKT = range(4)
 
@@ -83,12 +84,13 @@ def lib(path: str | None = None):
                                   ct.POINTER(i32), ct.POINTER(ct.c_float)]
         L.sf_get_launch.argtypes = [vp, ct.POINTER(i32), ct.POINTER(i32), ct.POINTER(i32)]
         L.sf_set_option.argtypes = [vp, i32, i32]
+        L.sf_fit_positions.argtypes = [i32, i32, i32, ct.POINTER(i32), ct.POINTER(i32), vp, vp, vp]
         L.sf_get_option.argtypes = [vp, i32, ct.POINTER(i32)]
         L.sf_strerror.argtypes = [i32]
         L.sf_strerror.restype = ct.c_char_p
         L.sf_version.restype = i32
         for f in ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
-                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune"):
+                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -288,6 +290,29 @@ class SFSolver:
             self.close()
         except Exception:
             pass
+
+
+def fit_positions(positions, n_xi=11, stream=None):
+    """sf_fit_positions: endpoint-pinned least-squares coefficients of sampled trajectories.
+    positions: list of [n_d][n][H] arrays (one per instance, any H >= n_xi); returns the
+    list of [n_d][n][n_xi] float64 arrays."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("fit_positions needs a CUDA device; there is no CPU path")
+    arrs = [np.asarray(p, dtype=np.float64) for p in positions]
+    nd = arrs[0].shape[0]
+    ns = (ct.c_int32 * len(arrs))(*[a.shape[1] for a in arrs])
+    Hs = (ct.c_int32 * len(arrs))(*[a.shape[2] for a in arrs])
+    pos = torch.as_tensor(np.concatenate([a.ravel() for a in arrs]), device="cuda")
+    out = torch.empty(sum(nd * a.shape[1] * n_xi for a in arrs), dtype=torch.float64, device="cuda")
+    _check(lib().sf_fit_positions(nd, int(n_xi), len(arrs), ns, Hs, _ptr(pos), _ptr(out), _stream(stream)),
+           "sf_fit_positions")
+    flat = out.cpu().numpy()
+    res, o = [], 0
+    for a in arrs:
+        m = nd * a.shape[1] * n_xi
+        res.append(flat[o:o + m].reshape(nd, a.shape[1], n_xi))
+        o += m
+    return res
 
 
 class SFSolve(torch.autograd.Function):

@@ -381,3 +381,31 @@ def test_batch_matches_single_instances():
         ref = oracle.solve(inst, 20, rho=RHO)["xi"]
         np.testing.assert_array_equal(x, ref)
         np.testing.assert_allclose(r, oracle.residual(inst, ref)[:2], rtol=0, atol=0)
+
+
+# ---- endpoint-pinned least-squares fit (candidate helper) -----------------------------
+
+@pytest.mark.parametrize("H,nxi", [(11, 11), (40, 11), (200, 7), (9, 9)])
+def test_fit_recovers_representable_curves(H, nxi):
+    """Samples of a polynomial of the basis are fitted exactly (zero residual), endpoints included."""
+    rng = np.random.default_rng(H + nxi)
+    xi = rng.normal(size=(2, 5, nxi)) * 3.0
+    pos = np.einsum("kc,dic->dik", oracle.basis(H, nxi), xi)
+    assert np.abs(oracle.fit_positions(pos, nxi) - xi).max() <= 1e-9
+
+
+def test_fit_pins_endpoints_and_is_optimal():
+    """Endpoints equal the first and last samples exactly; no interior perturbation lowers
+    the squared error (brute force over random directions)."""
+    rng = np.random.default_rng(3)
+    H, nxi = 50, 11
+    pos = rng.normal(size=(3, 4, H)) * 2.0
+    xi = oracle.fit_positions(pos, nxi)
+    assert np.array_equal(xi[..., 0], pos[..., 0]) and np.array_equal(xi[..., -1], pos[..., -1])
+    W = oracle.basis(H, nxi)
+    err = lambda x: ((np.einsum("kc,dic->dik", W, x) - pos) ** 2).sum()
+    e0 = err(xi)
+    for _ in range(200):
+        d = np.zeros_like(xi)
+        d[..., 1:-1] = rng.normal(size=xi[..., 1:-1].shape) * 10 ** rng.uniform(-6, -1)
+        assert err(xi + d) >= e0 - 1e-12 * max(e0, 1.0)
