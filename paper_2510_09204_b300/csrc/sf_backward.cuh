@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     X.load_constants(A, A.p_rows);
     X.tc_setup(A, smem_raw);
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T *xs = sm + cv.xs, *ls = sm + cv.ls, *cs = sm + cv.cs;
+    T *xs = sm + cv.xs, *ls = sm + cv.ls, *cs = sm + cv.cs, *xn = sm + cv.xn;
     VP *Rs = reinterpret_cast<VP *>(sm + cv.Rs);
     const int tid = X.tid, nt = X.nt, NN = X.NN, nxi = X.nxi, N = X.N, n = X.n;
     const int64_t off = X.I.off_xi;
@@ -83,20 +83,45 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     }
 
     const int S = ce > 0 ? (Lit + ce - 1) / ce : 0;
+    // The next segment's checkpoint is fetched into registers while the current segment
+    // runs (lambda only when the segment has iterations to recompute).
+    constexpr int kPF = 4;
+    T pfx[kPF], pfl[kPF];
+    auto fetch = [&](int sg) {
+        const bool wl = ce > 1;
+#pragma unroll
+        for (int q = 0; q < kPF; ++q) {
+            const int e = tid + q * nt;
+            if (e < NN) {
+                pfx[q] = A.ck_x[(int64_t)sg * A.ck_slot + off + e];
+                if (wl) pfl[q] = A.ck_l[(int64_t)sg * A.ck_slot + off + e];
+            }
+        }
+    };
+    if (S > 0) fetch(S - 1);
     for (int sg = S - 1; sg >= 0; --sg) {
         const int l0 = sg * ce, l1 = min(Lit, l0 + ce);
         __syncthreads();
-        for (int e = tid; e < NN; e += nt) {
-            X.xb[e] = A.ck_x[(int64_t)sg * A.ck_slot + off + e];
-            X.lam[e] = A.ck_l[(int64_t)sg * A.ck_slot + off + e];
+#pragma unroll
+        for (int q = 0; q < kPF; ++q) {
+            const int e = tid + q * nt;
+            if (e < NN) {
+                X.xb[e] = pfx[q];
+                if (ce > 1) X.lam[e] = pfl[q];
+            }
         }
+        for (int e = tid + kPF * nt; e < NN; e += nt) {
+            X.xb[e] = A.ck_x[(int64_t)sg * A.ck_slot + off + e];
+            if (ce > 1) X.lam[e] = A.ck_l[(int64_t)sg * A.ck_slot + off + e];
+        }
+        if (sg > 0) fetch(sg - 1);
         if (sg == 0) X.boundary_gap();   // b - A xi_bar^0 for the first step's P_b term
         // recompute the segment's iterates x^l0 .. x^(l1-1) with the forward's code (the
         // reverse sweep needs the iterate each step started from, so x^l1 is not computed;
-        // with a checkpoint every iteration nothing is recomputed)
-        for (int l = l0; l < l1; ++l) {
+        // x^(l1-1) stays in xb, the earlier ones go to the segment scratch; with a checkpoint
+        // every iteration nothing is recomputed)
+        for (int l = l0; l + 1 < l1; ++l) {
             for (int e = tid; e < NN; e += nt) seg[(int64_t)(l - l0) * NN + e] = X.xb[e];
-            if (l + 1 == l1) break;
             T *gme = X.gp + (step & 1) * X.gstride;
             ++step;
             T rp2 = T(0), mx2 = T(0);
@@ -106,8 +131,8 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
         }
         // reverse through the segment
         for (int l = l1 - 1; l >= l0; --l) {
-            const T *xl = seg + (int64_t)(l - l0) * NN;
-            T *xz = X.v, *vs = X.dd, *gs = X.lam, *xn = X.xb;
+            const T *xl = l + 1 == l1 ? X.xb : seg + (int64_t)(l - l0) * NN;
+            T *xz = X.v, *vs = X.dd, *gs = X.lam;
             __syncthreads();
             for (int e = tid; e < NN; e += nt) {
                 const int c = e - (e / nxi) * nxi;

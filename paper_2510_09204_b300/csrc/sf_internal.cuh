@@ -130,7 +130,7 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n,
 // (dL/dxi_bar, dL/dlambda, dL/dxi_cand) and R* in the vector layout of the positions.
 struct BwdCarve {
     FwdCarve f;
-    int64_t xs, ls, cs, Rs, total;
+    int64_t xs, ls, cs, xn, Rs, total;
 };
 
 __host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
@@ -143,6 +143,7 @@ __host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n
     b.xs = o; o += carve_round(NN, esz);
     b.ls = o; o += carve_round(NN, esz);
     b.cs = o; o += carve_round(NN, esz);
+    b.xn = o; o += carve_round(NN, esz);
     b.Rs = o; o += carve_round((npad + 4) * hc * ndp, esz);
     b.total = o;
     return b;
