@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     X.tc_setup(A, smem_raw);
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *xs = sm + cv.xs, *ls = sm + cv.ls, *cs = sm + cv.cs, *xn = sm + cv.xn;
+    T *xz = sm + cv.xz;   // xs with the end coefficients cleared: the next reverse step's x*
     VP *Rs = reinterpret_cast<VP *>(sm + cv.Rs);
     const int tid = X.tid, nt = X.nt, NN = X.NN, nxi = X.nxi, N = X.N, n = X.n;
     const int64_t off = X.I.off_xi;
@@ -80,6 +81,10 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, q)[e];
             xs[e] += s;
         }
+    }
+    for (int e = tid; e < NN; e += nt) {
+        const int c = e - (e / nxi) * nxi;
+        xz[e] = (c == 0 || c == nxi - 1) ? T(0) : xs[e];
     }
 
     const int S = ce > 0 ? (Lit + ce - 1) / ce : 0;
@@ -132,13 +137,8 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
         // reverse through the segment
         for (int l = l1 - 1; l >= l0; --l) {
             const T *xl = l + 1 == l1 ? X.xb : seg + (int64_t)(l - l0) * NN;
-            T *xz = X.v, *vs = X.dd, *gs = X.lam;
-            __syncthreads();
-            for (int e = tid; e < NN; e += nt) {
-                const int c = e - (e / nxi) * nxi;
-                xz[e] = (c == 0 || c == nxi - 1) ? T(0) : xs[e];
-            }
-            __syncthreads();
+            T *vs = X.dd, *gs = X.lam;
+            __syncthreads();   // xz of the previous step's gather (or the seed) complete
             X.project(cl, xz, vs, false);
             for (int e = tid; e < NN; e += nt) {
                 const T vst = vs[e];
@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
                 cs[e] += vst;
                 ls[e] += vst;
             }
-            __syncthreads();
             if (l == 0) {   // - A' P_b' x*: the end coefficients of xi_bar^0
+                __syncthreads();
                 for (int q2 = tid; q2 < ND * 2 * n; q2 += nt) {
                     const int ax = q2 / (2 * n), q = q2 - ax * 2 * n;
                     T s = T(0);
@@ -175,7 +175,10 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             for (int e = tid; e < NN; e += nt) {
                 T s = T(0);
                 for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, q)[e];
-                xs[e] = xn[e] + s;
+                const T x = xn[e] + s;
+                const int c = e - (e / nxi) * nxi;
+                xs[e] = x;
+                xz[e] = (c == 0 || c == nxi - 1) ? T(0) : x;
             }
         }
     }

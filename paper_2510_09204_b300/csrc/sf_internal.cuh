@@ -130,7 +130,7 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n,
 // (dL/dxi_bar, dL/dlambda, dL/dxi_cand) and R* in the vector layout of the positions.
 struct BwdCarve {
     FwdCarve f;
-    int64_t xs, ls, cs, xn, Rs, total;
+    int64_t xs, ls, cs, xn, xz, Rs, total;
 };
 
 __host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
@@ -144,6 +144,7 @@ __host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n
     b.ls = o; o += carve_round(NN, esz);
     b.cs = o; o += carve_round(NN, esz);
     b.xn = o; o += carve_round(NN, esz);
+    b.xz = o; o += carve_round(NN, esz);
     b.Rs = o; o += carve_round((npad + 4) * hc * ndp, esz);
     b.total = o;
     return b;
