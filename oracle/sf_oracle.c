@@ -43,6 +43,15 @@
  *      is identically zero).
  *  R9  derivative conventions: d/dx max(1,x) = [x > 1], d/dx max(0,x) = [x > 0],
  *      atan2(0,0) = 0 with zero derivative.
+ *
+ * Cost modes.  cost = 0: the SF projection cost above.  cost = 1: the trajectory
+ * optimiser of eq. eq::form with the smoothness cost of eq. cost,
+ * 1/2 sum_i sum_k ||p''_{i|k}||^2 = 1/2 xi' Q xi with Q = blockdiag(Wdd' Wdd) and q = 0,
+ * solved by the same alternating minimisation: the Hessian of the xi_bar step becomes
+ * Q + rho F'F + rho G'G and its right-hand side loses the candidate term.
+ *  R13 time scale: p'' is taken with respect to time t = tau (H - 1) dt, dt a parameter
+ *      (the paper gives no time step); the smoothness mode needs the workspace terms in
+ *      the Hessian (ws_hess = 1), which make it positive definite.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -51,8 +60,8 @@
 #define SFO_NHIST 4 /* per-iteration history: ||r_p||, max residual, FP residual, kink margin */
 
 typedef struct {
-    int nd, nxi, n, nobs, H, dyn, ws_hess;
-    double rho, a, b;
+    int nd, nxi, n, nobs, H, dyn, ws_hess, cost;
+    double rho, a, b, dt;
     const double *pmin, *pmax, *obs_c, *obs_ab, *bnd, *xi;
 } prob_t;
 
@@ -82,6 +91,30 @@ int sfo_basis(int H, int nxi, double *W)
         double tau = (double)k / (double)(H - 1);
         for (int c = 0; c < nxi; c++)
             W[k * nxi + c] = binom(deg, c) * pow(tau, c) * pow(1.0 - tau, deg - c);
+    }
+    return 0;
+}
+
+/* Wdd[k][c] = d^2/dt^2 of the c-th basis polynomial at t_k = tau_k T, T = (H-1) dt:
+   the second derivative of a degree-d Bernstein polynomial is d (d-1) times the second
+   difference of the degree-(d-2) polynomials, scaled by 1/T^2 (reading R13). */
+int sfo_basis_dd(int H, int nxi, double dt, double *Wdd)
+{
+    if (H < 2 || nxi < 3 || !(dt > 0.0)) return -1;
+    int deg = nxi - 1;
+    double T = (double)(H - 1) * dt;
+    double scale = (double)deg * (double)(deg - 1) / (T * T);
+    for (int k = 0; k < H; k++) {
+        const double tau = k / (H - 1.0);
+        for (int c = 0; c < nxi; c++) {
+            double v = 0.0;
+            for (int j = c - 2; j <= c; j++) {
+                if (j < 0 || j > deg - 2) continue;
+                double w = j == c - 1 ? -2.0 : 1.0;
+                v += w * binom(deg - 2, j) * pow(tau, j) * pow(1.0 - tau, deg - 2 - j);
+            }
+            Wdd[k * nxi + c] = scale * v;
+        }
     }
     return 0;
 }
@@ -342,7 +375,20 @@ static int ctx_init(const prob_t *P, ctx_t *C)
                                 P->rho * (sg * C->W[k * nxi + u]) * (sg * C->W[k * nxi + v]);
                 }
     }
-    for (int u = 0; u < N; u++) Hm[u * N + u] += 1.0;
+    if (P->cost == 0) {
+        for (int u = 0; u < N; u++) Hm[u * N + u] += 1.0;   /* 1/2 ||xi_bar - xi||^2 */
+    } else {                                                /* 1/2 xi' Q xi, one block per robot */
+        double *Wdd = malloc(sizeof(double) * H * nxi);
+        if (!Wdd || sfo_basis_dd(H, nxi, P->dt, Wdd)) { free(Wdd); free(f); ctx_free(C); return -1; }
+        for (int i = 0; i < n; i++)
+            for (int u = 0; u < nxi; u++)
+                for (int v = 0; v < nxi; v++) {
+                    double q = 0.0;
+                    for (int k = 0; k < H; k++) q += Wdd[k * nxi + u] * Wdd[k * nxi + v];
+                    Hm[(i * nxi + u) * N + i * nxi + v] += q;
+                }
+        free(Wdd);
+    }
     free(f);
     if (cholesky(N, C->L)) { ctx_free(C); return -3; }
 
@@ -478,12 +524,14 @@ static void T_apply(const prob_t *P, const ctx_t *C, const double *xib, const do
         GT_apply(P, C, B->r2 + (size_t)ax * RG, g);
         for (int u = 0; u < N; u++) lam_new[(size_t)ax * N + u] = lam[(size_t)ax * N + u] - P->rho * g[u];
     }
-    /* xi_bar step (eq. xi_step): eta = xi + lambda' + rho F'e (+ rho G'(h - s)), KKT solve */
+    /* xi_bar step (eq. xi_step): eta = xi + lambda' + rho F'e (+ rho G'(h - s)), KKT solve
+       (the smoothness cost has no linear term: eta = lambda' + ...) */
     double *hs = malloc(sizeof(double) * RG);
     double *bb = malloc(sizeof(double) * 2 * P->n);
     for (int ax = 0; ax < nd; ax++) {
         double *eta = B->v2 + (size_t)ax * N;
-        for (int u = 0; u < N; u++) eta[u] = P->xi[(size_t)ax * N + u] + lam_new[(size_t)ax * N + u];
+        for (int u = 0; u < N; u++)
+            eta[u] = (P->cost == 0 ? P->xi[(size_t)ax * N + u] : 0.0) + lam_new[(size_t)ax * N + u];
         double *fe = B->v1 + (size_t)ax * N;
         memset(fe, 0, sizeof(double) * N);
         FT_apply(P, C, B->e + (size_t)ax * RF, fe);
@@ -505,29 +553,31 @@ static void T_apply(const prob_t *P, const ctx_t *C, const double *xib, const do
 /* ------------------------------------------------------------ exported API */
 static void fill_prob(prob_t *P, int nd, int nxi, double rho, int n, int nobs, int H, int dyn,
                       double a, double b, const double *pmin, const double *pmax, const double *obs_c,
-                      const double *obs_ab, const double *bnd, const double *xi, int ws_hess)
+                      const double *obs_ab, const double *bnd, const double *xi, int ws_hess, int cost,
+                      double dt)
 {
     P->nd = nd; P->nxi = nxi; P->rho = rho; P->n = n; P->nobs = nobs; P->H = H; P->dyn = dyn;
     P->a = a; P->b = b; P->pmin = pmin; P->pmax = pmax; P->obs_c = obs_c; P->obs_ab = obs_ab;
-    P->bnd = bnd; P->xi = xi; P->ws_hess = ws_hess;
+    P->bnd = bnd; P->xi = xi; P->ws_hess = ws_hess; P->cost = cost; P->dt = dt;
 }
 
 static int check_prob(const prob_t *P)
 {
     if (P->nd < 2 || P->nd > 3 || P->nxi < 2 || P->n < 1 || P->nobs < 0 || P->H < 2) return -1;
     if (!(P->rho > 0.0) || !(P->a > 0.0) || !(P->b > 0.0)) return -1;
+    if (P->cost != 0 && (P->cost != 1 || !P->ws_hess || P->nxi < 3 || !(P->dt > 0.0))) return -1;
     return 0;
 }
 
 /* Explicit pieces of the KKT system for one axis (pins only):
    Hm = I + rho F'F (+ rho G'G)  (N x N), Peta (N x N) and Pb (N x 2n) with
    argmin_{Ax=b} 1/2 x'Hx - eta'x = Peta eta + Pb b. */
-int sfo_kkt(int nd, int nxi, double rho, int n, int nobs, int H, int ws_hess,
+int sfo_kkt(int nd, int nxi, double rho, int n, int nobs, int H, int ws_hess, int cost, double dt,
             double *Hm, double *Peta, double *Pb)
 {
     prob_t P;
     double zeros[3] = {0, 0, 0};
-    fill_prob(&P, nd, nxi, rho, n, nobs, H, 0, 1.0, 1.0, zeros, zeros, NULL, NULL, NULL, NULL, ws_hess);
+    fill_prob(&P, nd, nxi, rho, n, nobs, H, 0, 1.0, 1.0, zeros, zeros, NULL, NULL, NULL, NULL, ws_hess, cost, dt);
     if (check_prob(&P)) return -1;
     ctx_t C;
     int rc = ctx_init(&P, &C);
@@ -572,7 +622,7 @@ int sfo_residual(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, d
                  const double *xib, double *out, double *g)
 {
     prob_t P;
-    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, NULL, NULL, 1);
+    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, NULL, NULL, 1, 0, 0.0);
     if (check_prob(&P)) return -1;
     ctx_t C;
     memset(&C, 0, sizeof(C));
@@ -617,10 +667,11 @@ int sfo_residual(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, d
 int sfo_solve(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, double a, double b,
               const double *pmin, const double *pmax, const double *obs_c, const double *obs_ab,
               const double *bnd, const double *xi, const double *xi0, const double *lam0,
-              int iters, int ws_hess, double *xi_out, double *lam_out, double *hist, double *traj)
+              int iters, int ws_hess, int cost, double dt, double *xi_out, double *lam_out,
+              double *hist, double *traj)
 {
     prob_t P;
-    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, bnd, xi, ws_hess);
+    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, bnd, xi, ws_hess, cost, dt);
     if (check_prob(&P) || iters < 0) return -1;
     ctx_t C;
     int rc = ctx_init(&P, &C);
@@ -668,11 +719,11 @@ int sfo_solve(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, doub
 int sfo_solve_backward(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, double a, double b,
                        const double *pmin, const double *pmax, const double *obs_c, const double *obs_ab,
                        const double *bnd, const double *xi, const double *xi0, const double *lam0,
-                       int iters, int ws_hess, const double *g_xi_out, const double *g_lam_out,
-                       double g_rp2, double *g_xi, double *g_xi0, double *g_lam0)
+                       int iters, int ws_hess, int cost, double dt, const double *g_xi_out,
+                       const double *g_lam_out, double g_rp2, double *g_xi, double *g_xi0, double *g_lam0)
 {
     prob_t P;
-    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, bnd, xi, ws_hess);
+    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, bnd, xi, ws_hess, cost, dt);
     if (check_prob(&P) || iters < 0) return -1;
     ctx_t C;
     int rc = ctx_init(&P, &C);
@@ -738,7 +789,7 @@ int sfo_solve_backward(int nd, int nxi, double rho, int n, int nobs, int H, int 
             /* eta_bar = Peta^T xi_bar'_bar (Peta symmetric: one KKT solve with b = 0) */
             kkt_solve(&P, &C, xb + (size_t)ax * N, NULL, etab + (size_t)ax * N);
             for (int u = 0; u < N; u++) {
-                gx[(size_t)ax * N + u] += etab[(size_t)ax * N + u];
+                if (P.cost == 0) gx[(size_t)ax * N + u] += etab[(size_t)ax * N + u];   /* d eta / d xi = I */
                 lt[(size_t)ax * N + u] = lb[(size_t)ax * N + u] + etab[(size_t)ax * N + u];
             }
             /* e_bar = rho F eta_bar - r1_bar, r1_bar = -rho F lt;  y_bar = r1_bar */
@@ -806,7 +857,8 @@ int sfo_solve_batch(int B, int nd, int nxi, double rho, const int *shp, const do
                     const double *box, const double *obs_c, const long long *off_obs,
                     const double *obs_ab, const long long *off_oab, const double *bnd,
                     const long long *off_bnd, const double *xi, const long long *off_xi,
-                    int iters, int ws_hess, double *xi_out, double *lam_out, double *resid)
+                    int iters, int ws_hess, int cost, double dt, double *xi_out, double *lam_out,
+                    double *resid)
 {
     int status = 0;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -814,7 +866,7 @@ int sfo_solve_batch(int B, int nd, int nxi, double rho, const int *shp, const do
         const int *s = shp + 4 * i;
         int rc = sfo_solve(nd, nxi, rho, s[0], s[1], s[2], s[3], ab[2 * i], ab[2 * i + 1],
                            box + 6 * i, box + 6 * i + 3, obs_c + off_obs[i], obs_ab + off_oab[i],
-                           bnd + off_bnd[i], xi + off_xi[i], NULL, NULL, iters, ws_hess,
+                           bnd + off_bnd[i], xi + off_xi[i], NULL, NULL, iters, ws_hess, cost, dt,
                            xi_out + off_xi[i], lam_out ? lam_out + off_xi[i] : NULL, NULL, NULL);
         if (rc == 0 && resid) {
             double out[3];

@@ -20,6 +20,15 @@ def bernstein(H, n_xi):
     return np.stack(cols, axis=1)
 
 
+def bernstein_dd(H, n_xi, dt):
+    """Second time derivative of the Bernstein basis at t_k = k dt on [0, (H-1) dt], via
+    scipy.BPoly.derivative (smoothness cost of the trajectory optimiser)."""
+    T = (H - 1) * dt
+    t = np.linspace(0.0, T, H)
+    cols = [si.BPoly(np.eye(n_xi)[c][:, None], [0.0, T]).derivative(2)(t) for c in range(n_xi)]
+    return np.stack(cols, axis=1)
+
+
 def incidence(n):
     """Stacked F_{r,i} = [F_i, -I] of the Appendix: row (i, j>i) is e_i - e_j."""
     rows = []
@@ -84,7 +93,7 @@ def exterior_projection_bruteforce(delta, a):
     return cost_dir(res.x)[1]
 
 
-def one_step_reference(inst, xib, lam, rho, ws_hess=True):
+def one_step_reference(inst, xib, lam, rho, ws_hess=True, Q1=None):
     """One AM sweep (alpha, beta, d, s, lambda, xi_bar) built from the augmented Lagrangian.
 
     Isotropic robots and obstacles only: the joint (alpha, beta, d) minimiser of
@@ -107,8 +116,10 @@ def one_step_reference(inst, xib, lam, rho, ws_hess=True):
         r1 = y[ax] - e[ax]
         r2 = q - h + s
         lam_new[ax] = (lam[ax].ravel() - rho * F.T @ r1 - rho * G.T @ r2).reshape(n, n_xi)
-        Hm = np.eye(n * n_xi) + rho * F.T @ F + (rho * G.T @ G if ws_hess else 0.0)
-        lin = inst["xi"][ax].ravel() + lam_new[ax].ravel() + rho * F.T @ e[ax]
+        # cost: 1/2 ||xi_bar - xi||^2, or with Q1 the smoothness cost 1/2 xi_bar' (I (x) Q1) xi_bar
+        C = np.eye(n * n_xi) if Q1 is None else np.kron(np.eye(n), Q1)
+        Hm = C + rho * F.T @ F + (rho * G.T @ G if ws_hess else 0.0)
+        lin = (inst["xi"][ax].ravel() if Q1 is None else 0.0) + lam_new[ax].ravel() + rho * F.T @ e[ax]
         if ws_hess:
             lin = lin + rho * G.T @ (h - s)
         b = inst["bnd"][ax].reshape(-1)  # (start, goal) per robot, robot-major
@@ -154,8 +165,10 @@ def projection_bruteforce(inst):
     return full(res.x), res
 
 
-def torch_T(inst, rho, W, F, G, A):
-    """Differentiable float64 PyTorch restatement of T (trig closed forms), for gradient pins."""
+def torch_T(inst, rho, W, F, G, A, Q1=None):
+    """Differentiable float64 PyTorch restatement of T (trig closed forms), for gradient pins.
+    Q1: the per-robot smoothness Hessian block (trajectory-optimiser cost) instead of the
+    projection cost."""
     import torch
 
     n, n_obs, H, nd, n_xi = inst["n"], inst["n_obs"], inst["H"], inst["n_d"], inst["n_xi"]
@@ -174,7 +187,8 @@ def torch_T(inst, rho, W, F, G, A):
     Ar, Br = tt(Arad), tt(Brad)
     h = [torch.cat([torch.full((n * H,), float(inst["pmax"][ax]), dtype=torch.float64),
                     torch.full((n * H,), float(-inst["pmin"][ax]), dtype=torch.float64)]) for ax in range(nd)]
-    Hm = torch.eye(n * n_xi, dtype=torch.float64) + rho * Ft.T @ Ft + rho * Gt.T @ Gt
+    Cm = torch.eye(n * n_xi, dtype=torch.float64) if Q1 is None else tt(np.kron(np.eye(n), Q1))
+    Hm = Cm + rho * Ft.T @ Ft + rho * Gt.T @ Gt
     K = torch.cat([torch.cat([Hm, At.T], 1), torch.cat([At, torch.zeros(A.shape[0], A.shape[0], dtype=torch.float64)], 1)], 0)
 
     def estep(D):
@@ -214,7 +228,8 @@ def torch_T(inst, rho, W, F, G, A):
             r1 = y[ax] - e[ax]
             r2 = q - h[ax] + s
             ln = lam[ax].reshape(-1) - rho * Ft.T @ r1 - rho * Gt.T @ r2
-            eta = xi_c[ax].reshape(-1) + ln + rho * Ft.T @ e[ax] + rho * Gt.T @ (h[ax] - s)
+            lin = xi_c[ax].reshape(-1) if Q1 is None else 0.0
+            eta = lin + ln + rho * Ft.T @ e[ax] + rho * Gt.T @ (h[ax] - s)
             bb = tt(inst["bnd"][ax].reshape(-1))
             sol = torch.linalg.solve(K, torch.cat([eta, bb]))
             xs.append(sol[:n * n_xi].reshape(n, n_xi))

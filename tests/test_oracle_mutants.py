@@ -34,6 +34,10 @@ MUTANTS = {
     "adjoint_jacobian_transposed": ("s += J[rr * nd + q] * eb[(size_t)rr * RF + r];",
                                     "s += J[q * nd + rr] * eb[(size_t)rr * RF + r];"),
     "adjoint_slack_gate_inverted": ("qbx[gq] = r2b - sb * act;", "qbx[gq] = r2b - sb * (1.0 - act);"),
+    "smooth_eta_keeps_candidate": ("eta[u] = (P->cost == 0 ? P->xi[(size_t)ax * N + u] : 0.0) + lam_new",
+                                   "eta[u] = P->xi[(size_t)ax * N + u] + lam_new"),
+    "smooth_time_scale_not_squared": ("/ (T * T);", "/ T;"),
+    "adjoint_smooth_candidate_gradient": ("if (P.cost == 0) gx[(size_t)ax * N + u] += etab", "gx[(size_t)ax * N + u] += etab"),
 }
 
 

@@ -409,3 +409,96 @@ def test_fit_pins_endpoints_and_is_optimal():
         d = np.zeros_like(xi)
         d[..., 1:-1] = rng.normal(size=xi[..., 1:-1].shape) * 10 ** rng.uniform(-6, -1)
         assert err(xi + d) >= e0 - 1e-12 * max(e0, 1.0)
+
+
+# ---- trajectory optimiser: smoothness cost (eq. cost, eq. eq::form) ------------------------
+
+DT = 0.05
+
+
+def _q1(H, nxi, dt=DT):
+    Wdd = pinlib.bernstein_dd(H, nxi, dt)
+    return Wdd.T @ Wdd
+
+
+@pytest.mark.parametrize("H,nxi,dt", [(20, 6, 0.1), (100, 11, 0.05), (7, 3, 1.0)])
+def test_smooth_basis_is_bernstein_second_derivative(H, nxi, dt):
+    ref = pinlib.bernstein_dd(H, nxi, dt)
+    np.testing.assert_allclose(oracle.basis_dd(H, nxi, dt), ref, atol=1e-9 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n,n_obs,H,nxi", [(1, 0, 10, 5), (3, 2, 12, 6), (4, 3, 30, 11)])
+def test_smooth_kkt_matches_dense_and_kronecker(n, n_obs, H, nxi):
+    """H = (I (x) Wdd'Wdd) + rho F'F + rho G'G; the Kronecker form keeps P_dev / P_mean with
+    Q1 + rho c W'W in place of I + rho c W'W."""
+    rho = 0.7
+    W, F, G, A = pinlib.dense_mats(n, n_obs, H, nxi)
+    Q1 = _q1(H, nxi)
+    Hm, Pe, Pb = oracle.kkt(2, nxi, rho, n, n_obs, H, cost="smoothness", dt=DT)
+    ref = np.kron(np.eye(n), Q1) + rho * F.T @ F + rho * G.T @ G
+    np.testing.assert_allclose(Hm, ref, atol=1e-10 * np.abs(ref).max())
+    Kinv = np.linalg.inv(np.block([[ref, A.T], [A, np.zeros((2 * n, 2 * n))]]))
+    np.testing.assert_allclose(Pe, Kinv[:n * nxi, :n * nxi], atol=1e-9 * np.abs(Kinv).max())
+    A0 = np.vstack([W[0], W[-1]])
+
+    def cinv(c):
+        Ki = np.linalg.inv(np.block([[Q1 + rho * c * W.T @ W, A0.T], [A0, np.zeros((2, 2))]]))
+        return Ki[:nxi, :nxi], Ki[:nxi, nxi:]
+
+    Qn = np.ones((n, n)) / n
+    (Pd, Bd), (Pm, Bm) = cinv(n + n_obs + 2), cinv(n_obs + 2)
+    np.testing.assert_allclose(Pe, np.kron(np.eye(n) - Qn, Pd) + np.kron(Qn, Pm), atol=1e-9 * np.abs(Pe).max())
+    np.testing.assert_allclose(Pb, np.kron(np.eye(n) - Qn, Bd) + np.kron(Qn, Bm), atol=1e-9 * np.abs(Pb).max())
+
+
+@pytest.mark.parametrize("nd,seed", [(2, 0), (3, 2)])
+def test_smooth_one_sweep_is_block_argmin(nd, seed):
+    """One sweep of the optimiser equals the independently built block minimisers, with the
+    smoothness cost in the xi_bar step and no candidate term."""
+    H = 8
+    inst = pinlib.small_instance(n=3, n_obs=2, H=H, n_d=nd, n_xi=6, seed=seed)
+    rng = np.random.default_rng(200 + seed)
+    xib = inst["xi"] + rng.normal(0, 0.3, size=inst["xi"].shape)
+    lam = rng.normal(0, 0.2, size=inst["xi"].shape)
+    got = oracle.solve(inst, 1, rho=RHO, xi0=xib, lam0=lam, cost="smoothness", dt=DT)
+    ref_x, ref_l = pinlib.one_step_reference(inst, xib, lam, RHO, Q1=_q1(H, 6))
+    np.testing.assert_allclose(got["lam"], ref_l, atol=1e-8)
+    np.testing.assert_allclose(got["xi"], ref_x, atol=1e-8 * max(1.0, np.abs(ref_x).max()))
+
+
+def test_smooth_unconstrained_optimum_is_the_straight_line():
+    """One robot, no obstacles, a box it never touches: the minimum-acceleration trajectory
+    between fixed endpoints is the straight line at constant speed, which the basis holds
+    exactly as the linear ramp of coefficients."""
+    inst = pinlib.small_instance(n=1, n_obs=0, H=30, n_d=2, n_xi=8, seed=5, sigma=0.4, extent=40.0)
+    out = oracle.solve(inst, 3000, rho=1.0, cost="smoothness", dt=0.02)
+    b = inst["bnd"]
+    ramp = b[..., :1] + (b[..., 1:] - b[..., :1]) * np.linspace(0.0, 1.0, 8)
+    assert oracle.residual(inst, out["xi"], rho=1.0)[1] == 0.0
+    np.testing.assert_allclose(out["xi"], ramp, atol=1e-8)
+
+
+def test_smooth_backward_matches_torch_autograd():
+    import torch
+    iters = 5
+    inst = _grad_instance(2, 77, iters, False)
+    W, F, G, A = pinlib.dense_mats(inst["n"], inst["n_obs"], inst["H"], inst["n_xi"])
+    T, rsq = pinlib.torch_T(inst, RHO, W, F, G, A, Q1=_q1(inst["H"], inst["n_xi"]))
+    rng = np.random.default_rng(2)
+    gx_out = rng.normal(size=inst["xi"].shape)
+    gl_out = rng.normal(size=inst["xi"].shape)
+    xi_c = torch.tensor(inst["xi"], requires_grad=True)
+    lam0 = torch.tensor(rng.normal(0, 0.1, size=inst["xi"].shape), requires_grad=True)
+    xi0 = torch.tensor(inst["xi"] + rng.normal(0, 0.05, size=inst["xi"].shape), requires_grad=True)
+    x, l = xi0, lam0
+    for _ in range(iters):
+        x, l = T(x, l, xi_c)
+    loss = (x * torch.tensor(gx_out)).sum() + (l * torch.tensor(gl_out)).sum() + 0.7 * rsq(x)
+    loss.backward()
+    gx, gx0, gl0 = oracle.solve_backward(inst, iters, gx_out, gl_out, 0.7, rho=RHO, xi0=xi0.detach().numpy(),
+                                         lam0=lam0.detach().numpy(), cost="smoothness", dt=DT)
+    assert xi_c.grad is None or np.abs(xi_c.grad.numpy()).max() == 0.0   # the candidate does not enter
+    assert np.abs(gx).max() == 0.0
+    for got, ref in [(gx0, xi0.grad), (gl0, lam0.grad)]:
+        ref = ref.numpy()
+        np.testing.assert_allclose(got, ref, atol=1e-10 * max(1.0, np.abs(ref).max()))
