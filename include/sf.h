@@ -69,6 +69,16 @@ enum {
     SF_PROJ_STRUCTURED = 1  /* same operator through its Kronecker form (n_xi x n_xi blocks) */
 };
 
+/* Cost of the xi_bar step (the constraints and the iteration are the same) */
+enum {
+    SF_COST_PROJECTION = 0, /* the Safety Filter: 1/2 ||xi_bar - xi||^2 to the candidate xi
+                               (eq. proj_cost)                                              */
+    SF_COST_SMOOTHNESS = 1  /* the trajectory optimiser of eq. eq::form: 1/2 sum over robots
+                               and timesteps of ||p''||^2 (eq. cost), p'' in time
+                               t = tau (H - 1) dt; xi_cand then serves only as the default
+                               initial iterate and receives no gradient                   */
+};
+
 /* ---- per-instance shape ---------------------------------------------------- */
 typedef struct sf_shape {
     int32_t n;          /* robots, >= 1                                                    */
@@ -103,6 +113,8 @@ typedef struct sf_desc {
     int32_t n_inst;     /* number of instances, >= 1                                       */
     const sf_shape *shapes; /* host array [n_inst], copied by sf_create                    */
     void *stream;       /* cudaStream_t on which sf_create runs the factorisations         */
+    int32_t cost;       /* SF_COST_PROJECTION (0) or SF_COST_SMOOTHNESS                    */
+    double dt;          /* time step in seconds of the smoothness cost (> 0 when used)     */
 } sf_desc;
 
 typedef struct sf_handle sf_handle;
@@ -195,7 +207,9 @@ int sf_get_status(sf_handle *h, int32_t *per_instance_status);
  *   which = 1: P_eta [N][N]            (N = n * n_xi)
  *   which = 2: P_b [N][2n]             (columns robot-major: start, goal)
  *   which = 3: Kronecker blocks P_dev [n_xi][n_xi], P_mean [n_xi][n_xi],
- *              B_dev [n_xi][2], B_mean [n_xi][2], back to back
+ *              B_dev [n_xi][2], B_mean [n_xi][2], then the per-robot cost block
+ *              [n_xi][n_xi] (the identity, or Wdd' Wdd of the smoothness cost with Wdd
+ *              the basis' second time derivative), back to back
  * Synchronises the device.  Errors: SF_EINVAL, SF_ECUDA.
  */
 int sf_shape_operator(const sf_handle *h, int32_t inst, int32_t which, double *host_out);

@@ -195,6 +195,8 @@ static int validate(const sf_desc *d)
     if (d->precision < SF_FP64 || d->precision > SF_BF16) return SF_EINVAL;
     if (d->proj != SF_PROJ_DENSE && d->proj != SF_PROJ_STRUCTURED) return SF_EINVAL;
     if (d->max_iters < 0 || d->ckpt_every < 0 || d->n_refine < 0 || d->n_refine > 8 || !(d->tol >= 0.0)) return SF_EINVAL;
+    if (d->cost != SF_COST_PROJECTION && d->cost != SF_COST_SMOOTHNESS) return SF_EINVAL;
+    if (d->cost == SF_COST_SMOOTHNESS && (!(d->dt > 0.0) || !isfinite(d->dt) || d->n_xi < 3)) return SF_EINVAL;
     for (int i = 0; i < d->n_inst; ++i) {
         const sf_shape &s = d->shapes[i];
         if (s.n < 1 || s.n > 256 || s.n_obs < 0 || s.n_obs > 4096 || s.H < 2 || s.H > 4096) return SF_EINVAL;
@@ -359,7 +361,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
             oW += (int64_t)s.H * nxi;
             oP += (int64_t)S.N * S.N;
             oPb += (int64_t)S.N * 2 * s.n;
-            oS += 2 * (int64_t)nxi * nxi + 4 * (int64_t)nxi;
+            oS += 3 * (int64_t)nxi * nxi + 4 * (int64_t)nxi;   // Kronecker blocks + cost block
             it = key.emplace(k, (int)h->shapes_h.size()).first;
             h->shapes_h.push_back(S);
         }
@@ -439,7 +441,8 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
         }
         cudaMemsetAsync(info.p, 0, sizeof(int) * h->n_shapes, st);
         cudaError_t e = factor_shapes((const Shape *)h->shapes_dev.p, h->n_shapes, h->shapes_h.data(), nxi,
-                                      desc->rho, (double *)h->W64.p, (double *)h->P64.p, (double *)h->Pb64.p,
+                                      desc->rho, desc->cost, desc->dt, (double *)h->W64.p, (double *)h->P64.p,
+                                      (double *)h->Pb64.p,
                                       (double *)h->S64.p, (double *)scratch.p, 3 * oP, (int *)info.p, st);
         std::vector<int> inf(h->n_shapes, 0);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -532,6 +535,7 @@ static FwdArgs<T> fwd_args(const sf_handle *h, const void *bnd, const void *obs,
     a.status = (int32_t *)h->status_dev.p;
     a.tc_mode = h->tc_mode;
     a.tc_res = h->plan.tc_res;
+    a.cost = h->d.cost;
     a.cull = h->plan.cull;
     a.n_refine = h->tc_mode ? h->d.n_refine : 0;
     a.tcA = (const unsigned char *)h->tcA.p;
@@ -839,7 +843,7 @@ extern "C" int sf_shape_operator(const sf_handle *h, int32_t inst, int32_t which
     case 0: src = (const double *)h->W64.p + S.off_W; cnt = (size_t)S.H * nxi; break;
     case 1: src = (const double *)h->P64.p + S.off_P; cnt = (size_t)S.N * S.N; break;
     case 2: src = (const double *)h->Pb64.p + S.off_Pb; cnt = (size_t)S.N * 2 * S.n; break;
-    default: src = (const double *)h->S64.p + S.off_S; cnt = 2 * (size_t)nxi * nxi + 4 * (size_t)nxi; break;
+    default: src = (const double *)h->S64.p + S.off_S; cnt = 3 * (size_t)nxi * nxi + 4 * (size_t)nxi; break;
     }
     SF_TRY(cudaDeviceSynchronize());
     SF_TRY(cudaMemcpy(host_out, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
@@ -863,4 +867,4 @@ extern "C" const char *sf_strerror(int32_t code)
     }
 }
 
-extern "C" int32_t sf_version(void) { return 100; }
+extern "C" int32_t sf_version(void) { return 200; }

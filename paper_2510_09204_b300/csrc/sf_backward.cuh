@@ -8,14 +8,16 @@
 // the forward's own code (stored per CTA in global scratch) and then reversed.
 //
 // Adjoint of one iteration l in correction form, xi_bar' = xi_bar + P_eta v +
-// P_b (b - A xi_bar) with v = xi - xi_bar + lambda - 2 rho g and lambda' = lambda -
-// rho g, g = W'R(p), p = W xi_bar, from (xi_bar'*, lambda'*):
+// P_b (b - A xi_bar) with v = xi - xi_bar + lambda - 2 rho g (projection cost; the
+// smoothness cost has -Q1 xi_bar per robot in place of xi - xi_bar) and lambda' =
+// lambda - rho g, g = W'R(p), p = W xi_bar, from (xi_bar'*, lambda'*):
 //   x*  = xi_bar'* with its end coefficients cleared (they are overwritten by b)
 //   v*  = P_eta x*                        (P_eta symmetric)
-//   xi*      += v*,   lambda* = lambda'* + v*,   g* = -rho lambda'* - 2 rho v*
+//   xi*      += v* (projection only),   lambda* = lambda'* + v*,   g* = -rho lambda'* - 2 rho v*
 //   R*  = W g*;  p* = sum over active rows of J' (R*_i - R*_j) (pairs; J even, r_1 odd),
 //                J' R*_i (obstacles), mask R*_i (box)
-//   xi_bar*  = x* - v* + W' p*   [- A' P_b' x* at l = 0, the end coefficients of xi_bar^0]
+//   xi_bar*  = x* - v* (- Q1 v* per robot, smoothness) + W' p*
+//              [- A' P_b' x* at l = 0, the end coefficients of xi_bar^0]
 // with J = dr_1/dDelta = (1 - s) I + s^3 Delta (M^-2 Delta)' on active rows and 0 on
 // inactive ones (derivative conventions of the kinks: the clamped branch counts as
 // active, Delta = 0 has zero derivative).
@@ -140,11 +142,19 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             T *vs = X.dd, *gs = X.lam;
             __syncthreads();   // xz of the previous step's gather (or the seed) complete
             X.project(cl, xz, vs, false);
+            if (X.smooth) __syncthreads();   // the cost block mixes a row's coefficients
             for (int e = tid; e < NN; e += nt) {
                 const T vst = vs[e];
                 gs[e] = -rho * ls[e] - T(2) * rho * vst;
-                xn[e] = xz[e] - vst;
-                cs[e] += vst;
+                if (X.smooth) {   // d v / d xi_bar = -Q1 (symmetric); the candidate does not enter
+                    const int r = e / nxi, c = e - r * nxi;
+                    T qv = T(0);
+                    for (int k = 0; k < nxi; ++k) qv += X.Qc[c * nxi + k] * vs[r * nxi + k];
+                    xn[e] = xz[e] - qv;
+                } else {          // d v / d xi_bar = -I, d v / d xi = I
+                    xn[e] = xz[e] - vst;
+                    cs[e] += vst;
+                }
                 ls[e] += vst;
             }
             if (l == 0) {   // - A' P_b' x*: the end coefficients of xi_bar^0

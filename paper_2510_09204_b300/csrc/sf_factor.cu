@@ -36,12 +36,49 @@ __global__ void k_basis(const Shape *sh, int nxi, double *W)
     }
 }
 
-__global__ void k_build_H(const Shape *sh, int nxi, double rho, const double *W, double *Hs)
+// Per-robot block of the cost's Hessian, into the shape's Kronecker record after the
+// projection blocks: the identity (projection cost) or Q1 = Wdd' Wdd (smoothness cost,
+// eq. cost), Wdd the second time derivative of the basis at t_k = k dt: d (d - 1) / T^2
+// times the second difference of the degree-(d - 2) Bernstein polynomials, T = (H-1) dt.
+__global__ void k_cost_block(const Shape *sh, int nxi, int cost, double dt, double *Sx)
+{
+    const Shape S = sh[blockIdx.x];
+    double *Cb = Sx + S.off_S + 2 * nxi * nxi + 4 * nxi;
+    const int deg = nxi - 1, H = S.H;
+    const double T = (double)(H - 1) * dt, scale = (double)deg * (double)(deg - 1) / (T * T);
+    for (int e = threadIdx.x; e < nxi * nxi; e += blockDim.x) {
+        const int u = e / nxi, v = e % nxi;
+        if (cost == SF_COST_PROJECTION) {
+            Cb[e] = u == v ? 1.0 : 0.0;
+            continue;
+        }
+        double q = 0.0;
+        for (int k = 0; k < H; ++k) {
+            const double tau = (double)k / (double)(H - 1);
+            double du = 0.0, dv = 0.0;
+            for (int j = 0; j <= deg - 2; ++j) {
+                double bin = 1.0;
+                for (int t = 1; t <= j; ++t) bin = bin * (double)(deg - 2 - j + t) / (double)t;
+                const double b = bin * pow(tau, (double)j) * pow(1.0 - tau, (double)(deg - 2 - j));
+                // B_c'' gets + b for j = c - 2 and j = c, - 2 b for j = c - 1
+                if (j == u - 2 || j == u) du += b;
+                if (j == u - 1) du -= 2.0 * b;
+                if (j == v - 2 || j == v) dv += b;
+                if (j == v - 1) dv -= 2.0 * b;
+            }
+            q += (scale * du) * (scale * dv);
+        }
+        Cb[e] = q;
+    }
+}
+
+__global__ void k_build_H(const Shape *sh, int nxi, double rho, const double *W, const double *Sx, double *Hs)
 {
     const Shape S = sh[blockIdx.y];
     const int N = S.N;
     double *Hm = Hs + S.off_P;
     const double *Ws = W + S.off_W;
+    const double *Cb = Sx + S.off_S + 2 * nxi * nxi + 4 * nxi;   // per-robot cost block
     const double cdiag = (double)(S.n + S.n_obs + 2);
     const int64_t tot = (int64_t)N * N;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
@@ -50,7 +87,7 @@ __global__ void k_build_H(const Shape *sh, int nxi, double rho, const double *W,
         double wtw = 0.0;
         for (int k = 0; k < S.H; ++k) wtw += Ws[k * nxi + u] * Ws[k * nxi + v];
         const double lap = (i == j ? cdiag : 0.0) - 1.0;
-        Hm[e] = (r == c ? 1.0 : 0.0) + rho * lap * wtw;
+        Hm[e] = (i == j ? Cb[u * nxi + v] : 0.0) + rho * lap * wtw;
     }
 }
 
@@ -312,7 +349,7 @@ cudaError_t arrange_tc(const Shape *shapes_dev, int n_shapes, const Shape *shape
 }
 
 cudaError_t factor_shapes(const Shape *shapes_dev, int n_shapes, const Shape *shapes_host, int nxi,
-                          double rho, double *W64, double *P64, double *Pb64, double *S64,
+                          double rho, int cost, double dt, double *W64, double *P64, double *Pb64, double *S64,
                           double *scratch, int64_t scratch_elems, int *info, cudaStream_t s)
 {
     // scratch holds three pools laid out like P64: L (Cholesky), Y, S
@@ -326,9 +363,10 @@ cudaError_t factor_shapes(const Shape *shapes_dev, int n_shapes, const Shape *sh
     }
     double *Lp = scratch, *Yp = scratch + poolP, *Sp = scratch + 2 * poolP;
     k_basis<<<n_shapes, 256, 0, s>>>(shapes_dev, nxi, W64);
+    k_cost_block<<<n_shapes, 128, 0, s>>>(shapes_dev, nxi, cost, dt, S64);
     const int64_t hblocks = ((int64_t)maxN * maxN + 255) / 256;
     dim3 gH((unsigned)(hblocks > 1024 ? 1024 : hblocks), n_shapes);
-    k_build_H<<<gH, 256, 0, s>>>(shapes_dev, nxi, rho, W64, Lp);
+    k_build_H<<<gH, 256, 0, s>>>(shapes_dev, nxi, rho, W64, S64, Lp);
     k_cholesky<<<n_shapes, 1024, 0, s>>>(shapes_dev, Lp, info);
     dim3 gI((maxN + 31) / 32, n_shapes);
     k_chol_inverse<<<gI, 32, 0, s>>>(shapes_dev, Lp, P64);

@@ -110,7 +110,7 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n,
     c.ob = o;  o += carve_round((opad + 4) * 8, esz);             // obstacle records (+ dummies)
     c.bd = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b
     c.db = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b - A xi_bar^0
-    c.sx = o;  o += carve_round(2 * (int64_t)nxi * nxi + 4 * nxi + 2 * (int64_t)nd * nxi + 2 * nd, esz);
+    c.sx = o;  o += carve_round(3 * (int64_t)nxi * nxi + 4 * nxi + 2 * (int64_t)nd * nxi + 2 * nd, esz);
     c.red = o; o += carve_round(4 * 32, esz);
     c.Ps = o;  o += carve_round((int64_t)p_rows * N, esz);
     // culling, per segment of at most 32 timesteps: boxes [ax][lo, hi][segment][robot |
@@ -158,6 +158,7 @@ struct FwdArgs {
     int tc_mode;      // tensor-core projection: 0 none, 1 TF32, 2 BF16, 3 BF16 x3
     int tc_res;       // the CTA's projector chunks stay resident in shared memory
     int cull;         // row loops over per-chunk candidate lists (bounding-box culling)
+    int cost;         // SF_COST_PROJECTION or SF_COST_SMOOTHNESS (per-robot cost block Q1)
     int n_refine;     // refinement passes of the tensor-core projection
     const unsigned char *tcA;   // arranged P_eta chunks for the current cluster size
     const int64_t *tc_off;      // byte offset of each shape's chunks in tcA
@@ -254,7 +255,7 @@ __host__ __device__ inline int64_t residual_doubles(int nd, int nxi, int H, int 
 // FP64 factorisation of every shape (sf_factor.cu).  W64/P64/Pb64/S64 are pools laid out by
 // Shape offsets; info[s] receives 0 or a failing pivot index + 1.
 cudaError_t factor_shapes(const Shape *shapes_dev, int n_shapes, const Shape *shapes_host, int nxi,
-                          double rho, double *W64, double *P64, double *Pb64, double *S64,
+                          double rho, int cost, double dt, double *W64, double *P64, double *Pb64, double *S64,
                           double *scratch, int64_t scratch_elems, int *info, cudaStream_t s);
 cudaError_t convert_pool(const double *src, float *dst, int64_t n, cudaStream_t s);
 

@@ -157,6 +157,8 @@ struct Cta {
     const T *Prow, *Pbg, *obs_g;
     int64_t gstride;
     T *Pdev, *Pdif, *Bdev, *Bdif, *mv, *pm, *mb;
+    T *Qc;            // per-robot cost block of the smoothness cost (n_xi x n_xi)
+    int smooth;       // the trajectory optimiser's smoothness cost instead of the projection
     int need_b;
     // culled row loops: boxes, candidate lists (partners, obstacles) and their counts
     T *bbx, *osa;
@@ -233,6 +235,8 @@ struct Cta {
         obs_g = A.obs + I.off_obs;
         Pdev = sx; Pdif = sx + nxi * nxi; Bdev = sx + 2 * nxi * nxi; Bdif = Bdev + 2 * nxi;
         mv = Bdif + 2 * nxi; pm = mv + ND * nxi; mb = pm + ND * nxi;
+        Qc = mb + 2 * ND;
+        smooth = A.cost == SF_COST_SMOOTHNESS;
         Prow = nullptr;
         need_b = 0;
         tcm = 0;
@@ -347,6 +351,10 @@ struct Cta {
         if (dense && p_rows > 0)
             for (int e = tid; e < (r_hi - r_lo) * N; e += nt) Ps[e] = Pg[(int64_t)r_lo * N + e];
         Prow = (dense && p_rows > 0) ? Ps - (int64_t)r_lo * N : Pg;   // Prow[r * N + c], r in [r_lo, r_hi)
+        if (smooth) {
+            const T *Cg = A.Sx + S.off_S + 2 * nxi * nxi + 4 * nxi;
+            for (int e = tid; e < nxi * nxi; e += nt) Qc[e] = Cg[e];
+        }
         if (!dense) {
             const T *Sg = A.Sx + S.off_S;
             for (int e = tid; e < nxi * nxi; e += nt) {
@@ -971,7 +979,7 @@ struct Cta {
                 dst[e] = cl.map_shared_rank(dl, fL.q(row))[e];
             }
             // refinement: dst += P~ (src - H dst) on the interior coefficients, the residual in
-            // FP32 through H = I + rho ((n + n_obs + 2) I - 11') (x) W'W
+            // FP32 through H = I (x) C + rho ((n + n_obs + 2) I - 11') (x) W'W, C the cost block
             for (int pass = 0; pass < n_refine; ++pass) {
                 __syncthreads();
                 T *sums = wtw + nxi * nxi;   // [ND][nxi] robot sums of dst
@@ -988,9 +996,12 @@ struct Cta {
                 const T cn = T(n + n_obs_ + 2);
                 for (int e = tid; e < NN; e += nt) {
                     const int r = e / nxi, u = e - r * nxi, ax = fn.q(r);
-                    T hv = T(0);
-                    for (int c = 0; c < nxi; ++c) hv += wtw[u * nxi + c] * (cn * dst[r * nxi + c] - sums[ax * nxi + c]);
-                    const T res = src[e] - (dst[e] + rho * hv);
+                    T hv = T(0), cd = smooth ? T(0) : dst[e];   // C dst: identity or the smoothness block
+                    for (int c = 0; c < nxi; ++c) {
+                        hv += wtw[u * nxi + c] * (cn * dst[r * nxi + c] - sums[ax * nxi + c]);
+                        if (smooth) cd += Qc[u * nxi + c] * dst[r * nxi + c];
+                    }
+                    const T res = src[e] - (cd + rho * hv);
                     rr[e] = (u == 0 || u == nxi - 1) ? T(0) : res;
                 }
                 __syncthreads();
@@ -1095,6 +1106,18 @@ struct Cta {
         }
     }
 
+    // Minus the cost's gradient at xi_bar, element e: xi - xi_bar (projection) or
+    // -(Q1 xi_bar_row)_c (smoothness cost, the same block for every robot).
+    __device__ __forceinline__ T cost_term(int e) const
+    {
+        if (!smooth) return xc[e] - xb[e];
+        const int r = e / nxi, c = e - r * nxi;
+        const T *q = Qc + c * nxi, *x = xb + r * nxi;
+        T s = T(0);
+        for (int k = 0; k < nxi; ++k) s += q[k] * x[k];
+        return -s;
+    }
+
     // update() without side work (the adjoint's recomputation of the iterates)
     __device__ __forceinline__ T update(cg::cluster_group &cl, const T *gme, bool corr_b)
     {
@@ -1161,7 +1184,7 @@ struct Cta {
             const T ln = lam[e] - rho * gg;
             const T dlam = ln - lam[e];
             fp += dlam * dlam;
-            v[e] = xc[e] - xb[e] + ln - rho * gg;
+            v[e] = cost_term(e) + ln - rho * gg;
             lam[e] = ln;
         }
         if (tid >> 5 == (nt >> 5) - 1) side();

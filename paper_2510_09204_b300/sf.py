@@ -24,6 +24,7 @@ SF_RES_RP, SF_RES_MAX, SF_RES_FP, SF_RES_ITERS, SF_NRES = range(5)
 
 PRECISIONS = {"fp64": SF_FP64, "fp32": SF_FP32, "tf32": SF_TF32, "bf16x3": SF_BF16X3, "bf16": SF_BF16}
 PROJECTIONS = {"dense": SF_PROJ_DENSE, "structured": SF_PROJ_STRUCTURED}
+COSTS = {"projection": 0, "smoothness": 1}
 
 # every symbol declared in include/sf.h
 EXPORTS = ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
@@ -43,7 +44,7 @@ class sf_desc(ct.Structure):
     _fields_ = [("n_d", ct.c_int32), ("n_xi", ct.c_int32), ("rho", ct.c_double), ("precision", ct.c_int32),
                 ("proj", ct.c_int32), ("n_refine", ct.c_int32), ("max_iters", ct.c_int32),
                 ("ckpt_every", ct.c_int32), ("tol", ct.c_double), ("n_inst", ct.c_int32),
-                ("shapes", ct.POINTER(sf_shape)), ("stream", ct.c_void_p)]
+                ("shapes", ct.POINTER(sf_shape)), ("stream", ct.c_void_p), ("cost", ct.c_int32), ("dt", ct.c_double)]
 
 
 class sf_instance_data(ct.Structure):
@@ -119,7 +120,7 @@ class SFSolver:
     """
 
     def __init__(self, shapes, n_d, n_xi=11, rho=0.3, precision="fp32", proj="dense", max_iters=1000,
-                 ckpt_every=0, tol=1e-3, n_refine=0, stream=None):
+                 ckpt_every=0, tol=1e-3, n_refine=0, stream=None, cost="projection", dt=0.1):
         if not torch.cuda.is_available():
             raise RuntimeError("SFSolver needs a CUDA device; there is no CPU path")
         L = lib()
@@ -138,7 +139,9 @@ class SFSolver:
         self._shapes = [dict(n=int(s["n"]), n_obs=int(s["n_obs"]), H=int(s["H"]),
                              dyn_obs=bool(s.get("dyn_obs", False))) for s in shapes]
         d = sf_desc(self.n_d, self.n_xi, self.rho, PRECISIONS[precision], PROJECTIONS[proj], int(n_refine),
-                    int(max_iters), int(ckpt_every), float(tol), self.B, arr, _stream(stream))
+                    int(max_iters), int(ckpt_every), float(tol), self.B, arr, _stream(stream), COSTS[cost],
+                    float(dt))
+        self.cost = cost
         h = ct.c_void_p()
         _check(L.sf_create(ct.byref(d), ct.byref(h)), "sf_create")
         self.h = h
@@ -273,7 +276,7 @@ class SFSolver:
         s = self._shapes[k]
         N = s["n"] * self.n_xi
         size = {0: s["H"] * self.n_xi, 1: N * N, 2: N * 2 * s["n"],
-                3: 2 * self.n_xi ** 2 + 4 * self.n_xi}[which]
+                3: 3 * self.n_xi ** 2 + 4 * self.n_xi}[which]
         out = np.empty(size)
         _check(lib().sf_shape_operator(self.h, k, which, out.ctypes.data_as(ct.POINTER(ct.c_double))),
                "sf_shape_operator")
