@@ -383,6 +383,38 @@ def _variant(insts, nd, iters, a, precision, proj, n_refine, dev, stream, flush,
     return out
 
 
+def _optimizer(insts, nd, iters, a, dev, stream, flush, pairs, dt=0.05, reps=10):
+    """The trajectory optimiser (smoothness cost, eq. eq::form) on the same batch and
+    iteration count: forward solve with the FP64 residual check, ms per batch, the final
+    residual and the smoothness cost 1/2 sum xi' Q1 xi from the library's cost block."""
+    import torch
+
+    from paper_2510_09204_b300 import SFSolver
+    s = SFSolver(insts, nd, 11, rho=RHO, precision=a.precision, proj=a.proj, max_iters=iters,
+                 cost="smoothness", dt=dt)
+    d = s.pack(insts, device=dev)
+    if not a.no_autotune:
+        s.autotune(d, d["xi"], iters, reps=1, stream=stream)
+    st = Step(s, d, iters, True, stream)
+    for _ in range(2):
+        st()
+    torch.cuda.synchronize()
+    times, _ = _time_steps(st, reps, stream, flush)
+    ms = statistics.median(times)
+    r = st.res.cpu().numpy()
+    costs = []
+    for k in range(len(insts)):
+        q1 = torch.as_tensor(s.operator(k, 3)[2 * 121 + 44:].reshape(11, 11), device=dev)
+        x = s.unpack(st.xo, k).double()
+        costs.append(0.5 * float(torch.einsum("anc,cd,and->", x, q1, x)))
+    out = {"cost": "smoothness", "dt": dt, "precision": a.precision, "projection": a.proj, "iterations": iters,
+           "ms_per_batch": ms, "value": pairs * iters / (ms * 1e-3), "unit": "pair-timestep updates/s",
+           "final_max_residual_m_median": float(np.median(r[:, 1])),
+           "smoothness_cost_median": float(np.median(costs)), "launch": list(s.launch()[:2])}
+    s.close()
+    return out
+
+
 def main():
     a = args_()
     if a.impl == "reference":
@@ -505,7 +537,7 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
     # plain FP64 GPU solve of the same step, and the tensor-core / structured variants
-    fp64, variants = None, []
+    fp64, variants, optimizer = None, [], None
     if not a.no_compare and rank == 0:
         v64 = _variant(insts, nd, iters, a, "fp64", "dense", 0, dev, stream, flush, None, None, reps=5)
         p64, r64 = v64.pop("_pos"), v64.pop("_res")
@@ -514,6 +546,7 @@ def main():
                     chosen_max_final_residual_diff_m=float(np.abs(r[:, 1] - r64[:, 1]).max()),
                     frac_instances_resid_le_1e3=float(np.mean(r64[:, 1] <= 1e-3)),
                     chosen_speedup=v64["ms_per_step"] / ms_step)
+        optimizer = _optimizer(insts, nd, iters, a, dev, stream, flush, pairs)
         for prec, proj, nr in [("fp32", "structured" if a.proj == "dense" else "dense", 0), ("tf32", "dense", 2),
                                ("bf16x3", "dense", 1), ("bf16", "dense", 3)]:
             if (prec, proj, nr) == (a.precision, a.proj, a.n_refine):
@@ -571,6 +604,8 @@ def main():
             line["fp64_gpu"] = fp64
         if variants:
             line["variants"] = variants
+        if optimizer:
+            line["trajectory_optimizer"] = optimizer
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(insts, iters, a.forward_only)
         print(json.dumps(line), flush=True)
