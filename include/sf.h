@@ -343,6 +343,39 @@ int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_shape *shap
 int sf_fit_positions(int32_t n_d, int32_t n_xi, int32_t n_inst, const int32_t *n, const int32_t *H,
                      const double *pos, double *xi_out, void *stream);
 
+/*
+ * sf_metrics — per instance of the handle, in FP64 from the coefficients `xi` (DEVICE,
+ * packed like sf_solve's arrays, the handle's precision) and the instance data:
+ *   out[k][0] = ||r_p||_2 and out[k][1] = the max residual in metres (as SF_RES_RP,
+ *               SF_RES_MAX; eq. primal_residual),
+ *   out[k][2] = smoothness cost, sum over timesteps of ||p''||^2 averaged across robots,
+ *   out[k][3] = path length, the polygon length of the H positions averaged across robots
+ *               (the paper's trajectory-quality metrics, Sec. V "Metrics"),
+ * with p'' in time t = tau (H - 1) dt, dt from sf_desc (the handle must have dt > 0).
+ * out: DEVICE, double, [n_inst][4].  Asynchronous on `stream`.
+ * Errors: SF_EINVAL, SF_ECUDA.
+ */
+int sf_metrics(sf_handle *h, const sf_instance_data *data, const void *xi, double *out, void *stream);
+
+/*
+ * sf_select — per group of candidates, the indices of the k best, in order (the ranking
+ * stages of the paper's pipeline: keep the candidates of least constraint violation
+ * before the SF; return the feasible one of least smoothness cost after it).
+ * A candidate is feasible when primary <= threshold.  Feasible candidates come first,
+ * ordered by `secondary` (or by `primary` when secondary is NULL); then the others,
+ * ordered by `primary`; NaN scores last; ties to the lower index.
+ *  n_groups, group_size  HOST: groups of consecutive candidates, each 0..4096
+ *  primary, secondary    DEVICE, double, one score per candidate (secondary may be NULL)
+ *  threshold             e.g. -INFINITY to rank every candidate by `primary`
+ *  k                     1..4096
+ *  out_idx               DEVICE, int32, [n_groups][k]: indices within the group, -1 past
+ *                        the group's size
+ * Asynchronous on `stream` (its small scratch is stream-ordered).
+ * Errors: SF_EINVAL, SF_ENOMEM, SF_ECUDA.
+ */
+int sf_select(int32_t n_groups, const int32_t *group_size, const double *primary, const double *secondary,
+              double threshold, int32_t k, int32_t *out_idx, void *stream);
+
 const char *sf_strerror(int32_t code);
 
 /* sf_version — library version as an integer (major * 10000 + minor * 100 + patch). */

@@ -254,6 +254,38 @@ def fit_positions(pos, n_xi, lib=None):
     return xi
 
 
+def metrics(inst, xi_bar, rho=DEFAULT_RHO, dt=DEFAULT_DT, lib=None):
+    """(||r_p||, max residual in m, smoothness cost, path length) of xi_bar: the residuals of
+    ``residual``; the smoothness cost sum_k ||p''_{i|k}||^2 and the path length
+    sum_k ||p_{i|k+1} - p_{i|k}|| averaged over robots (the paper's quality metrics)."""
+    xi_bar = np.asarray(xi_bar, dtype=np.float64)
+    H, nxi = int(inst["H"]), int(inst["n_xi"])
+    r = residual(inst, xi_bar, rho=rho, lib=lib)
+    acc = np.einsum("kc,dic->dik", basis_dd(H, nxi, dt, lib), xi_bar)
+    pos = np.einsum("kc,dic->dik", basis(H, nxi, lib), xi_bar)
+    smooth = (acc ** 2).sum(axis=(0, 2)).mean()
+    path = np.sqrt((np.diff(pos, axis=2) ** 2).sum(axis=0)).sum(axis=1).mean()
+    return np.array([r[0], r[1], smooth, path])
+
+
+def select(scores_primary, scores_secondary=None, threshold=-np.inf, k=1):
+    """Indices of the k best candidates of one group: feasible ones (primary <= threshold)
+    first by secondary (or primary), then the rest by primary, NaN last, ties to the lower
+    index; -1 past the group's size."""
+    p = np.asarray(scores_primary, dtype=np.float64)
+    q = p if scores_secondary is None else np.asarray(scores_secondary, dtype=np.float64)
+
+    def key(j):
+        feas = p[j] <= threshold
+        v = q[j] if feas else p[j]
+        if np.isnan(v):
+            return (2, 0.0, j)
+        return (0 if feas else 1, v, j)
+
+    order = sorted(range(len(p)), key=key)[:k]
+    return order + [-1] * (k - len(order))
+
+
 def positions(xi_bar, H, lib=None):
     """p = W xi_bar for every axis and robot: [n_d][n][H]."""
     W = basis(H, xi_bar.shape[-1], lib)

@@ -59,6 +59,7 @@ struct sf_handle {
     DevBuf Wt, Pt, Pbt, St;            // in T (aliases of the FP64 pools when T = double)
     DevBuf ck_x, ck_l;
     DevBuf seg;                        // adjoint: recomputed iterates of a checkpoint segment
+    DevBuf Wdd64;                      // second time derivative of the basis (metrics; dt > 0)
     DevBuf tcA, tcoff;                 // tensor-core chunks of P_eta for the current cluster size
     int tc_mode = 0, tc_c = 0;
     int cull_req = 1;                  // culled row loops (sf_set_option SF_OPT_CULL)
@@ -250,7 +251,7 @@ static void destroy_all(sf_handle *h)
             h->ev[k] = nullptr;
         }
     DevBuf *bufs[] = {&h->inst_dev, &h->shapes_dev, &h->order_dev, &h->status_dev, &h->W64, &h->P64,
-                      &h->Pb64, &h->S64, &h->ck_x, &h->ck_l, &h->seg, &h->tcA, &h->tcoff};
+                      &h->Pb64, &h->S64, &h->ck_x, &h->ck_l, &h->seg, &h->tcA, &h->tcoff, &h->Wdd64};
     if (h->esz == 4) {
         h->Wt.release();
         h->Pt.release();
@@ -445,6 +446,11 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
                                       (double *)h->Pb64.p,
                                       (double *)h->S64.p, (double *)scratch.p, 3 * oP, (int *)info.p, st);
         std::vector<int> inf(h->n_shapes, 0);
+        if (e == cudaSuccess && desc->dt > 0.0 && isfinite(desc->dt)) {   // basis'' for sf_metrics
+            e = h->Wdd64.alloc(sizeof(double) * oW);
+            if (e == cudaSuccess) e = basis_dd((const Shape *)h->shapes_dev.p, h->n_shapes, nxi, desc->dt,
+                                               (double *)h->Wdd64.p, st);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e == cudaSuccess) e = cudaMemcpy(inf.data(), info.p, sizeof(int) * h->n_shapes, cudaMemcpyDeviceToHost);
         scratch.release();
@@ -587,6 +593,7 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
         r.status = a.status;
         r.smem_doubles = (int64_t)(h->plan.smem_res / sizeof(double));
         r.csize = h->plan.csize;
+        r.its_fixup = 1;
         if (prof) SF_TRY(cudaEventRecord(h->ev[2], st));
         SF_TRY(launch_residual(r, std::min(h->plan.threads, 512), h->plan.smem_res, st));
         if (prof) {
@@ -774,6 +781,40 @@ extern "C" int sf_get_launch(const sf_handle *h, int32_t *cluster, int32_t *thre
     if (threads) *threads = h->plan.threads;
     if (p_rows) *p_rows = h->plan.p_rows;
     return SF_OK;
+}
+
+extern "C" int sf_metrics(sf_handle *h, const sf_instance_data *data, const void *xi, double *out, void *stream)
+{
+    if (!h || !data || !xi || !out || !data->bnd) return SF_EINVAL;
+    if (!h->Wdd64.p) return SF_EINVAL;   // the handle was created without a time step
+    const bool any_obs = h->off[SF_LAYOUT_OBS][h->d.n_inst] > 0;
+    if (any_obs && (!data->obs_c || !data->obs_ab)) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto go = [&](auto tag) -> int {
+        using T = decltype(tag);
+        ResArgs<T> r;
+        memset(&r, 0, sizeof(r));
+        r.nd = h->d.n_d;
+        r.nxi = h->d.n_xi;
+        r.n_inst = h->d.n_inst;
+        r.tol = h->d.tol;
+        r.inst = (const Inst<T> *)h->inst_dev.p;
+        r.shapes = (const Shape *)h->shapes_dev.p;
+        r.W = (const double *)h->W64.p;
+        r.x = (const T *)xi;
+        r.obs = (const T *)data->obs_c;
+        r.oab = (const T *)data->obs_ab;
+        r.resid = out;
+        r.status = (int32_t *)h->status_dev.p;
+        r.smem_doubles = (int64_t)(h->plan.smem_res / sizeof(double));
+        r.csize = h->plan.csize;
+        r.its_fixup = 0;
+        SF_TRY(launch_residual(r, std::min(h->plan.threads, 512), h->plan.smem_res, st));
+        SF_TRY(shape_metrics(r.inst, r.shapes, h->d.n_inst, h->d.n_d, h->d.n_xi, (const double *)h->W64.p,
+                             (const double *)h->Wdd64.p, (const T *)xi, out, st));
+        return SF_OK;
+    };
+    return h->esz == 8 ? go(double(0)) : go(float(0));
 }
 
 extern "C" int sf_set_option(sf_handle *h, int32_t option, int32_t value)

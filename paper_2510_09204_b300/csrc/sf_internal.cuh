@@ -207,6 +207,7 @@ struct ResArgs {
     int32_t *status;
     int64_t smem_doubles;       // dynamic shared memory of the launch, in doubles
     int csize;                  // CTAs per instance (thread-block cluster)
+    int its_fixup;              // update SF_RES_ITERS (a solve's residual check; not for metrics)
 };
 
 // ---- launchers (defined in the .cu files) ---------------------------------
@@ -235,6 +236,11 @@ cudaError_t arrange_tc(const Shape *shapes_dev, int n_shapes, const Shape *shape
                        const int64_t *tc_off_dev, const int64_t *tc_off_host, int mode, int C, unsigned char *out,
                        cudaStream_t s);
 int64_t tc_pool_bytes(int mode, int N, int C);
+cudaError_t basis_dd(const Shape *shapes_dev, int n_shapes, int nxi, double dt, double *Wdd, cudaStream_t s);
+cudaError_t shape_metrics(const Inst<double> *inst, const Shape *shapes, int n_inst, int nd, int nxi, const double *W,
+                          const double *Wdd, const double *x, double *out, cudaStream_t s);
+cudaError_t shape_metrics(const Inst<float> *inst, const Shape *shapes, int n_inst, int nd, int nxi, const double *W,
+                          const double *Wdd, const float *x, double *out, cudaStream_t s);
 
 // Both launch n_inst clusters of a.csize CTAs (one cluster per instance).
 cudaError_t launch_forward(const FwdArgs<double> &a, int threads, size_t smem, cudaStream_t s);

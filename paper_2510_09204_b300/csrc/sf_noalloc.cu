@@ -254,6 +254,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
         r.status = S->status;
         r.smem_doubles = (int64_t)(plan.smem_res / sizeof(double));
         r.csize = plan.csize;
+        r.its_fixup = 1;
         if (launch_residual(r, std::min(threads, 512), plan.smem_res, st) != cudaSuccess) return SF_ECUDA;
     }
     return SF_OK;

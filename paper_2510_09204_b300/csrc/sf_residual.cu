@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(512) k_residual(ResArgs<T> A)
         const double mx = sqrt(s_mx2);
         A.resid[(int64_t)ii * SF_NRES + SF_RES_RP] = sqrt(s_rp2);
         A.resid[(int64_t)ii * SF_NRES + SF_RES_MAX] = mx;
-        const double itv = A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS];
+        const double itv = A.its_fixup ? A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS] : 0.0;
         if (itv < 0.0 && mx <= A.tol) {
             A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS] = (double)A.iters;
             if (A.its) A.its[ii] = A.iters;

@@ -29,8 +29,8 @@ COSTS = {"projection": 0, "smoothness": 1}
 # every symbol declared in include/sf.h
 EXPORTS = ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
            "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch",
-           "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions", "sf_strerror",
-           "sf_version")
+           "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions", "sf_metrics",
+           "sf_select", "sf_strerror", "sf_version")
 SF_OPT_CULL = 1
 SF_KT_FORWARD, SF_KT_RESIDUAL, SF_KT_BACKWARD, SF_NKT = range(4)
 
@@ -86,12 +86,14 @@ def lib(path: str | None = None):
         L.sf_get_launch.argtypes = [vp, ct.POINTER(i32), ct.POINTER(i32), ct.POINTER(i32)]
         L.sf_set_option.argtypes = [vp, i32, i32]
         L.sf_fit_positions.argtypes = [i32, i32, i32, ct.POINTER(i32), ct.POINTER(i32), vp, vp, vp]
+        L.sf_metrics.argtypes = [vp, ct.POINTER(sf_instance_data), vp, vp, vp]
+        L.sf_select.argtypes = [i32, ct.POINTER(i32), vp, vp, ct.c_double, i32, vp, vp]
         L.sf_get_option.argtypes = [vp, i32, ct.POINTER(i32)]
         L.sf_strerror.argtypes = [i32]
         L.sf_strerror.restype = ct.c_char_p
         L.sf_version.restype = i32
         for f in ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
-                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions"):
+                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions", "sf_metrics", "sf_select"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -214,6 +216,14 @@ class SFSolver:
                                        _ptr(g_x0), _ptr(g_l0), _stream(stream)), "sf_solve_backward")
         return g_xc, g_x0, g_l0
 
+    def metrics(self, data, xi, stream=None):
+        """sf_metrics: FP64 [B, 4] device tensor of (||r_p||, max residual in m, smoothness
+        cost, path length) per instance of the coefficients ``xi``."""
+        out = torch.empty((self.B, 4), dtype=torch.float64, device=xi.device)
+        dd = self._data(data)
+        _check(lib().sf_metrics(self.h, ct.byref(dd), _ptr(xi), _ptr(out), _stream(stream)), "sf_metrics")
+        return out
+
     def set_launch(self, cluster=0, threads=0):
         """sf_set_launch: CTAs per instance (0 = automatic) and threads per CTA (0 = 512)."""
         _check(lib().sf_set_launch(self.h, int(cluster), int(threads)), "sf_set_launch")
@@ -316,6 +326,18 @@ def fit_positions(positions, n_xi=11, stream=None):
         res.append(flat[o:o + m].reshape(nd, a.shape[1], n_xi))
         o += m
     return res
+
+
+def select(group_sizes, primary, secondary=None, threshold=float("-inf"), k=1, stream=None):
+    """sf_select: [groups, k] int32 device tensor of the k best candidates of each group of
+    consecutive candidates (feasible = primary <= threshold first, by secondary; then the
+    rest by primary; -1 past a group's size)."""
+    sizes = (ct.c_int32 * len(group_sizes))(*[int(g) for g in group_sizes])
+    out = torch.empty((len(group_sizes), int(k)), dtype=torch.int32, device=primary.device)
+    _check(lib().sf_select(len(group_sizes), sizes, _ptr(primary.contiguous()),
+                           _ptr(None if secondary is None else secondary.contiguous()), float(threshold), int(k),
+                           _ptr(out), _stream(stream)), "sf_select")
+    return out
 
 
 class SFSolve(torch.autograd.Function):

@@ -502,3 +502,34 @@ def test_smooth_backward_matches_torch_autograd():
     for got, ref in [(gx0, xi0.grad), (gl0, lam0.grad)]:
         ref = ref.numpy()
         np.testing.assert_allclose(got, ref, atol=1e-10 * max(1.0, np.abs(ref).max()))
+
+
+# ---- candidate metrics and selection (the ranking stages of the pipeline) -------------------
+
+def test_metrics_of_a_straight_line_and_a_parabola():
+    """A straight line at constant speed has zero smoothness cost and path length
+    ||goal - start||; the parabola s + (g - s) tau + c tau (1 - tau) has the constant
+    acceleration -2 c / T^2, so its smoothness cost is H 4 ||c||^2 / T^4."""
+    H, nxi, dt = 40, 11, 0.05
+    T = (H - 1) * dt
+    rng = np.random.default_rng(8)
+    inst = pinlib.small_instance(n=3, n_obs=0, H=H, n_d=2, n_xi=nxi, seed=3, extent=50.0)
+    b = inst["bnd"]
+    ramp = b[..., :1] + (b[..., 1:] - b[..., :1]) * np.linspace(0.0, 1.0, nxi)
+    m = oracle.metrics(inst, ramp, dt=dt)
+    assert abs(m[2]) <= 1e-18 * H
+    np.testing.assert_allclose(m[3], np.linalg.norm(b[..., 1] - b[..., 0], axis=0).mean(), rtol=1e-12)
+    tau = np.linspace(0.0, 1.0, H)
+    c = rng.normal(size=(2, 3)) * 0.5
+    pos = b[..., :1] + (b[..., 1:] - b[..., :1]) * tau + c[..., None] * tau * (1.0 - tau)
+    xi = oracle.fit_positions(pos, nxi)
+    m = oracle.metrics(inst, xi, dt=dt)
+    np.testing.assert_allclose(m[2], (H * 4.0 * (c ** 2).sum(axis=0) / T ** 4).mean(), rtol=1e-9)
+
+
+def test_select_orders_feasible_by_secondary_then_the_rest():
+    p = [0.5, 1e-4, np.nan, 2e-4, 3.0, 1e-4]
+    q = [9.0, 5.0, 1.0, 4.0, 0.0, 5.0]
+    assert oracle.select(p, q, 1e-3, 6) == [3, 1, 5, 0, 4, 2]
+    assert oracle.select(p, None, -np.inf, 3) == [1, 5, 3]
+    assert oracle.select([1.0, 0.5], None, -np.inf, 4) == [1, 0, -1, -1]
