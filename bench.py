@@ -415,6 +415,47 @@ def _optimizer(insts, nd, iters, a, dev, stream, flush, pairs, dt=0.05, reps=10)
     return out
 
 
+def _pipeline(a, dev, stream, problems=50, per=10, keep=5, iters=500):
+    """The paper's throughput scenario for the pipeline: 50 problems of the 16-robot 2D
+    shape, 10 candidates each (the problem's candidate plus smooth noise), keep the 5 least
+    violating, refine them with `iters` SF iterations and pick the best per problem.
+    Timed end to end through pipeline.refine_candidates (handles, packing, factorisation,
+    every stage), and the 250-trajectory SF solve alone on a prepared handle."""
+    import torch
+
+    from paper_2510_09204_b300 import SFSolver
+    from paper_2510_09204_b300.pipeline import refine_candidates
+    probs = sfgen.make_batch(2, B=problems, start=1000)
+    rng = np.random.default_rng(17)
+    cands = []
+    for p in probs:
+        x = np.repeat(p["xi"][None], per, axis=0)
+        x[..., 1:-1] += rng.normal(0, 0.3, size=x[..., 1:-1].shape)
+        cands.append(x)
+    kw = dict(keep=keep, iters=iters, precision=a.precision, proj=a.proj, rho=RHO)
+    refine_candidates(probs, cands, **kw)   # warm-up (kernels, allocator)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = refine_candidates(probs, cands, **kw)
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t0
+    kept = [dict(probs[g], xi=cands[g][j]) for g in range(problems) for j in out[g]["refined"]]
+    s = SFSolver(kept, 2, 11, rho=RHO, precision=a.precision, proj=a.proj, max_iters=iters)
+    d = s.pack(kept, device=dev)
+    if not a.no_autotune:
+        s.autotune(d, d["xi"], iters, reps=1, stream=stream)
+    st = Step(s, d, iters, True, stream)
+    st()
+    torch.cuda.synchronize()
+    times, _ = _time_steps(st, 5, stream)
+    s.close()
+    return {"problems": problems, "candidates_per_problem": per, "kept": keep, "trajectories_refined": len(kept),
+            "robots": 16, "iterations": iters, "precision": a.precision, "projection": a.proj,
+            "ms_end_to_end": 1e3 * total, "ms_sf_solve_250": statistics.median(times),
+            "feasible_fraction": float(np.mean([o["feasible"] for o in out])),
+            "paper": "< 300 ms to refine 250 trajectories (RTX 5090, JAX; robots and iterations not stated)"}
+
+
 def main():
     a = args_()
     if a.impl == "reference":
@@ -537,7 +578,7 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
     # plain FP64 GPU solve of the same step, and the tensor-core / structured variants
-    fp64, variants, optimizer = None, [], None
+    fp64, variants, optimizer, pipeline = None, [], None, None
     if not a.no_compare and rank == 0:
         v64 = _variant(insts, nd, iters, a, "fp64", "dense", 0, dev, stream, flush, None, None, reps=5)
         p64, r64 = v64.pop("_pos"), v64.pop("_res")
@@ -547,6 +588,7 @@ def main():
                     frac_instances_resid_le_1e3=float(np.mean(r64[:, 1] <= 1e-3)),
                     chosen_speedup=v64["ms_per_step"] / ms_step)
         optimizer = _optimizer(insts, nd, iters, a, dev, stream, flush, pairs)
+        pipeline = _pipeline(a, dev, stream)
         for prec, proj, nr in [("fp32", "structured" if a.proj == "dense" else "dense", 0), ("tf32", "dense", 2),
                                ("bf16x3", "dense", 1), ("bf16", "dense", 3)]:
             if (prec, proj, nr) == (a.precision, a.proj, a.n_refine):
@@ -606,6 +648,8 @@ def main():
             line["variants"] = variants
         if optimizer:
             line["trajectory_optimizer"] = optimizer
+        if pipeline:
+            line["pipeline"] = pipeline
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(insts, iters, a.forward_only)
         print(json.dumps(line), flush=True)

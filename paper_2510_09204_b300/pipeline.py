@@ -14,9 +14,11 @@ from .sf import SFSolver, select
 
 
 def refine_candidates(problems, candidates, keep=10, iters=200, precision="fp32", proj="structured",
-                      tol=1e-3, rho=0.3, dt=0.05, n_xi=11, stream=None):
+                      tol=1e-3, rho=0.3, dt=0.05, n_xi=11, autotune=False, stream=None):
     """problems: instance dicts (shape and data; their "xi" is not used); candidates: per
-    problem an array [m][n_d][n][n_xi] of candidate coefficients.  Returns per problem a
+    problem an array [m][n_d][n][n_xi] of candidate coefficients.  autotune: time the launch
+    geometries of the refinement batch first (worth it when the same batch shape recurs).
+    Returns per problem a
     dict with the chosen coefficients, the candidate's index, its metrics
     (||r_p||, max residual, smoothness cost, path length) after refinement, whether it is
     feasible (max residual <= tol), and the indices that were refined."""
@@ -37,7 +39,8 @@ def refine_candidates(problems, candidates, keep=10, iters=200, precision="fp32"
     s2 = SFSolver(batch, nd, n_xi, rho=rho, precision=precision, proj=proj, max_iters=max(iters, 1), tol=tol,
                   dt=dt, stream=stream)
     d2 = s2.pack(batch, device=dev)
-    s2.autotune(d2, d2["xi"], max(iters, 1), reps=1, stream=stream)
+    if autotune:   # costs several solves; the automatic geometry covers the SMs already
+        s2.autotune(d2, d2["xi"], max(iters, 1), reps=1, stream=stream)
     xo, _, _ = s2.solve(d2, d2["xi"], iters, want_resid=False, stream=stream)
     # stage 3: feasible first by smoothness cost, else least residual
     m2 = s2.metrics(d2, xo, stream=stream)
