@@ -26,7 +26,7 @@
 
 namespace sf {
 
-template <typename T, int ND, int MAXT, bool TC, int NXI>
+template <typename T, int ND, int MAXT, bool TC, int NXI, int MODE>
 __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
 {
     using VP = Vec<T, NDP<ND>::v>;
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     const Inst<T> I0 = A.inst[ii];
     const BwdCarve cv = backward_carve(ND, NXI > 0 ? NXI : A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
                                     tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
-    Cta<T, ND, TC, NXI> X;
+    Cta<T, ND, TC, NXI, MODE> X;
     X.init(A, smem_raw, cv.f, ii, cr, C);
     X.load_constants(A, A.p_rows);
     X.tc_setup(A, smem_raw);
@@ -204,13 +204,21 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
-// n_xi = 11 (the default basis) runs a specialisation with the coefficient count fixed at
-// compile time (FP32 kernels); other sizes, and FP64, the generic kernel.
+// The default configuration runs a kernel with its choices fixed at compile time (the
+// code of the other choices compiled away): FP32, n_xi = 11, culled rows, the projection
+// cost, and the structured (MODE 1) or dense (MODE 2) projection.  Every other
+// combination runs the generic kernel, whose choices are runtime flags.
 template <typename T, int ND, int MAXT, bool TC>
 static cudaError_t go_backward(const BwdArgs<T> &a, int nxi, int ni, int cs, int threads, size_t smem, cudaStream_t s)
 {
-    if (sizeof(T) == 4 && nxi == 11) return launch_cluster(k_backward<T, ND, MAXT, TC, sizeof(T) == 4 ? 11 : 0>, a, ni, cs, threads, smem, s);
-    return launch_cluster(k_backward<T, ND, MAXT, TC, 0>, a, ni, cs, threads, smem, s);
+    constexpr bool f32 = sizeof(T) == 4;
+    const auto &f = a.f;
+    if (f32 && nxi == 11 && f.cull && f.cost == SF_COST_PROJECTION) {
+        if (f.proj == SF_PROJ_DENSE)
+            return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 2 : 0>, a, ni, cs, threads, smem, s);
+        if (!TC) return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 1 : 0>, a, ni, cs, threads, smem, s);
+    }
+    return launch_cluster(k_backward<T, ND, MAXT, TC, 0, 0>, a, ni, cs, threads, smem, s);
 }
 
 // Launch for one dimension: tensor-core projection or not, 512- or 1024-thread CTAs.

@@ -142,8 +142,10 @@ __device__ __forceinline__ void block_reduce3_to(T a, T b, T c, T *red)
 
 // TC: compile in the tensor-core projection (FP32 only); other instantiations stay lean.
 // NXI > 0: the coefficient count fixed at compile time (loops over it unroll, divisions by
-// it become multiplications); 0: taken from the arguments.
-template <typename T, int ND, bool TC = false, int NXI = 0>
+// it become multiplications); 0: taken from the arguments.  MODE 0: the projection form,
+// culling and cost are runtime flags; MODE 1 / 2: fixed to culled rows with the
+// projection cost and the structured (1) or dense (2) projection.
+template <typename T, int ND, bool TC = false, int NXI = 0, int MODE = 0>
 struct Cta {
     using VP = Vec<T, NDP<ND>::v>;
     int tid, nt, C, cr, nxi, n, npad, H, N, NN, nobs, opad, hc, k_lo, k_hi, L, r_lo, r_hi, ii;
@@ -201,7 +203,7 @@ struct Cta {
         hc = I.hc;
         rho = A.rho;
         invn = T(1) / T(n);
-        dense = A.proj == SF_PROJ_DENSE;
+        dense = MODE == 2 ? true : MODE == 1 ? false : A.proj == SF_PROJ_DENSE;
         k_lo = (int)((int64_t)cr * H / C);
         k_hi = (int)((int64_t)(cr + 1) * H / C);
         L = (N + C - 1) / C;
@@ -212,7 +214,7 @@ struct Cta {
         Rb = sm + cv.Rb; ob = sm + cv.ob;
         n_refine = A.n_refine;
         n_obs_ = I.n_obs;
-        cull = A.cull;
+        cull = MODE ? 1 : A.cull;
         bbx = sm + cv.bb;
         osa = sm + cv.os;
         lpl = reinterpret_cast<unsigned short *>(sm + cv.lp);
@@ -236,7 +238,7 @@ struct Cta {
         Pdev = sx; Pdif = sx + nxi * nxi; Bdev = sx + 2 * nxi * nxi; Bdif = Bdev + 2 * nxi;
         mv = Bdif + 2 * nxi; pm = mv + ND * nxi; mb = pm + ND * nxi;
         Qc = mb + 2 * ND;
-        smooth = A.cost == SF_COST_SMOOTHNESS;
+        smooth = MODE ? 0 : A.cost == SF_COST_SMOOTHNESS;
         Prow = nullptr;
         need_b = 0;
         tcm = 0;
