@@ -147,6 +147,9 @@ enum {
  * changes with rho or the horizon).  Runs on desc->stream and synchronises it.
  * On success *out owns all device memory of the solver.
  * Errors: SF_EINVAL (bad sizes/values, NULL), SF_ENOMEM, SF_ECUDA, SF_EUNSUPPORTED.
+ * On any error every allocation made so far is freed and *out is NULL.  For tests of
+ * that unwinding, the environment variable SF_TEST_FAIL_ALLOC = k (k >= 0) makes the
+ * (k+1)-th device allocation of this call fail as out of memory (SF_ENOMEM).
  */
 int sf_create(const sf_desc *desc, sf_handle **out);
 
@@ -245,18 +248,27 @@ int sf_get_launch(const sf_handle *h, int32_t *cluster, int32_t *threads, int32_
 
 /* Options of sf_set_option / sf_get_option */
 enum {
-    SF_OPT_CULL = 1   /* row culling: 1 (default) loops, per chunk of timesteps, over the
+    SF_OPT_CULL = 1,  /* row culling: 1 (default) loops, per chunk of timesteps, over the
                          partners and obstacles whose bounding boxes come within the
                          activity threshold of the robot's box (steps alpha..d of the
                          iteration, and their adjoint); 0 loops over all of them.  The
                          two give identical bits: a culled row is inactive throughout
                          the chunk and contributes nothing.  Culling is dropped silently
                          when its lists do not fit in shared memory.                   */
+    SF_OPT_TEST_TIMEOUT = 2, /* tests of the failure path only: 1 gives the tensor-core
+                         projection's pipeline waits a zero polling budget, so the first
+                         wait of each CTA gives up at once, no MMA is issued, the copies
+                         in flight are still drained before the CTA exits, and every
+                         instance reports SF_ETIMEOUT; 0 (default) restores the budget */
+    SF_OPT_TC_RESIDENT = 3  /* read-only: 1 when the plan keeps each CTA's tensor-core
+                         projector rows resident in shared memory (loaded once per solve),
+                         0 when they stream through a two-stage ring every projection   */
 };
 
 /*
  * sf_set_option — set an option (SF_OPT_*) and re-plan the launch with the current
- * geometry (synchronises the device).  Errors: SF_EINVAL (unknown option or value),
+ * geometry (synchronises the device).  Errors: SF_EINVAL (unknown or read-only
+ * option, bad value),
  * SF_EUNSUPPORTED (the re-plan does not fit).
  * sf_get_option — the option's effective value in the current plan (for SF_OPT_CULL,
  * 0 when culling was requested but does not fit).

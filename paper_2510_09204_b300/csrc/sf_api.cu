@@ -11,11 +11,24 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sf_internal.cuh"
 
 using namespace sf;
 
 namespace {
+
+// NVTX range around a host entry point (visible in nsys / ncu timelines).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Simulated allocation failure for tests of the unwinding paths (no device fault): the
+// environment variable SF_TEST_FAIL_ALLOC = k makes the (k+1)-th device allocation of
+// the next sf_create on this thread fail as out of memory.  Unset: -1, no effect.
+thread_local int t_fail_countdown = -1;
 
 struct DevBuf {
     void *p = nullptr;
@@ -24,6 +37,11 @@ struct DevBuf {
     {
         bytes = b;
         if (b == 0) return cudaSuccess;
+        if (t_fail_countdown == 0) {
+            bytes = 0;
+            return cudaErrorMemoryAllocation;
+        }
+        if (t_fail_countdown > 0) --t_fail_countdown;
         return cudaMalloc(&p, b);
     }
     void release()
@@ -63,6 +81,7 @@ struct sf_handle {
     DevBuf tcA, tcoff;                 // tensor-core chunks of P_eta for the current cluster size
     int tc_mode = 0, tc_c = 0;
     int cull_req = 1;                  // culled row loops (sf_set_option SF_OPT_CULL)
+    int test_timeout = 0;              // SF_OPT_TEST_TIMEOUT: zero polling budget
     int n_slots = 0;
     int64_t xi_total = 0;
     // launch configuration
@@ -311,6 +330,14 @@ static int build_tc_pool(sf_handle *h, cudaStream_t st)
 
 extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
 {
+    NvtxRange nv("sf_create");
+    {
+        const char *fa = getenv("SF_TEST_FAIL_ALLOC");
+        t_fail_countdown = fa ? atoi(fa) : -1;
+    }
+    struct CountdownOff {
+        ~CountdownOff() { t_fail_countdown = -1; }
+    } countdown_off;
     if (!out) return SF_EINVAL;
     *out = nullptr;
     int rc = validate(desc);
@@ -542,6 +569,7 @@ static FwdArgs<T> fwd_args(const sf_handle *h, const void *bnd, const void *obs,
     a.tc_mode = h->tc_mode;
     a.tc_res = h->plan.tc_res;
     a.cost = h->d.cost;
+    a.wait_budget = h->test_timeout ? 0u : kWaitLimit;
     a.cull = h->plan.cull;
     a.n_refine = h->tc_mode ? h->d.n_refine : 0;
     a.tcA = (const unsigned char *)h->tcA.p;
@@ -608,6 +636,7 @@ extern "C" int sf_solve(sf_handle *h, const sf_instance_data *data, const void *
                         const void *lam0, int32_t iters, void *xi_out, void *lam_out, double *resid_out,
                         int32_t *iters_to_tol, void *stream)
 {
+    NvtxRange nv("sf_solve");
     if (!h || !data || !xi_cand || !xi_out || !data->bnd) return SF_EINVAL;
     if (iters < 0 || iters > h->d.max_iters) return SF_EINVAL;
     bool any_obs = h->off[SF_LAYOUT_OBS][h->d.n_inst] > 0;
@@ -631,6 +660,7 @@ extern "C" int sf_solve(sf_handle *h, const sf_instance_data *data, const void *
 extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void *g_lam_out, const double *g_rp2,
                                  void *g_xi_cand, void *g_xi0, void *g_lam0, void *stream)
 {
+    NvtxRange nv("sf_solve_backward");
     if (!h || !g_xi_cand) return SF_EINVAL;
     if (!h->last.valid) return SF_ESTATE;
     if (!h->plan.smem_bwd) return SF_EUNSUPPORTED;
@@ -694,6 +724,7 @@ extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
 extern "C" int sf_autotune(sf_handle *h, const sf_instance_data *data, const void *xi_cand, int32_t iters,
                            int32_t reps, void *stream, int32_t *best_cluster, int32_t *best_threads, float *best_ms)
 {
+    NvtxRange nv("sf_autotune");
     if (!h || !data || !xi_cand || iters < 1 || iters > h->d.max_iters || reps < 1) return SF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)h->xi_total * h->esz;
@@ -785,6 +816,7 @@ extern "C" int sf_get_launch(const sf_handle *h, int32_t *cluster, int32_t *thre
 
 extern "C" int sf_metrics(sf_handle *h, const sf_instance_data *data, const void *xi, double *out, void *stream)
 {
+    NvtxRange nv("sf_metrics");
     if (!h || !data || !xi || !out || !data->bnd) return SF_EINVAL;
     if (!h->Wdd64.p) return SF_EINVAL;   // the handle was created without a time step
     const bool any_obs = h->off[SF_LAYOUT_OBS][h->d.n_inst] > 0;
@@ -820,6 +852,11 @@ extern "C" int sf_metrics(sf_handle *h, const sf_instance_data *data, const void
 extern "C" int sf_set_option(sf_handle *h, int32_t option, int32_t value)
 {
     if (!h) return SF_EINVAL;
+    if (option == SF_OPT_TEST_TIMEOUT) {
+        if (value != 0 && value != 1) return SF_EINVAL;
+        h->test_timeout = value;
+        return SF_OK;
+    }
     if (option == SF_OPT_CULL) {
         if (value != 0 && value != 1) return SF_EINVAL;
         const int keep = h->cull_req;
@@ -836,6 +873,14 @@ extern "C" int sf_get_option(const sf_handle *h, int32_t option, int32_t *value)
     if (!h || !value) return SF_EINVAL;
     if (option == SF_OPT_CULL) {
         *value = h->plan.cull;
+        return SF_OK;
+    }
+    if (option == SF_OPT_TEST_TIMEOUT) {
+        *value = h->test_timeout;
+        return SF_OK;
+    }
+    if (option == SF_OPT_TC_RESIDENT) {
+        *value = h->plan.tc_res;
         return SF_OK;
     }
     return SF_EINVAL;

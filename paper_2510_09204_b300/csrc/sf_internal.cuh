@@ -49,6 +49,7 @@ __host__ __device__ inline int tc_nk(int mode, int N) { return (N + tc_kc(mode) 
 __host__ __device__ inline int tc_na(int mode) { return mode == 3 ? 2 : 1; }          // A (and B) parts
 __host__ __device__ inline int tc_ntiles(int N, int C) { return (((N + C - 1) / C) + 127) / 128; }
 constexpr int kTcChunkBytes = 128 * 128;   // one 128-row x 128-byte A chunk
+constexpr uint32_t kWaitLimit = 1u << 20;   // polls of a bounded mbarrier wait (tens of ms)
 
 // A ring stages of a CTA: every chunk of its rows when they stay resident in shared
 // memory for the whole launch (res), else two stages that stream from global memory.
@@ -159,6 +160,7 @@ struct FwdArgs {
     int tc_res;       // the CTA's projector chunks stay resident in shared memory
     int cull;         // row loops over per-chunk candidate lists (bounding-box culling)
     int cost;         // SF_COST_PROJECTION or SF_COST_SMOOTHNESS (per-robot cost block Q1)
+    uint32_t wait_budget;   // polls of the tensor-core pipeline's waits (0 only in tests)
     int n_refine;     // refinement passes of the tensor-core projection
     const unsigned char *tcA;   // arranged P_eta chunks for the current cluster size
     const int64_t *tc_off;      // byte offset of each shape's chunks in tcA

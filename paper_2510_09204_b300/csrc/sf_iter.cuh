@@ -19,7 +19,6 @@ namespace sf {
 
 namespace cg = cooperative_groups;
 
-constexpr uint32_t kWaitLimit = 1u << 20;   // polls of a bounded mbarrier wait (tens of ms)
 
 template <typename T> __device__ __forceinline__ T rsq(T x);
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
@@ -173,13 +172,14 @@ struct Cta {
     T cdel;           // inflation of the robots' boxes
     // tensor-core projection (FP32 kernels, dense mode)
     int tcm, tc_nK, tc_nT, tc_na, tc_es, tc_bbytes, tc_sbo_b, tc_res;
+    uint32_t wbud;             // polls of a pipeline wait; the teardown's drain always uses kWaitLimit
     unsigned char *tc_ring, *tc_B;
     uint64_t *tc_bar;          // full[2], empty[2], done
     int *tc_flag;              // sticky failure flag
     uint32_t *tc_slot;         // tensor-memory address written by tcgen05.alloc
     // per ring stage s: full-barrier phases waited (fw), loads issued (ld), MMA commits (ec);
     // scalars, not arrays, so that a runtime stage index keeps the object in registers
-    uint32_t tmem_base, tmem_cols, tc_done, tc_fw0, tc_fw1, tc_ld0, tc_ld1, tc_ec0, tc_ec1;
+    uint32_t tmem_base, tmem_cols, tc_done, tc_seen, tc_fw0, tc_fw1, tc_ld0, tc_ld1, tc_ec0, tc_ec1;
     const unsigned char *tc_src;
 
     __device__ __forceinline__ void init(const FwdArgs<T> &A, unsigned char *smem_raw, const FwdCarve &cv, int inst, int rank, int csize)
@@ -259,6 +259,7 @@ struct Cta {
             tc_bbytes = 16 * kpad * tc_es;
             tc_sbo_b = (kpad * tc_es / 16) * 128;
             tc_res = A.tc_res;
+            wbud = A.wait_budget;
             tc_ring = smem_raw;
             tc_B = tc_ring + (int64_t)tc_stages(tcm, N, C, tc_res) * kTcChunkBytes * tc_na;
             unsigned char *bars = tc_B + (int64_t)tc_bbytes * tc_na + tc_bbytes + 1024;
@@ -286,7 +287,7 @@ struct Cta {
                         tc::bulk_g2s(tc_ring + (int64_t)w * stage_bytes, tc_src + (int64_t)w * stage_bytes, stage_bytes,
                                      tc_bar);
                     tc_ld0 = 1;
-                    if (tc::mbar_wait(tc_bar, 0, kWaitLimit)) tc_fw0 = 1;
+                    if (tc::mbar_wait(tc_bar, 0, wbud)) tc_fw0 = 1;
                     else *tc_flag = 1;
                 }
             }
@@ -300,7 +301,7 @@ struct Cta {
             __syncthreads();
             tc::fence_after_sync();
             tmem_base = *tc_slot;
-            tc_done = 0;
+            tc_done = tc_seen = 0;
         }
     }
 
@@ -312,6 +313,8 @@ struct Cta {
             if (tid == 0) {
                 while (tc_fw0 < tc_ld0 && tc::mbar_wait(tc_bar + 0, tc_fw0 & 1, kWaitLimit)) ++tc_fw0;
                 while (tc_fw1 < tc_ld1 && tc::mbar_wait(tc_bar + 1, tc_fw1 & 1, kWaitLimit)) ++tc_fw1;
+                // an MMA commit whose completion a timed-out wait did not observe
+                while (tc_seen < tc_done && tc::mbar_wait(tc_bar + 4, tc_seen & 1, kWaitLimit)) ++tc_seen;
             }
             tc::fence_before_sync();
             __syncthreads();
@@ -907,7 +910,7 @@ struct Cta {
                 for (int w = 0; w < items && !tc_res; ++w) {
                     const int st = w & 1;
                     const uint32_t fw = st ? tc_fw1 : tc_fw0;
-                    if (!tc::mbar_wait(tc_bar + st, fw & 1, kWaitLimit)) {
+                    if (!tc::mbar_wait(tc_bar + st, fw & 1, wbud)) {
                         bad = true;
                         break;
                     }
@@ -919,7 +922,7 @@ struct Cta {
                     if (st) ++tc_ec1; else ++tc_ec0;
                     if (w + 2 < items) {
                         const uint32_t ec = st ? tc_ec1 : tc_ec0;
-                        if (!tc::mbar_wait(tc_bar + 2 + st, (ec - 1) & 1, kWaitLimit)) {
+                        if (!tc::mbar_wait(tc_bar + 2 + st, (ec - 1) & 1, wbud)) {
                             bad = true;
                             break;
                         }
@@ -934,10 +937,12 @@ struct Cta {
             }
             bool ok = !failed;
             if (!failed) {
-                ok = tc::mbar_wait(tc_bar + 4, tc_done & 1, kWaitLimit);
+                ok = tc::mbar_wait(tc_bar + 4, tc_done & 1, wbud);
                 ++tc_done;
+                if (ok) tc_seen = tc_done;
             }
             ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+            if (!ok && (tid & 31) == 0) *tc_flag = 1;   // later calls skip the tensor cores
             tc::fence_after_sync();
             const int wp = tid >> 5, lane = tid & 31;
             if (wp < 4) {
@@ -1056,14 +1061,21 @@ struct Cta {
         } else {
             // Kronecker form, per axis with robot mean m of src:
             //   dst_i = P_dev src_i + (P_mean - P_dev) m   (+ the same with B for b - A xi_bar)
-            const int lane = tid & 31, nw = nt >> 5;
-            for (int pq = tid >> 5; pq < ND * nxi; pq += nw) {
+            // robot means: one thread per (axis, coefficient), four independent partial sums
+            // (shorter than a warp's shuffle reduction for tens of robots)
+            for (int pq = tid; pq < ND * nxi; pq += nt) {
                 const int ax = pq / nxi, c = pq - ax * nxi;
-                T s = T(0);
-                for (int i = lane; i < n; i += 32) s += src[(ax * n + i) * nxi + c];
-#pragma unroll
-                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) mv[pq] = s * invn;
+                const T *sp = src + ax * n * nxi + c;
+                T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+                int i = 0;
+                for (; i + 3 < n; i += 4) {
+                    s0 += sp[i * nxi];
+                    s1 += sp[(i + 1) * nxi];
+                    s2 += sp[(i + 2) * nxi];
+                    s3 += sp[(i + 3) * nxi];
+                }
+                for (; i < n; ++i) s0 += sp[i * nxi];
+                mv[pq] = ((s0 + s1) + (s2 + s3)) * invn;
             }
             __syncthreads();
             for (int e = tid; e < ND * nxi; e += nt) {

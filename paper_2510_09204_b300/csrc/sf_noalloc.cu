@@ -219,6 +219,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
     a.csize = plan.csize;
     a.p_rows = 0;
     a.cull = plan.cull;
+    a.wait_budget = kWaitLimit;
     a.proj = SF_PROJ_STRUCTURED;
     a.rho = (float)rho;
     a.tol = 1e-3;

@@ -1,0 +1,183 @@
+"""Failure detection without a GPU fault.
+
+- A bounded wait that runs out: SF_OPT_TEST_TIMEOUT gives the tensor-core pipeline's
+  waits a zero polling budget; every instance must report SF_ETIMEOUT (forward and
+  adjoint), the copies in flight are drained, and the same handle then solves normally,
+  bit for bit like a fresh one.  Both the resident and the streaming projector paths.
+- An allocation that fails: SF_TEST_FAIL_ALLOC = k fails the (k+1)-th device allocation
+  of sf_create; every k must give SF_ENOMEM, a NULL handle and no leaked memory.
+- A non-finite input: only the instance that holds it reports SF_ENONFINITE; the other
+  instances' outputs are the same bits as in a batch without it.
+- Run-to-run determinism: two solves of the same batch give identical bits."""
+import ctypes as ct
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import sfgen
+from paper_2510_09204_b300 import SFSolver, SFError
+from paper_2510_09204_b300.sf import (SF_OPT_TEST_TIMEOUT, SF_OPT_TC_RESIDENT, SF_ENOMEM, SF_ETIMEOUT,
+                                      SF_ENONFINITE, lib, sf_desc, sf_shape, PRECISIONS, PROJECTIONS, COSTS)
+
+pytestmark = pytest.mark.gpu
+RHO = 0.3
+
+
+def _bits(t):
+    return t.detach().cpu().numpy().view(np.uint32 if t.dtype == torch.float32 else np.uint64).copy()
+
+
+def _solve(s, insts, iters, backward=False):
+    data = s.pack(insts)
+    xo, lo, res = s.solve(data, data["xi"], iters)
+    out = dict(xi=_bits(xo), lam=_bits(lo))
+    if backward:
+        g = torch.ones_like(xo)
+        gx = s.backward(g, want_xi0=False, want_lam0=False)
+        out["g"] = _bits(gx[0])
+    torch.cuda.synchronize()
+    out["status"] = s.status()
+    return out
+
+
+CASES = {
+    # 4 robots: the 44 x 44 projector fits in shared memory whatever the cluster
+    "resident": (lambda: [sfgen.custom_instance(n=4, n_obs=2, H=20, seed=s, extent=6.0) for s in range(3)], 0),
+    # 32 robots on one CTA: the 352 x 352 projector streams through the ring
+    "streaming": (lambda: [sfgen.custom_instance(n=32, n_obs=8, H=40, seed=s, extent=10.0) for s in range(2)], 1),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("precision", ["tf32", "bf16x3"])
+def test_zero_wait_budget_reports_timeout_and_the_handle_recovers(case, precision):
+    make, cluster = CASES[case]
+    insts = make()
+    s = SFSolver(insts, insts[0]["n_d"], insts[0]["n_xi"], rho=RHO, precision=precision, proj="dense",
+                 max_iters=8, ckpt_every=1)
+    if cluster:
+        s.set_launch(cluster, 0)
+    expect_res = 1 if case == "resident" else 0
+    assert s.option(SF_OPT_TC_RESIDENT) == expect_res
+    fresh = _solve(s, insts, 8, backward=True)
+    assert (fresh["status"] == 0).all()
+
+    s.set_option(SF_OPT_TEST_TIMEOUT, 1)
+    assert s.option(SF_OPT_TEST_TIMEOUT) == 1
+    data = s.pack(insts)
+    s.solve(data, data["xi"], 8)
+    torch.cuda.synchronize()
+    assert (s.status() == SF_ETIMEOUT).all()
+    assert (s.status() == 0).all()          # sf_get_status clears the words it returns
+    xo, _, _ = s.solve(data, data["xi"], 8)
+    s.backward(torch.ones_like(xo), want_xi0=False, want_lam0=False)
+    torch.cuda.synchronize()
+    assert (s.status() == SF_ETIMEOUT).all()
+
+    s.set_option(SF_OPT_TEST_TIMEOUT, 0)
+    again = _solve(s, insts, 8, backward=True)
+    assert (again["status"] == 0).all()
+    for key in ("xi", "lam", "g"):
+        np.testing.assert_array_equal(again[key], fresh[key])
+    s.close()
+
+
+def test_read_only_and_unknown_options_are_rejected():
+    insts = sfgen.make_batch(2, B=1)
+    s = SFSolver(insts, 2, insts[0]["n_xi"], precision="fp32", proj="dense")
+    for opt, val in [(SF_OPT_TC_RESIDENT, 1), (SF_OPT_TEST_TIMEOUT, 2), (99, 0)]:
+        with pytest.raises(SFError):
+            s.set_option(opt, val)
+    s.close()
+
+
+def _desc(insts, precision="fp32", proj="dense"):
+    arr = (sf_shape * len(insts))()
+    for k, i in enumerate(insts):
+        arr[k].n, arr[k].n_obs, arr[k].H, arr[k].dyn_obs = i["n"], i["n_obs"], i["H"], 0
+        arr[k].a, arr[k].b = i["a"], i["b"]
+        for ax in range(i["n_d"]):
+            arr[k].p_min[ax], arr[k].p_max[ax] = i["pmin"][ax], i["pmax"][ax]
+    d = sf_desc(insts[0]["n_d"], insts[0]["n_xi"], RHO, PRECISIONS[precision], PROJECTIONS[proj], 0, 16, 1,
+                1e-3, len(insts), arr, None, COSTS["projection"], 0.1)
+    return d, arr
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_every_failed_allocation_in_create_unwinds(precision):
+    insts = sfgen.make_batch(2, B=3)
+    d, keep = _desc(insts, precision)
+    L = lib()
+    h = ct.c_void_p()
+    assert L.sf_create(ct.byref(d), ct.byref(h)) == 0   # warm-up: module loading, context
+    L.sf_destroy(h)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failures = 0
+    try:
+        for k in range(64):
+            os.environ["SF_TEST_FAIL_ALLOC"] = str(k)
+            h = ct.c_void_p(1)   # must come back NULL on failure
+            rc = L.sf_create(ct.byref(d), ct.byref(h))
+            if rc == 0:
+                L.sf_destroy(h)
+                break
+            assert rc == SF_ENOMEM, (k, rc)
+            assert h.value is None, k
+            failures += 1
+        else:
+            pytest.fail("sf_create never succeeded")
+    finally:
+        os.environ.pop("SF_TEST_FAIL_ALLOC", None)
+    assert failures >= 7          # the fixed allocations of the handle come first
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 >= free0 - (4 << 20), (free0, free1)
+    # the hook is off once the variable is gone
+    h = ct.c_void_p()
+    assert L.sf_create(ct.byref(d), ct.byref(h)) == 0
+    L.sf_destroy(h)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "tf32"])
+@pytest.mark.parametrize("proj", ["dense", "structured"])
+def test_non_finite_input_is_reported_for_its_instance_only(precision, proj):
+    if precision == "tf32" and proj == "structured":
+        pytest.skip("the tensor-core path is the dense projection")
+    insts = sfgen.make_batch(2, B=4)
+    s = SFSolver(insts, 2, insts[0]["n_xi"], rho=RHO, precision=precision, proj=proj, max_iters=20)
+    clean = _solve(s, insts, 20)
+    assert (clean["status"] == 0).all()
+    bad = [dict(i) for i in insts]
+    bad[2]["xi"] = bad[2]["xi"].copy()
+    bad[2]["xi"][0, 1, 4] = np.nan
+    got = _solve(s, bad, 20)
+    expect = np.zeros(4, dtype=np.int32)
+    expect[2] = SF_ENONFINITE
+    np.testing.assert_array_equal(got["status"], expect)
+    lay = s.offsets[0]
+    for k in (0, 1, 3):
+        sl = slice(lay[k], lay[k + 1])
+        np.testing.assert_array_equal(got["xi"][sl], clean["xi"][sl])
+        np.testing.assert_array_equal(got["lam"][sl], clean["lam"][sl])
+    s.close()
+
+
+@pytest.mark.parametrize("precision,proj", [("fp32", "structured"), ("fp32", "dense"), ("fp64", "structured"),
+                                            ("bf16x3", "dense")])
+def test_solves_are_bit_reproducible(precision, proj):
+    insts = sfgen.make_batch(4, B=6)
+    s = SFSolver(insts, insts[0]["n_d"], insts[0]["n_xi"], rho=RHO, precision=precision, proj=proj,
+                 max_iters=30, ckpt_every=1)
+    a = _solve(s, insts, 30, backward=True)
+    b = _solve(s, insts, 30, backward=True)
+    s.close()
+    s2 = SFSolver(insts, insts[0]["n_d"], insts[0]["n_xi"], rho=RHO, precision=precision, proj=proj,
+                  max_iters=30, ckpt_every=1)
+    c = _solve(s2, insts, 30, backward=True)
+    s2.close()
+    for key in ("xi", "lam", "g"):
+        np.testing.assert_array_equal(a[key], b[key])
+        np.testing.assert_array_equal(a[key], c[key])
