@@ -173,8 +173,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
                 const int hcc = min(X.hc, X.k_hi - k0);
                 __syncthreads();
                 X.begin_chunk();
-                X.positions(k0, hcc, xl);
-                X.wvec(k0, hcc, gs, Rs);
+                X.positions2(k0, hcc, xl, gs, Rs);
                 X.sync_lists();
                 X.cull_lists(k0, hcc);
                 X.rows_adjoint(k0, hcc, Rs, T(0));

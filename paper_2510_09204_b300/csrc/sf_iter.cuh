@@ -426,6 +426,46 @@ struct Cta {
         }
     }
 
+    // wvec of c1 into out1 (with the escape check when chk) and of c2 into out2 in one pass
+    // over the items: the adjoint needs both products for every chunk, and they share the
+    // basis rows and the index arithmetic.  The same sums as two wvec calls.
+    __device__ __forceinline__ void wvec2(int k0, int hcc, const T *c1, VP *out1, const T *c2, VP *out2, bool chk)
+    {
+        T *o1 = reinterpret_cast<T *>(out1), *o2 = reinterpret_cast<T *>(out2);
+        const int S = seg_len(hcc), ns = nseg_of(hcc);
+        FDiv fh, fS;
+        fh.set(hcc);
+        fS.set(S);
+        for (int e = tid; e < ND * n * hcc; e += nt) {
+            const int r = fh.q(e), kl = e - r * hcc, ax = fn.q(r), i = r - ax * n;
+            const T *wr = W + (k0 + kl) * nxi;
+            const T *xr = c1 + r * nxi, *yr = c2 + r * nxi;
+            T s0 = T(0), s1 = T(0), s2 = T(0), t0 = T(0), t1 = T(0), t2 = T(0);
+            int c = 0;
+            for (; c + 2 < nxi; c += 3) {
+                s0 += wr[c] * xr[c];
+                s1 += wr[c + 1] * xr[c + 1];
+                s2 += wr[c + 2] * xr[c + 2];
+                t0 += wr[c] * yr[c];
+                t1 += wr[c + 1] * yr[c + 1];
+                t2 += wr[c + 2] * yr[c + 2];
+            }
+            for (; c < nxi; ++c) {
+                s0 += wr[c] * xr[c];
+                t0 += wr[c] * yr[c];
+            }
+            const T val = (s0 + s1) + s2;
+            const int oi = (i * hcc + kl) * NDP<ND>::v + ax;
+            o1[oi] = val;
+            o2[oi] = (t0 + t1) + t2;
+            if (chk) {
+                const int sg = fS.q(kl);
+                if (!(val >= bbx[((2 * ax) * ns + sg) * NBX + i] && val <= bbx[((2 * ax + 1) * ns + sg) * NBX + i]))
+                    esc = true;
+            }
+        }
+    }
+
     // Segments of a chunk for the culling boxes: at most 32 timesteps each.
     __device__ __forceinline__ static int nseg_of(int hcc) { return (hcc + 31) >> 5; }
     __device__ __forceinline__ static int seg_len(int hcc) { return (hcc + nseg_of(hcc) - 1) / nseg_of(hcc); }
@@ -460,9 +500,50 @@ struct Cta {
         }
     }
 
+    // positions() of coeff together with W c2 into out2 (the adjoint's R* = W g*)
+    __device__ __forceinline__ void positions2(int k0, int hcc, const T *coeff, const T *c2, VP *out2)
+    {
+        wvec2(k0, hcc, coeff, P, c2, out2, cull && lv);
+        for (int e = n * hcc + tid; e < (npad + 4) * hcc; e += nt) {
+            VP p;
+#pragma unroll
+            for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = Far<T>::v;
+            P[e] = p;
+        }
+    }
+
+    // wt_acc for a chunk of exactly HCC timesteps: the same sums in the same order, with the
+    // loop fully unrolled (all loads issued ahead of the multiply-adds)
+    template <int HCC>
+    __device__ __forceinline__ void wt_acc_fixed(int k0, const T *src, T *dst)
+    {
+        for (int e = tid; e < NN; e += nt) {
+            const int r = e / NXI, c = e - r * NXI;
+            const T *rr = src + r * HCC;
+            const T *wc = W + k0 * NXI + c;
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+            for (int kl = 0; kl + 3 < HCC; kl += 4) {
+                s0 += wc[kl * NXI] * rr[kl];
+                s1 += wc[(kl + 1) * NXI] * rr[kl + 1];
+                s2 += wc[(kl + 2) * NXI] * rr[kl + 2];
+                s3 += wc[(kl + 3) * NXI] * rr[kl + 3];
+            }
+#pragma unroll
+            for (int kl = HCC & ~3; kl < HCC; ++kl) s0 += wc[kl * NXI] * rr[kl];
+            dst[e] += (s0 + s1) + (s2 + s3);
+        }
+    }
+
     // dst[ax][i][c] += sum_kl W[k0 + kl][c] src[ax][i][kl]
     __device__ __forceinline__ void wt_acc(int k0, int hcc, const T *src, T *dst)
     {
+        if constexpr (NXI > 0) {
+            if (hcc == 25) {   // a quarter of a 100-step horizon, the common chunk
+                wt_acc_fixed<25>(k0, src, dst);
+                return;
+            }
+        }
         for (int e = tid; e < NN; e += nt) {
             const int r = e / nxi, c = e - r * nxi;
             const T *rr = src + r * hcc;
