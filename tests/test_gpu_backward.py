@@ -122,6 +122,37 @@ def test_fp32_adjoint_within_tolerance():
         assert close(got, ref, 1e-4), rel(got, ref)
 
 
+@pytest.mark.parametrize("proj", ["dense", "structured"])
+@pytest.mark.parametrize("cluster", [4, 3])
+def test_fp32_specialised_kernels_forward_and_adjoint(proj, cluster):
+    """The compile-time kernels of the default configuration (FP32, n_xi = 11, culling) on
+    a 100-step horizon: split over 4 CTAs every chunk has 25 timesteps (the unrolled W'
+    aggregation), over 3 it has 33 or 34 (the runtime-length loop).  Forward iterate and
+    adjoint against the oracle."""
+    iters = 12
+    inst = kink_free(lambda s: pinlib.small_instance(n=4, n_obs=3, H=100, n_d=2, n_xi=11, seed=1200 + s,
+                                                     extent=5.0), iters)
+    gxo, glo, grp2 = seeds([inst], 11)
+    s = SFSolver([inst], 2, 11, rho=RHO, precision="fp32", proj=proj, max_iters=iters, ckpt_every=1)
+    s.set_launch(cluster, 0)
+    assert s.launch()[0] == cluster
+    data = s.pack([inst])
+    xo, lo, _ = s.solve(data, data["xi"], iters)
+    g_rp2 = torch.as_tensor(np.asarray(grp2, dtype=np.float64), device="cuda")
+    gx, gx0, gl0 = s.backward(pack_list(s, gxo), pack_list(s, glo), g_rp2)
+    torch.cuda.synchronize()
+    assert (s.status() == 0).all()
+    ref = oracle.solve(inst, iters, rho=RHO)
+    W = oracle.basis(100, 11)
+    got_x = s.unpack(xo, 0).double().cpu().numpy()
+    assert np.abs(np.einsum("kc,dic->dik", W, got_x - ref["xi"])).max() <= 1e-4
+    r = oracle_grads(inst, iters, gxo[0], glo[0], grp2[0])
+    for got, want in zip((gx, gx0, gl0), r):
+        g = s.unpack(got, 0).double().cpu().numpy()
+        assert close(g, want, 1e-4), rel(g, want)
+    s.close()
+
+
 def test_autograd_function_loss_of_config4_form():
     """loss = sum ||r_p(out)||^2 + 0.1 ||out - candidate||^2 through SFSolve, against the
     oracle's reverse pass with the matching seeds."""
