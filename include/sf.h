@@ -50,7 +50,9 @@ enum {
     SF_ENONFINITE = 6,  /* NaN/Inf met in an iterate (reported per instance)              */
     SF_ESTATE = 7,      /* call order violated (e.g. backward without checkpoints)        */
     SF_EUNSUPPORTED = 8, /* option not built into this library                            */
-    SF_ETOOBIG = 9       /* sizes beyond the fixed limits of sf_solve_noalloc                  */
+    SF_ETOOBIG = 9,      /* sizes beyond the fixed limits of sf_solve_noalloc                  */
+    SF_EBOUNDS = 10      /* a device-side bounds check failed (per instance; only libraries
+                            built with SF_BOUNDS_CHECK run the checks)                        */
 };
 
 /* ---- precision of the iteration ------------------------------------------ */

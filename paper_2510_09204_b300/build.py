@@ -12,6 +12,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libsf.so")
+# the same sources with the device-side bounds checks compiled in (SF_BOUNDS_CHECK): a
+# test build that reports SF_EBOUNDS per instance instead of touching memory out of bounds
+LIB_CHECK = os.path.join(PKG, "libsf_check.so")
+CHECK_FLAGS = ("-DSF_BOUNDS_CHECK",)
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -52,7 +56,7 @@ def build(force: bool = False, verbose: bool = False, out: str = LIB, extra=()) 
     one shared library; returns its path."""
     if not force and not stale(out):
         return out
-    objdir = os.path.join(PKG, "_build")
+    objdir = os.path.join(PKG, "_build" if not extra else "_build_" + os.path.splitext(os.path.basename(out))[0])
     os.makedirs(objdir, exist_ok=True)
     flags = [NVCC, "-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC, *extra]
     if verbose:
@@ -77,6 +81,13 @@ def build(force: bool = False, verbose: bool = False, out: str = LIB, extra=()) 
     return out
 
 
+def build_check(force: bool = False) -> str:
+    """The bounds-checked library (libsf_check.so)."""
+    return build(force=force, out=LIB_CHECK, extra=CHECK_FLAGS)
+
+
 if __name__ == "__main__":
     build(force=True, verbose="-v" in sys.argv)
     print(LIB)
+    if "--check" in sys.argv:
+        print(build_check(force=True))

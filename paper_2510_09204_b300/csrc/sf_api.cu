@@ -949,6 +949,7 @@ extern "C" const char *sf_strerror(int32_t code)
     case SF_ESTATE: return "call order violated";
     case SF_EUNSUPPORTED: return "option not supported";
     case SF_ETOOBIG: return "size beyond the fixed limits of sf_solve_noalloc";
+    case SF_EBOUNDS: return "device-side bounds check failed";
     default: return "unknown status";
     }
 }

@@ -39,6 +39,16 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     const Inst<T> I0 = A.inst[ii];
     const BwdCarve cv = backward_carve(ND, NXI > 0 ? NXI : A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
                                     tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
+#ifdef SF_BOUNDS_CHECK
+    {   // the carve must fit the launch's dynamic shared memory (the same in every CTA)
+        uint32_t dsm;
+        asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+        if ((uint64_t)cv.total * sizeof(T) > dsm) {
+            if (threadIdx.x == 0) A.status[ii] = SF_EBOUNDS;
+            return;
+        }
+    }
+#endif
     Cta<T, ND, TC, NXI, MODE> X;
     X.init(A, smem_raw, cv.f, ii, cr, C);
     X.load_constants(A, A.p_rows);
@@ -198,6 +208,9 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             if (B.gl0) B.gl0[off + e] = ls[e];
         }
     }
+#ifdef SF_BOUNDS_CHECK
+    if (__syncthreads_or(X.oob) && tid == 0) A.status[ii] = SF_EBOUNDS;
+#endif
     if (tid == 0 && X.tc_timed_out()) A.status[ii] = SF_ETIMEOUT;
     X.tc_teardown();
     cl.sync();   // no CTA leaves while another may still read its shared memory

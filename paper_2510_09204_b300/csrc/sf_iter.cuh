@@ -168,6 +168,7 @@ struct Cta {
     int cull, LPs, LOs, NBX;
     FDiv fn, fN, fL;  // divisions by n, N and L
     int lv, need;     // lists valid for the current chunk; rebuild asked (block-uniform)
+    int oob;          // a bounds check failed in this thread (builds with SF_BOUNDS_CHECK)
     bool esc;         // this thread saw a position outside its robot's inflated box
     T cdel;           // inflation of the robots' boxes
     // tensor-core projection (FP32 kernels, dense mode)
@@ -228,6 +229,7 @@ struct Cta {
         fL.set(L);
         lv = 0;
         need = 0;
+        oob = 0;
         esc = false;
         cdel = T(0.5) * fmax(I.a, I.b);
         bd = sm + cv.bd; db = sm + cv.db; sx = sm + cv.sx; red = sm + cv.red; Ps = sm + cv.Ps;
@@ -646,10 +648,12 @@ struct Cta {
                     c = qdist<T, ND>(g, kz) <= a2c;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, c);
-                if (c) L[cp + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)j;
+                const int at = cp + __popc(bal & ((1u << lane) - 1u));
+                if (c && in_bounds(at < LPs)) L[at] = (unsigned short)j;
                 cp += __popc(bal);
             }
-            for (int u = cp + lane; u < ((cp + 3) & ~3); u += 32) L[u] = (unsigned short)npad;
+            for (int u = cp + lane; u < ((cp + 3) & ~3); u += 32)
+                if (in_bounds(u < LPs)) L[u] = (unsigned short)npad;
             unsigned short *M = lol + task * LOs;
             int co = 0;
             for (int m0 = 0; m0 < nobs; m0 += 32) {
@@ -673,10 +677,12 @@ struct Cta {
                     c = q <= osa[3 * nobs + m] * T(1.00001);
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, c);
-                if (c) M[co + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)m;
+                const int at = co + __popc(bal & ((1u << lane) - 1u));
+                if (c && in_bounds(at < LOs)) M[at] = (unsigned short)m;
                 co += __popc(bal);
             }
-            for (int u = co + lane; u < ((co + 3) & ~3); u += 32) M[u] = (unsigned short)opad;
+            for (int u = co + lane; u < ((co + 3) & ~3); u += 32)
+                if (in_bounds(u < LOs)) M[u] = (unsigned short)opad;
             if (lane == 0) {
                 lcn[2 * task] = cp;
                 lcn[2 * task + 1] = co;
@@ -687,8 +693,10 @@ struct Cta {
     }
 
     // Four partner (or obstacle) indices of block b of robot i's loop: the full loop's
-    // b*4 .. b*4+3, or the culled loop's list entries (far stand-ins past the count).
-    __device__ __forceinline__ void block_ids(const unsigned short *list, int cnt, int b4, int stand_in, int (&id)[4]) const
+    // b*4 .. b*4+3, or the culled loop's list entries (far stand-ins past the count).  With
+    // SF_BOUNDS_CHECK an index outside [0, stand_in + 4) is recorded and replaced by the
+    // stand-in.
+    __device__ __forceinline__ void block_ids(const unsigned short *list, int cnt, int b4, int stand_in, int (&id)[4])
     {
         if (b4 < cnt) {
             const ushort4 q = *reinterpret_cast<const ushort4 *>(list + b4);
@@ -696,6 +704,23 @@ struct Cta {
         } else {
             id[0] = id[1] = id[2] = id[3] = stand_in;
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (!in_bounds((unsigned)id[u] < (unsigned)(stand_in + 4))) id[u] = stand_in;
+    }
+
+    // true when c holds; with SF_BOUNDS_CHECK a false c is recorded in oob (the kernel
+    // reports SF_EBOUNDS for the instance) and the caller skips the access.  Without it the
+    // check compiles away.
+    __device__ __forceinline__ bool in_bounds(bool c)
+    {
+#ifdef SF_BOUNDS_CHECK
+        if (!c) oob = 1;
+        return c;
+#else
+        (void)c;
+        return true;
+#endif
     }
 
     // Rows of the items (i, k) of one chunk: R written to Rb[ax][i][kl].  Partners and

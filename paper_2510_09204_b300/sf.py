@@ -15,7 +15,7 @@ import torch
 from . import build as _build
 
 (SF_OK, SF_EINVAL, SF_ESHAPE, SF_ECUDA, SF_ENOMEM, SF_ETIMEOUT, SF_ENONFINITE, SF_ESTATE, SF_EUNSUPPORTED,
- SF_ETOOBIG) = range(10)
+ SF_ETOOBIG, SF_EBOUNDS) = range(11)
 SF_NOALLOC_MAX_INST, SF_NOALLOC_MAX_H = 256, 1024
 SF_FP64, SF_FP32, SF_TF32, SF_BF16X3, SF_BF16 = range(5)
 SF_PROJ_DENSE, SF_PROJ_STRUCTURED = 0, 1

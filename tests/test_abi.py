@@ -31,6 +31,15 @@ def test_library_exports_every_declared_symbol():
     assert sorted(EXPORTS) == declared_functions()
 
 
+def test_bounds_checked_build_exports_the_same_symbols():
+    from paper_2510_09204_b300 import build
+    L = ct.CDLL(build.build_check())
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    L.sf_strerror.restype = ct.c_char_p
+    assert L.sf_strerror(10).startswith(b"device-side bounds")
+
+
 def test_strerror_and_version_need_no_device():
     from paper_2510_09204_b300 import lib
     L = lib()
