@@ -56,18 +56,22 @@ class SFConfig:
     extra: dict = field(default_factory=dict)
 
 
-CONFIGS = {
-    1: SFConfig(1, "plain-fp64-1inst", 1, (4, 4), (4, 4), (50,), 2, 0.25, (10.0, 10.0),
-                (0.3, 0.6), "iid", 0.5, iters=100, precision="fp64"),
-    2: SFConfig(2, "b32-n16-2d", 32, (16, 16), (20, 20), (100,), 2, 0.25, (15.0, 15.0),
-                (0.3, 0.8), "gp", 0.7, ell=10.0, iters=200),
-    3: SFConfig(3, "uneven-b64", 64, (8, 64), (10, 50), (80, 100, 120), 2, 0.25, (10.0, 10.0),
-                (0.3, 0.6), "iid", 0.5, iters=200),
-    4: SFConfig(4, "diff-b128-n32", 128, (32, 32), (30, 30), (100,), 2, 0.25, (15.0, 15.0),
-                (0.3, 0.8), "gp", 0.7, ell=10.0, iters=50, extra={"ckpt_every": 10}),
-    5: SFConfig(5, "b16-n64-3d", 16, (64, 64), (100, 100), (100,), 3, 0.2, (20.0, 20.0, 6.0),
-                (0.3, 1.0), "gp", 0.7, ell=10.0, iters=300, precision="bf16x3"),
-}
+def _load_configs():
+    """The workloads of configs.json as SFConfig records, keyed by config id."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs.json")) as f:
+        spec = json.load(f)
+    out = {}
+    for c in spec["configs"]:
+        out[c["cid"]] = SFConfig(c["cid"], c["name"], c["B"], tuple(c["n"]), tuple(c["n_obs"]), tuple(c["H"]),
+                                 c["n_d"], c["r_robot"], tuple(c["extent"]), tuple(c["r_obs"]), c["noise"],
+                                 c["sigma"], ell=c.get("ell", 10.0), iters=c["iters"],
+                                 precision=c.get("precision", "fp32"), extra=dict(c.get("extra", {})))
+    return out, spec["solver"]
+
+
+CONFIGS, SOLVER_DEFAULTS = _load_configs()
 
 
 def rng_for(cid: int, idx: int) -> np.random.Generator:
