@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
 
 // The default configuration runs a kernel with its choices fixed at compile time (the
 // code of the other choices compiled away): FP32, n_xi = 11, culled rows, the projection
-// cost, and the structured (MODE 1) or dense (MODE 2) projection.  Every other
+// cost, and the structured (MODE 1) or dense (MODE 2) projection; the trajectory
+// optimiser's default (the smoothness cost, structured) runs MODE 3.  Every other
 // combination runs the generic kernel, whose choices are runtime flags.
 template <typename T, int ND, int MAXT, bool TC>
 static cudaError_t go_forward(const FwdArgs<T> &a, int nxi, int ni, int cs, int threads, size_t smem, cudaStream_t s)
@@ -150,6 +151,8 @@ static cudaError_t go_forward(const FwdArgs<T> &a, int nxi, int ni, int cs, int 
             return launch_cluster(k_forward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 2 : 0>, a, ni, cs, threads, smem, s);
         if (!TC) return launch_cluster(k_forward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 1 : 0>, a, ni, cs, threads, smem, s);
     }
+    if (f32 && !TC && nxi == 11 && f.cull && f.cost == SF_COST_SMOOTHNESS && f.proj == SF_PROJ_STRUCTURED)
+        return launch_cluster(k_forward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 3 : 0>, a, ni, cs, threads, smem, s);
     return launch_cluster(k_forward<T, ND, MAXT, TC, 0, 0>, a, ni, cs, threads, smem, s);
 }
 

@@ -143,7 +143,8 @@ __device__ __forceinline__ void block_reduce3_to(T a, T b, T c, T *red)
 // NXI > 0: the coefficient count fixed at compile time (loops over it unroll, divisions by
 // it become multiplications); 0: taken from the arguments.  MODE 0: the projection form,
 // culling and cost are runtime flags; MODE 1 / 2: fixed to culled rows with the
-// projection cost and the structured (1) or dense (2) projection.
+// projection cost and the structured (1) or dense (2) projection; MODE 3: culled rows, the
+// structured projection and the smoothness cost (the trajectory optimiser).
 template <typename T, int ND, bool TC = false, int NXI = 0, int MODE = 0>
 struct Cta {
     using VP = Vec<T, NDP<ND>::v>;
@@ -204,7 +205,7 @@ struct Cta {
         hc = I.hc;
         rho = A.rho;
         invn = T(1) / T(n);
-        dense = MODE == 2 ? true : MODE == 1 ? false : A.proj == SF_PROJ_DENSE;
+        dense = MODE == 2 ? true : (MODE == 1 || MODE == 3) ? false : A.proj == SF_PROJ_DENSE;
         k_lo = (int)((int64_t)cr * H / C);
         k_hi = (int)((int64_t)(cr + 1) * H / C);
         L = (N + C - 1) / C;
@@ -240,7 +241,7 @@ struct Cta {
         Pdev = sx; Pdif = sx + nxi * nxi; Bdev = sx + 2 * nxi * nxi; Bdif = Bdev + 2 * nxi;
         mv = Bdif + 2 * nxi; pm = mv + ND * nxi; mb = pm + ND * nxi;
         Qc = mb + 2 * ND;
-        smooth = MODE ? 0 : A.cost == SF_COST_SMOOTHNESS;
+        smooth = MODE == 3 ? 1 : MODE ? 0 : A.cost == SF_COST_SMOOTHNESS;
         Prow = nullptr;
         need_b = 0;
         tcm = 0;
