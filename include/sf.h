@@ -82,6 +82,12 @@ enum {
 };
 
 /* ---- per-instance shape ---------------------------------------------------- */
+/* sf_create accepts n <= 256, n_obs <= 4096, H <= 4096; an instance must also fit the
+ * per-CTA shared-memory budget (227 KB) at some cluster size: each CTA keeps its share of
+ * the horizon's basis rows, the instance's iterate, multipliers and obstacle records, and
+ * a chunk of positions.  For example H = 4096 fits in FP32 and FP64, n_obs = 4096 in FP32
+ * only, n = 256 robots in the 2-D FP32 forward only (no checkpoints); sizes that fit
+ * nowhere return SF_EUNSUPPORTED. */
 typedef struct sf_shape {
     int32_t n;          /* robots, >= 1                                                    */
     int32_t n_obs;      /* obstacles, >= 0                                                 */

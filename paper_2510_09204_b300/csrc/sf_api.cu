@@ -136,8 +136,8 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     int cull = cull_req ? 1 : 0;
     for (int i = 0; i < n_inst && cull; ++i) {
         const int h8 = std::min((H[i] + C - 1) / C, 8);
-        const size_t b = (size_t)std::max(forward_carve(nd, nxi, H[i], n[i], nobs[i], h8, 0, esz, tc_mode, 2, 1).total,
-                                          backward_carve(nd, nxi, H[i], n[i], nobs[i], h8, 0, esz, tc_mode, 2, 1).total) * esz;
+        const size_t b = (size_t)std::max(forward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h8, 0, esz, tc_mode, 2, 1).total,
+                                          backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h8, 0, esz, tc_mode, 2, 1).total) * esz;
         if (b > (size_t)optin || n[i] > 65535 - 8 || nobs[i] > 65535 - 8) cull = 0;
     }
     p.cull = cull;
@@ -151,8 +151,8 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
         if (tc_mode && tc_ntiles(n[i] * nxi, C) > 8) return SF_EUNSUPPORTED;   // 8 x 128 rows per CTA at most
         // the forward's carve, or the larger adjoint carve when the handle keeps checkpoints
         auto bytes = [&](int h, int rows) {
-            const int64_t f = forward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total;
-            const int64_t b = need_bwd ? backward_carve(nd, nxi, H[i], n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total : 0;
+            const int64_t f = forward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total;
+            const int64_t b = need_bwd ? backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total : 0;
             return (size_t)std::max(f, b) * esz;
         };
         while (hc > 1 && bytes(hc, 0) > (size_t)optin) --hc;
@@ -161,8 +161,8 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
             const int st = tc_stages(tc_mode, n[i] * nxi, C, 1);
             int hr = own;
             auto rbytes = [&](int h) {
-                return (size_t)std::max(forward_carve(nd, nxi, H[i], n[i], nobs[i], h, 0, esz, tc_mode, st, cull).total,
-                                        backward_carve(nd, nxi, H[i], n[i], nobs[i], h, 0, esz, tc_mode, st, cull).total) * esz;
+                return (size_t)std::max(forward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h, 0, esz, tc_mode, st, cull).total,
+                                        backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h, 0, esz, tc_mode, st, cull).total) * esz;
             };
             while (hr > 1 && rbytes(hr) > (size_t)optin) --hr;
             if (rbytes(hr) > (size_t)optin || hr < std::min(own, 8)) res_ok = false;
@@ -171,16 +171,19 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
         hc_out[i] = hc;
         need = std::max(need, bytes(hc, 0));
         maxL = std::max(maxL, (n[i] * nxi + C - 1) / C);
-        const size_t r1 = (size_t)residual_doubles(nd, nxi, H[i], n[i], nobs[i], 1) * sizeof(double);
-        if (r1 > (size_t)optin) return SF_EUNSUPPORTED;
-        need_r = std::max(need_r, (size_t)residual_doubles(nd, nxi, H[i], n[i], nobs[i], own) * sizeof(double));
+        // the residual check stages the obstacle records when they fit, else reads them from
+        // global memory (it decides the same way from the shared memory it is given)
+        const int wr = cta_rows(H[i], C);
+        const int nob = residual_doubles(nd, nxi, wr, n[i], nobs[i], 1) * (int64_t)sizeof(double) <= optin ? nobs[i] : 0;
+        if (residual_doubles(nd, nxi, wr, n[i], nob, 1) * (int64_t)sizeof(double) > optin) return SF_EUNSUPPORTED;
+        need_r = std::max(need_r, (size_t)residual_doubles(nd, nxi, wr, n[i], nob, own) * sizeof(double));
     }
     if (proj == SF_PROJ_DENSE && !tc_mode) {
         size_t with_p = 0;
         for (int i = 0; i < n_inst; ++i) {
-            with_p = std::max(with_p, (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], maxL, esz, 0, 2, cull).total * esz);
+            with_p = std::max(with_p, (size_t)forward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], hc_out[i], maxL, esz, 0, 2, cull).total * esz);
             if (need_bwd)
-                with_p = std::max(with_p, (size_t)backward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], maxL, esz, 0, 2, cull).total * esz);
+                with_p = std::max(with_p, (size_t)backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], hc_out[i], maxL, esz, 0, 2, cull).total * esz);
         }
         if (with_p <= (size_t)optin) {
             p.p_rows = maxL;
@@ -192,7 +195,7 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
         need = 0;
         for (int i = 0; i < n_inst; ++i) {
             hc_out[i] = hc_res[i];
-            need = std::max(need, (size_t)forward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], 0, esz, tc_mode,
+            need = std::max(need, (size_t)forward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], hc_out[i], 0, esz, tc_mode,
                                                         tc_stages(tc_mode, n[i] * nxi, C, 1), cull).total * esz);
         }
     }
@@ -200,7 +203,7 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     p.smem_res = std::min((size_t)optin, need_r);
     size_t need_b = 0;
     for (int i = 0; i < n_inst; ++i)
-        need_b = std::max(need_b, (size_t)backward_carve(nd, nxi, H[i], n[i], nobs[i], hc_out[i], p.p_rows, esz, tc_mode,
+        need_b = std::max(need_b, (size_t)backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], hc_out[i], p.p_rows, esz, tc_mode,
                                                          tc_stages(tc_mode, n[i] * nxi, C, p.tc_res), cull).total * esz);
     p.smem_bwd = need_b <= (size_t)optin ? need_b : 0;
     *out = p;

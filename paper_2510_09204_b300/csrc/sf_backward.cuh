@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     const int w = blockIdx.x / C;
     const int ii = A.order ? A.order[w] : w;
     const Inst<T> I0 = A.inst[ii];
-    const BwdCarve cv = backward_carve(ND, NXI > 0 ? NXI : A.nxi, I0.H, I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
+    const BwdCarve cv = backward_carve(ND, NXI > 0 ? NXI : A.nxi, cta_rows(I0.H, A.csize), I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
                                     tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
 #ifdef SF_BOUNDS_CHECK
     {   // the carve must fit the launch's dynamic shared memory (the same in every CTA)

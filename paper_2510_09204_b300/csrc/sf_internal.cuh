@@ -80,22 +80,27 @@ struct FwdCarve {
 __host__ __device__ inline int cull_lp(int n) { return (n + 3) / 4 * 4 + 4; }          // partner list stride
 __host__ __device__ inline int cull_lo(int nobs) { return (nobs + 3) / 4 * 4 + 4; }    // obstacle list stride
 
+// Timesteps of the horizon one CTA of a C-CTA cluster owns at most (CTA r owns
+// [r H / C, (r + 1) H / C)).
+__host__ __device__ inline int cta_rows(int H, int C) { return (H + C - 1) / C; }
+
 __host__ __device__ inline int64_t carve_round(int64_t cnt, int esz)
 {
     const int64_t q = 32 / esz;
     return (cnt + q - 1) / q * q;
 }
 
-// nd, nxi: dimension and coefficients; H, n, nobs: instance sizes; hc: timesteps per chunk;
+// nd, nxi: dimension and coefficients; wrows: rows of the basis a CTA keeps (its share
+// of the horizon, ceil(H / C)); n, nobs: instance sizes; hc: timesteps per chunk;
 // p_rows: rows of P_eta staged in shared memory (0: read from global memory); tc_mode,
 // tc_st: tensor-core projection mode and A ring stages.
-__host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
+__host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int wrows, int n, int nobs, int hc, int p_rows, int esz,
                                                   int tc_mode = 0, int tc_st = 2, int cull = 0)
 {
     const int64_t N = (int64_t)n * nxi, NN = nd * N, ndp = nd == 2 ? 2 : 4;
     FwdCarve c;
     int64_t o = (tc_smem_bytes(tc_mode, (int)N, tc_st) + 127) / 128 * 128 / esz;   // tensor-core buffers first
-    c.W = o;   o += carve_round((int64_t)H * nxi, esz);
+    c.W = o;   o += carve_round((int64_t)wrows * nxi, esz);            // this CTA's rows of W
     c.xb = o;  o += carve_round(NN, esz);
     c.lam = o; o += carve_round(NN, esz);
     c.xc = o;  o += carve_round(NN, esz);
@@ -134,11 +139,11 @@ struct BwdCarve {
     int64_t xs, ls, cs, xn, xz, Rs, total;
 };
 
-__host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int H, int n, int nobs, int hc, int p_rows, int esz,
+__host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int wrows, int n, int nobs, int hc, int p_rows, int esz,
                                                    int tc_mode = 0, int tc_st = 2, int cull = 0)
 {
     BwdCarve b;
-    b.f = forward_carve(nd, nxi, H, n, nobs, hc, p_rows, esz, tc_mode, tc_st, cull);
+    b.f = forward_carve(nd, nxi, wrows, n, nobs, hc, p_rows, esz, tc_mode, tc_st, cull);
     const int64_t NN = (int64_t)nd * n * nxi, npad = (n + 3) / 4 * 4, ndp = nd == 2 ? 2 : 4;
     int64_t o = b.f.total;
     b.xs = o; o += carve_round(NN, esz);
@@ -253,10 +258,10 @@ cudaError_t launch_backward(const BwdArgs<double> &a, int threads, size_t smem, 
 cudaError_t launch_backward(const BwdArgs<float> &a, int threads, size_t smem, cudaStream_t s);
 
 // Shared memory (doubles) the residual kernel needs for one instance at a chunk of hc timesteps.
-__host__ __device__ inline int64_t residual_doubles(int nd, int nxi, int H, int n, int nobs, int hc)
+__host__ __device__ inline int64_t residual_doubles(int nd, int nxi, int wrows, int n, int nobs, int hc)
 {
     const int64_t N = (int64_t)n * nxi;
-    return carve_round((int64_t)H * nxi, 8) + carve_round(nd * N, 8) + carve_round((int64_t)n * hc * (nd == 2 ? 2 : 4), 8) +
+    return carve_round((int64_t)wrows * nxi, 8) + carve_round(nd * N, 8) + carve_round((int64_t)n * hc * (nd == 2 ? 2 : 4), 8) +
            carve_round((int64_t)nobs * 8, 8) + kRedDoubles;
 }
 

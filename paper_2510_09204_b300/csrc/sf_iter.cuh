@@ -211,7 +211,9 @@ struct Cta {
         L = (N + C - 1) / C;
         r_lo = min(N, cr * L);
         r_hi = min(N, r_lo + L);
-        W = sm + cv.W; xb = sm + cv.xb; lam = sm + cv.lam; xc = sm + cv.xc; v = sm + cv.v;
+        // this CTA's rows [k_lo, k_hi) of W, addressed by the absolute timestep: W[k * nxi + c]
+        W = sm + cv.W - (int64_t)k_lo * nxi;
+        xb = sm + cv.xb; lam = sm + cv.lam; xc = sm + cv.xc; v = sm + cv.v;
         gp = sm + cv.gp; dl = sm + cv.dl; dd = sm + cv.dd; rr = sm + cv.rr; wtw = sm + cv.wtw;
         Rb = sm + cv.Rb; ob = sm + cv.ob;
         n_refine = A.n_refine;
@@ -274,7 +276,8 @@ struct Cta {
             for (int e = tid; e < nxi * nxi; e += nt) {   // W'W for the refinement's Hessian products
                 const int u = e / nxi, vv = e - u * nxi;
                 float acc = 0.f;
-                for (int k = 0; k < H; ++k) acc += W[k * nxi + u] * W[k * nxi + vv];
+                const T *Wg = A.W + S.off_W;   // every row: shared memory holds this CTA's only
+                for (int k = 0; k < H; ++k) acc += Wg[k * nxi + u] * Wg[k * nxi + vv];
                 wtw[e] = acc;
             }
             tc_fw0 = tc_fw1 = tc_ld0 = tc_ld1 = tc_ec0 = tc_ec1 = 0;
@@ -330,7 +333,7 @@ struct Cta {
     __device__ __forceinline__ void load_constants(const FwdArgs<T> &A, int p_rows)
     {
         const T *Wg = A.W + S.off_W;
-        for (int e = tid; e < H * nxi; e += nt) W[e] = Wg[e];
+        for (int e = k_lo * nxi + tid; e < k_hi * nxi; e += nt) W[e] = Wg[e];
         const T *xcg = A.xc + I.off_xi;
         for (int e = tid; e < NN; e += nt) xc[e] = xcg[e];
         for (int e = tid; e < ND * n * 2; e += nt) bd[e] = A.bnd[I.off_bnd + e];
