@@ -31,9 +31,9 @@ def batches():
             "uneven": uneven}
 
 
-def run(insts, precision, cull, iters=40):
-    s = SFSolver(insts, insts[0]["n_d"], 11, rho=RHO, precision=precision, proj="dense", max_iters=iters,
-                 ckpt_every=10)
+def run(insts, precision, cull, iters=40, proj="dense", cost="projection"):
+    s = SFSolver(insts, insts[0]["n_d"], 11, rho=RHO, precision=precision, proj=proj, max_iters=iters,
+                 ckpt_every=10, cost=cost, dt=0.05)
     s.set_option(SF_OPT_CULL, cull)
     assert s.option(SF_OPT_CULL) == cull
     data = s.pack(insts)
@@ -46,12 +46,17 @@ def run(insts, precision, cull, iters=40):
     return [t.cpu() for t in (xo, lo, res, gx, gx0, gl0)]
 
 
+# FP32 with culling runs the compile-time kernels (dense projection, structured projection,
+# and the structured projection with the smoothness cost); without culling, the generic
+# kernel: the two must agree bit for bit
+@pytest.mark.parametrize("proj,cost", [("dense", "projection"), ("structured", "projection"),
+                                       ("structured", "smoothness")])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("name", ["sparse", "crowded", "coincident", "aniso3d", "dyn", "uneven"])
-def test_culling_is_bit_exact(name, precision):
+def test_culling_is_bit_exact(name, precision, proj, cost):
     insts = batches()[name]
-    on = run(insts, precision, 1)
-    off = run(insts, precision, 0)
+    on = run(insts, precision, 1, proj=proj, cost=cost)
+    off = run(insts, precision, 0, proj=proj, cost=cost)
     for a, b in zip(on, off):
         assert torch.equal(a, b)
 
