@@ -375,6 +375,22 @@ def _variant(insts, nd, iters, a, precision, proj, n_refine, dev, stream, flush,
     r = st.res.cpu().numpy()
     out = {"precision": precision, "projection": proj, "n_refine": n_refine, "ms_per_step": statistics.median(times),
            "launch": list(s.launch()[:2]), "status_ok": bool((s.status() == 0).all())}
+    if precision in ("tf32", "bf16", "bf16x3"):
+        # the dense projection's tensor-core work (eq. batch_comp): 2 n_d N^2 per instance per
+        # projection, one projection per iteration forward and one per reverse step, each
+        # applied 1 + n_refine times, with three products per BF16 x3 product; its rate over the
+        # whole step is a lower bound on the tensor kernels' rate
+        pk = measured_peaks()
+        prods = (3 if precision == "bf16x3" else 1) * (1 + n_refine) * (1 if a.forward_only else 2)
+        flops = sum(2.0 * nd * (i["n"] * 11) ** 2 for i in insts) * iters * prods
+        tf = flops / (out["ms_per_step"] * 1e-3) / 1e12
+        peak = pk.get("bf16_tflops")
+        if peak and precision == "tf32":
+            peak = peak * 1.1 / 2.25   # the nominal TF32 : BF16 dense ratio
+        out["tensor"] = {"algorithmic_tflop_per_step": flops / 1e12, "achieved_tflops_over_step": tf,
+                         "peak_tflops": peak, "frac_of_measured": (tf / peak) if peak else None,
+                         "note": "tcgen05 products of the dense projection only; the step is bound by "
+                                 "the iteration's other phases"}
     if ref_pos is not None:
         out["max_position_error_vs_fp64_m"] = _max_pos_err(_positions(s, st.xo, insts), ref_pos)
         out["max_final_residual_diff_vs_fp64_m"] = float(np.abs(r[:, 1] - ref_res[:, 1]).max())
