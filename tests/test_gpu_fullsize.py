@@ -130,6 +130,36 @@ def test_differentiable_128_instances_fp32_against_fp64():
     assert np.median(grel) <= 1e-3
 
 
+def test_benchmark_step_config2():
+    """The benchmark's step exactly: all 32 instances of the 16-robot 2-D config, FP32,
+    structured projection, autotuned geometry, a checkpoint every iteration, forward,
+    FP64 residual check and adjoint of the 200 iterations.  Forward: sampled instances
+    against the oracle on the input as FP32 holds it.  Adjoint: against the FP64 GPU step
+    (pinned to the oracle's reverse pass elsewhere) on the same input."""
+    insts = [rounded32(i) for i in sfgen.make_batch(2)]
+    iters = sfgen.CONFIGS[2].iters
+    outs = {}
+    for prec in ("fp64", "fp32"):
+        s, d = tuned(insts, prec, "structured", iters, ckpt=1)
+        xo, _, res = s.solve(d, d["xi"], iters)
+        g = torch.as_tensor(np.random.default_rng(2).normal(size=xo.numel()) * 1e-2, dtype=xo.dtype, device="cuda")
+        gx, _, _ = s.backward(g, None, torch.ones(len(insts), dtype=torch.float64, device="cuda"))
+        torch.cuda.synchronize()
+        assert (s.status() == 0).all()
+        if prec == "fp32":
+            boundary_exact(s, xo, insts)
+        outs[prec] = (unpack_all(s, xo, len(insts)), res.cpu().numpy(), unpack_all(s, gx, len(insts)))
+        s.close()
+    W = oracle.basis(100, 11)
+    for k in (0, 13, 31):
+        ref = oracle.solve(insts[k], iters, rho=RHO)
+        assert max_pos_err(insts[k], outs["fp32"][0][k], ref["xi"], W) <= 1e-4
+        assert abs(outs["fp32"][1][k, 1] - oracle.residual(insts[k], ref["xi"], rho=RHO)[1]) <= 1e-3
+    grel = [rel(a, b) for a, b in zip(outs["fp32"][2], outs["fp64"][2])]
+    print("\nconfig 2 adjoint FP32 vs FP64: relative error median %.2e, max %.2e" % (np.median(grel), max(grel)))
+    assert np.median(grel) <= 1e-3
+
+
 @pytest.mark.parametrize("proj", ["structured", "dense"])
 def test_3d_64_robots_fp32(proj):
     insts = sfgen.make_batch(5)
