@@ -81,3 +81,24 @@ def test_pipeline_matches_oracle_driven_pipeline():
         assert got[g]["index"] == kept[b]
         assert rel(got[g]["xi"], outs[b]) <= 1e-10
         np.testing.assert_allclose(got[g]["metrics"], m2[b], rtol=1e-9, atol=1e-12)
+
+
+def test_pipeline_with_cached_handles_gives_the_same_choice():
+    """Three calls through a HandleCache (new data, same shapes) against calls without it:
+    the same kept sets, choices and bits; the cache keeps one handle per stage."""
+    from paper_2510_09204_b300.pipeline import HandleCache
+    rng = np.random.default_rng(21)
+    problems = [sfgen.custom_instance(n=4, n_obs=3, H=30, seed=80 + g, extent=5.0) for g in range(2)]
+    cache = HandleCache()
+    for call in range(3):
+        cands = [np.stack([p["xi"] + np.pad(rng.normal(0, 0.4, size=p["xi"][..., 1:-1].shape), ((0, 0), (0, 0), (1, 1)))
+                           for _ in range(6)]) for p in problems]
+        kw = dict(keep=3, iters=40, precision="fp32", rho=RHO, dt=DT)
+        a = refine_candidates(problems, cands, **kw)
+        b = refine_candidates(problems, cands, cache=cache, **kw)
+        for x, y in zip(a, b):
+            assert x["refined"] == y["refined"] and x["index"] == y["index"]
+            np.testing.assert_array_equal(x["xi"], y["xi"])
+        assert len(cache._h) == 2
+    cache.close()
+    assert len(cache._h) == 0
