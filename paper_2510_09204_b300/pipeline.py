@@ -87,10 +87,11 @@ def refine_candidates(problems, candidates, keep=10, iters=200, precision="fp32"
     best = select([len(c) for c in chosen], m2[:, 1].contiguous(), m2[:, 2].contiguous(), tol, 1,
                   stream=stream).cpu().numpy()[:, 0]
     m2h = m2.cpu().numpy()
+    xh = xo.double().cpu()   # one copy to the host, sliced per problem below
     out, base = [], 0
     for g in range(len(problems)):
         b = int(best[g])
-        out.append(dict(xi=s2.unpack(xo, base + b).double().cpu().numpy(), index=int(chosen[g][b]),
+        out.append(dict(xi=s2.unpack(xh, base + b).numpy(), index=int(chosen[g][b]),
                         metrics=m2h[base + b], feasible=bool(m2h[base + b, 1] <= tol), refined=list(chosen[g])))
         base += len(chosen[g])
     if cache is None:
