@@ -100,3 +100,27 @@ def test_unconstrained_optimum_is_the_straight_line():
     ramp = b[..., :1] + (b[..., 1:] - b[..., :1]) * np.linspace(0.0, 1.0, 8)
     np.testing.assert_allclose(s.unpack(xo, 0).cpu().numpy(), ramp, atol=1e-8)
     assert res.cpu().numpy()[0, 1] == 0.0
+
+
+@pytest.mark.parametrize("dyn", [False, True])
+def test_fp32_3d_and_moving_obstacles_within_tolerance(dyn):
+    """The compile-time kernel of the optimiser (FP32, n_xi = 11, culling, structured) in 3-D
+    with an anisotropic body, and in 2-D with moving obstacles, against the oracle."""
+    if dyn:
+        insts = [sfgen.custom_instance(n=8, n_obs=6, H=60, seed=40 + k, extent=7.0, dyn_obs=True) for k in range(2)]
+    else:
+        insts = [sfgen.custom_instance(n=10, n_obs=8, H=60, n_d=3, seed=50 + k, extent=(7.0, 7.0, 3.0))
+                 for k in range(2)]
+        for i in insts:
+            i["b"] = 0.7 * i["a"]
+    iters = 120
+    s = solver(insts, "fp32", "structured", iters)
+    d = s.pack(insts)
+    xo, _, res = s.solve(d, d["xi"], iters)
+    torch.cuda.synchronize()
+    assert (s.status() == 0).all()
+    W = oracle.basis(60, 11)
+    for k, inst in enumerate(insts):
+        ref = oracle.solve(inst, iters, rho=RHO, cost="smoothness", dt=DT)
+        assert max_pos_err(inst, s.unpack(xo, k).double().cpu().numpy(), ref["xi"], W) <= 1e-4
+        assert abs(res.cpu().numpy()[k, 1] - oracle.residual(inst, ref["xi"], rho=RHO)[1]) <= 1e-3
