@@ -225,3 +225,33 @@ def test_fp32_large_ctas_within_tolerance(cluster, threads):
     for k, inst in enumerate(insts):
         ref = oracle.solve(inst, 100, rho=RHO)
         assert max_pos_err(inst, out["xi"][k], ref["xi"], W) <= 1e-4
+
+
+@pytest.mark.parametrize("precision,proj", [("fp64", "dense"), ("fp32", "structured")])
+def test_zero_iterations_pass_the_input_through(precision, proj):
+    """iters = 0: the outputs are the initial iterate (xi_bar^0 = xi_cand, lambda^0 = 0) bit
+    for bit, the residual is the candidate's, and the adjoint passes the seeds through
+    (dL/dxi_cand = dL/dxi_bar^L and dL/dlambda^0 = dL/dlambda^L when ||r_p||^2 has no seed)."""
+    import torch
+    from paper_2510_09204_b300 import SFSolver
+    insts = sfgen.make_batch(2, B=3)
+    s = SFSolver(insts, 2, 11, rho=RHO, precision=precision, proj=proj, max_iters=5, ckpt_every=1)
+    d = s.pack(insts)
+    xo, lo, res = s.solve(d, d["xi"], 0)
+    g = torch.randn_like(xo)
+    gl = torch.randn_like(xo)
+    gx, gx0, gl0 = s.backward(g, gl, None)
+    torch.cuda.synchronize()
+    assert (s.status() == 0).all()
+    assert torch.equal(xo, d["xi"])
+    assert torch.equal(lo, torch.zeros_like(lo))
+    assert torch.equal(gx, g)
+    assert torch.equal(gl0, gl)
+    for k, inst in enumerate(insts):
+        if precision == "fp32":   # the instance as an FP32 handle holds it
+            inst = dict(inst, **{key: np.asarray(inst[key], dtype=np.float32).astype(np.float64)
+                                 for key in ("obs_c", "obs_ab", "pmin", "pmax")},
+                        a=float(np.float32(inst["a"])), b=float(np.float32(inst["b"])))
+        r = oracle.residual(inst, s.unpack(d["xi"], k).double().cpu().numpy())
+        np.testing.assert_allclose(res.cpu().numpy()[k, :2], r[:2], rtol=1e-9, atol=1e-12)
+    s.close()
