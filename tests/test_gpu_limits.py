@@ -6,7 +6,7 @@ instance's obstacle records in shared memory (227 KB per CTA):
 - n_obs = 4096 obstacles: FP32 (the FP64 records do not fit: SF_EUNSUPPORTED);
 - n = 256 robots: the 2-D FP32 forward (the adjoint's state does not fit beside it, so a
   handle that keeps checkpoints is SF_EUNSUPPORTED, as are FP64 and 3-D);
-- n_xi = 32 coefficients.
+- n_xi = 4 (the fewest the basis allows) to 32 coefficients.
 Where the oracle is affordable the results are compared with it; the 256-robot case uses
 the feasible-fixed-point property (a conflict-free candidate is returned unchanged)."""
 import numpy as np
@@ -99,9 +99,10 @@ def test_most_robots_feasible_fixed_point():
         assert e.value.code == SF_EUNSUPPORTED
 
 
+@pytest.mark.parametrize("n_xi", [4, 32])
 @pytest.mark.parametrize("precision,proj", [("fp32", "structured"), ("fp64", "dense")])
-def test_most_coefficients(precision, proj):
-    inst = sfgen.custom_instance(n=4, n_obs=3, H=50, n_xi=32, seed=7, extent=5.0)
+def test_fewest_and_most_coefficients(precision, proj, n_xi):
+    inst = sfgen.custom_instance(n=4, n_obs=3, H=50, n_xi=n_xi, seed=7, extent=5.0)
     iters = 20
     out = solve([inst], precision, proj, iters, ckpt=1, backward=True)
     assert (out["status"] == 0).all()
