@@ -431,6 +431,33 @@ def _optimizer(insts, nd, iters, a, dev, stream, flush, pairs, dt=0.05, reps=10)
     return out
 
 
+def _convergence(insts, nd, a, dev, stream, iters=4000, tol=1e-3):
+    """Time to the paper's residual threshold: the chosen path run for up to ``iters``
+    iterations on the same batch (forward only), with each instance's first iteration whose
+    max residual is <= tol (the solver's iterations-to-tolerance output)."""
+    import torch
+
+    from paper_2510_09204_b300 import SFSolver
+    s = SFSolver(insts, nd, 11, rho=RHO, precision=a.precision, proj=a.proj, max_iters=iters, tol=tol)
+    d = s.pack(insts, device=dev)
+    s.solve(d, d["xi"], iters, stream=stream)   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, _, res = s.solve(d, d["xi"], iters, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    its = res[:, 3].cpu().numpy()
+    ok = its >= 0
+    s.close()
+    need = int(its[ok].max()) if ok.all() else None
+    return {"iterations": iters, "tol_m": tol, "ms": ms, "frac_converged": float(ok.mean()),
+            "iters_to_tol_median": float(np.median(its[ok])) if ok.any() else None,
+            "iters_to_tol_max": int(its[ok].max()) if ok.any() else None,
+            "ms_until_every_instance_converged": ms * need / iters if need is not None else None}
+
+
 def _pipeline(a, dev, stream, problems=50, per=10, keep=5, iters=500):
     """The paper's throughput scenario for the pipeline: 50 problems of the 16-robot 2D
     shape, 10 candidates each (the problem's candidate plus smooth noise), keep the 5 least
@@ -605,7 +632,7 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
     # plain FP64 GPU solve of the same step, and the tensor-core / structured variants
-    fp64, variants, optimizer, pipeline = None, [], None, None
+    fp64, variants, optimizer, pipeline, convergence = None, [], None, None, None
     if not a.no_compare and rank == 0:
         v64 = _variant(insts, nd, iters, a, "fp64", "dense", 0, dev, stream, flush, None, None, reps=5)
         p64, r64 = v64.pop("_pos"), v64.pop("_res")
@@ -616,6 +643,7 @@ def main():
                     chosen_speedup=v64["ms_per_step"] / ms_step)
         optimizer = _optimizer(insts, nd, iters, a, dev, stream, flush, pairs)
         pipeline = _pipeline(a, dev, stream)
+        convergence = _convergence(insts, nd, a, dev, stream)
         for prec, proj, nr in [("fp32", "structured" if a.proj == "dense" else "dense", 0), ("tf32", "dense", 2),
                                ("bf16x3", "dense", 1), ("bf16", "dense", 3)]:
             if (prec, proj, nr) == (a.precision, a.proj, a.n_refine):
@@ -677,6 +705,8 @@ def main():
             line["trajectory_optimizer"] = optimizer
         if pipeline:
             line["pipeline"] = pipeline
+        if convergence:
+            line["convergence"] = convergence
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(insts, iters, a.forward_only)
         print(json.dumps(line), flush=True)
