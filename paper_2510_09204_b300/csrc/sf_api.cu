@@ -474,7 +474,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
         cudaError_t e = factor_shapes((const Shape *)h->shapes_dev.p, h->n_shapes, h->shapes_h.data(), nxi,
                                       desc->rho, desc->cost, desc->dt, (double *)h->W64.p, (double *)h->P64.p,
                                       (double *)h->Pb64.p,
-                                      (double *)h->S64.p, (double *)scratch.p, 3 * oP, (int *)info.p, st);
+                                      (double *)h->S64.p, (double *)scratch.p, 3 * oP, (int *)info.p, st, desc->proj == SF_PROJ_DENSE);
         std::vector<int> inf(h->n_shapes, 0);
         if (e == cudaSuccess && desc->dt > 0.0 && isfinite(desc->dt)) {   // basis'' for sf_metrics
             e = h->Wdd64.alloc(sizeof(double) * oW);

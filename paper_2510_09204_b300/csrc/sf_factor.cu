@@ -277,6 +277,118 @@ __global__ void k_structured(const Shape *sh, int nxi, const double *P, const do
     }
 }
 
+// The Kronecker blocks directly, without the dense factorisation (handles that project in
+// the structured form).  The Hessian I_n (x) C + rho ((n + n_obs + 2) I - 11') (x) W'W has
+// eigenvalue n + n_obs + 2 of its robot factor on the deviation from the robot mean and
+// n_obs + 2 on the mean, and A = I_n (x) A0 commutes with that split, so P_dev / P_mean and
+// B_dev / B_mean are the (x, x) and (x, b) blocks of the inverse of
+// [[C + rho c W'W, A0'], [A0, 0]] (A0: rows 0 and H - 1 of W) for the two values of c.
+// One CTA per shape; Gauss-Jordan elimination with partial pivoting; info = 0 or pivot + 1.
+constexpr int kKronMax = 32 + 2;
+__global__ void k_kron_blocks(const Shape *sh, int nxi, double rho, const double *W, double *Sx, int *info)
+{
+    const Shape S = sh[blockIdx.x];
+    const double *Ws = W + S.off_W;
+    const double *Cb = Sx + S.off_S + 2 * nxi * nxi + 4 * nxi;   // per-robot cost block
+    double *o = Sx + S.off_S;
+    const int tid = threadIdx.x, nt = blockDim.x, m = nxi + 2, H = S.H;
+    __shared__ double wtw[32 * 32];
+    __shared__ double K[kKronMax * kKronMax], X[kKronMax * kKronMax];
+    __shared__ int piv, bad;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < nxi * nxi; e += nt) {
+        const int u = e / nxi, v = e % nxi;
+        double acc = 0.0;
+        for (int k = 0; k < H; ++k) acc += Ws[k * nxi + u] * Ws[k * nxi + v];
+        wtw[e] = acc;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        const double c = pass == 0 ? (double)(S.n + S.n_obs + 2) : (double)(S.n_obs + 2);
+        __syncthreads();
+        for (int e = tid; e < m * m; e += nt) {
+            const int r = e / m, q = e % m;
+            double val;
+            if (r < nxi && q < nxi) val = Cb[r * nxi + q] + rho * c * wtw[r * nxi + q];
+            else if (r < nxi) val = Ws[(q == nxi ? 0 : H - 1) * nxi + r];
+            else if (q < nxi) val = Ws[(r == nxi ? 0 : H - 1) * nxi + q];
+            else val = 0.0;
+            K[e] = val;
+            X[e] = r == q ? 1.0 : 0.0;
+        }
+        for (int p = 0; p < m; ++p) {
+            __syncthreads();
+            if (tid == 0) {
+                int best = p;
+                for (int r = p + 1; r < m; ++r)
+                    if (fabs(K[r * m + p]) > fabs(K[best * m + p])) best = r;
+                piv = best;
+                if (!(fabs(K[best * m + p]) > 0.0) && !bad) bad = p + 1;
+            }
+            __syncthreads();
+            if (bad) break;
+            const int b = piv;
+            if (b != p)
+                for (int q = tid; q < m; q += nt) {
+                    double t = K[p * m + q]; K[p * m + q] = K[b * m + q]; K[b * m + q] = t;
+                    t = X[p * m + q]; X[p * m + q] = X[b * m + q]; X[b * m + q] = t;
+                }
+            __syncthreads();
+            const double d = K[p * m + p];
+            __syncthreads();
+            for (int q = tid; q < m; q += nt) {
+                K[p * m + q] /= d;
+                X[p * m + q] /= d;
+            }
+            __syncthreads();
+            // eliminate column p from the other rows; column p itself is read by every
+            // update, so it is cleared only after a barrier
+            for (int e = tid; e < m * m; e += nt) {
+                const int r = e / m, q = e % m;
+                if (r == p || q == p) continue;
+                K[r * m + q] -= K[r * m + p] * K[p * m + q];
+            }
+            for (int e = tid; e < m * m; e += nt) {
+                const int r = e / m, q = e % m;
+                if (r == p) continue;
+                X[r * m + q] -= K[r * m + p] * X[p * m + q];
+            }
+            __syncthreads();
+            for (int r = tid; r < m; r += nt)
+                if (r != p) K[r * m + p] = 0.0;
+        }
+        __syncthreads();
+        if (bad) break;
+        double *Po = o + pass * nxi * nxi, *Bo = o + 2 * nxi * nxi + pass * 2 * nxi;
+        for (int e = tid; e < nxi * nxi; e += nt) Po[e] = X[(e / nxi) * m + e % nxi];
+        for (int e = tid; e < nxi * 2; e += nt) Bo[e] = X[(e / 2) * m + nxi + e % 2];
+    }
+    __syncthreads();
+    if (tid == 0 && bad) info[blockIdx.x] = bad;
+}
+
+// Dense P_eta = (I - Q) (x) P_dev + Q (x) P_mean and P_b likewise (columns robot-major
+// (start, goal)), from the blocks: for the operator queries and the adjoint's P_b term.
+__global__ void k_kron_assemble(const Shape *sh, int nxi, const double *Sx, double *P, double *Pb)
+{
+    const Shape S = sh[blockIdx.y];
+    const int N = S.N, n = S.n, m2 = 2 * n;
+    const double *Pd = Sx + S.off_S, *Pm = Pd + nxi * nxi, *Bd = Pd + 2 * nxi * nxi, *Bm = Bd + 2 * nxi;
+    const double inv_n = 1.0 / (double)n;
+    const int64_t totP = (int64_t)N * N, totB = (int64_t)N * m2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < totP + totB; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < totP) {
+            const int r = (int)(e / N), c = (int)(e % N), i = r / nxi, u = r % nxi, j = c / nxi, v = c % nxi;
+            const double dv = Pd[u * nxi + v];
+            P[S.off_P + e] = (i == j ? dv : 0.0) + (Pm[u * nxi + v] - dv) * inv_n;
+        } else {
+            const int64_t f = e - totP;
+            const int r = (int)(f / m2), q = (int)(f % m2), i = r / nxi, u = r % nxi, j = q >> 1, sd = q & 1;
+            const double dv = Bd[u * 2 + sd];
+            Pb[S.off_Pb + f] = (i == j ? dv : 0.0) + (Bm[u * 2 + sd] - dv) * inv_n;
+        }
+    }
+}
+
 __global__ void k_convert(const double *src, float *dst, int64_t n)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -350,8 +462,24 @@ cudaError_t arrange_tc(const Shape *shapes_dev, int n_shapes, const Shape *shape
 
 cudaError_t factor_shapes(const Shape *shapes_dev, int n_shapes, const Shape *shapes_host, int nxi,
                           double rho, int cost, double dt, double *W64, double *P64, double *Pb64, double *S64,
-                          double *scratch, int64_t scratch_elems, int *info, cudaStream_t s)
+                          double *scratch, int64_t scratch_elems, int *info, cudaStream_t s, bool dense)
 {
+    if (!dense) {   // structured handles: the Kronecker blocks directly, dense forms assembled
+        int maxN = 0;
+        int64_t most = 0;
+        for (int i = 0; i < n_shapes; ++i) {
+            maxN = std::max(maxN, shapes_host[i].N);
+            most = std::max<int64_t>(most, (int64_t)shapes_host[i].N * (shapes_host[i].N + 2 * shapes_host[i].n));
+        }
+        k_basis<<<n_shapes, 256, 0, s>>>(shapes_dev, nxi, W64);
+        k_cost_block<<<n_shapes, 128, 0, s>>>(shapes_dev, nxi, cost, dt, S64);
+        k_kron_blocks<<<n_shapes, 128, 0, s>>>(shapes_dev, nxi, rho, W64, S64, info);
+        const int64_t blocks = (most + 255) / 256;
+        k_kron_assemble<<<dim3((unsigned)(blocks > 1024 ? 1024 : blocks), n_shapes), 256, 0, s>>>(shapes_dev, nxi, S64,
+                                                                                               P64, Pb64);
+        (void)maxN;
+        return cudaGetLastError();
+    }
     // scratch holds three pools laid out like P64: L (Cholesky), Y, S
     (void)scratch_elems;
     int maxN = 0;

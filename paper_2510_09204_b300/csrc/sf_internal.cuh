@@ -265,11 +265,13 @@ __host__ __device__ inline int64_t residual_doubles(int nd, int nxi, int wrows, 
            carve_round((int64_t)nobs * 8, 8) + kRedDoubles;
 }
 
-// FP64 factorisation of every shape (sf_factor.cu).  W64/P64/Pb64/S64 are pools laid out by
+// FP64 factorisation of every shape (sf_factor.cu): the dense KKT inverse (dense), or for
+// structured handles the Kronecker blocks from the n_xi-size systems with the dense
+// operators assembled from them.  W64/P64/Pb64/S64 are pools laid out by
 // Shape offsets; info[s] receives 0 or a failing pivot index + 1.
 cudaError_t factor_shapes(const Shape *shapes_dev, int n_shapes, const Shape *shapes_host, int nxi,
                           double rho, int cost, double dt, double *W64, double *P64, double *Pb64, double *S64,
-                          double *scratch, int64_t scratch_elems, int *info, cudaStream_t s);
+                          double *scratch, int64_t scratch_elems, int *info, cudaStream_t s, bool dense);
 cudaError_t convert_pool(const double *src, float *dst, int64_t n, cudaStream_t s);
 
 }  // namespace sf
