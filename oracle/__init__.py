@@ -61,16 +61,17 @@ def _declare(lib):
     i, d = ct.c_int, ct.c_double
     lib.sfo_basis.argtypes = [i, i, _D]
     lib.sfo_basis_dd.argtypes = [i, i, d, _D]
+    lib.sfo_basis_d.argtypes = [i, i, d, _D]
     lib.sfo_estep.argtypes = [i, _D, d, d, _D, _D]
-    lib.sfo_kkt.argtypes = [i, i, d, i, i, i, i, i, d, _D, _D, _D]
+    lib.sfo_kkt.argtypes = [i, i, d, i, i, i, i, i, d, i, _D, _D, _D]
     lib.sfo_residual.argtypes = [i, i, d, i, i, i, i, d, d, _D, _D, _D, _D, _D, _D, _D]
-    lib.sfo_solve.argtypes = [i, i, d, i, i, i, i, d, d, _D, _D, _D, _D, _D, _D, _D, _D, i, i, i, d,
+    lib.sfo_solve.argtypes = [i, i, d, i, i, i, i, d, d, _D, _D, _D, _D, _D, _D, _D, _D, i, i, i, d, i,
                               _D, _D, _D, _D]
     lib.sfo_solve_backward.argtypes = [i, i, d, i, i, i, i, d, d, _D, _D, _D, _D, _D, _D, _D, _D,
-                                       i, i, i, d, _D, _D, d, _D, _D, _D]
+                                       i, i, i, d, i, _D, _D, d, d, _D, _D, _D]
     lib.sfo_solve_batch.argtypes = [i, i, i, d, _I, _D, _D, _D, _LL, _D, _LL, _D, _LL, _D, _LL,
-                                    i, i, i, d, _D, _D, _D]
-    for f in ("sfo_basis", "sfo_basis_dd", "sfo_estep", "sfo_kkt", "sfo_residual", "sfo_solve",
+                                    i, i, i, d, i, _D, _D, _D]
+    for f in ("sfo_basis", "sfo_basis_dd", "sfo_basis_d", "sfo_estep", "sfo_kkt", "sfo_residual", "sfo_solve",
               "sfo_solve_backward", "sfo_solve_batch"):
         getattr(lib, f).restype = ct.c_int
     return lib
@@ -122,16 +123,31 @@ def basis_dd(H, n_xi, dt=DEFAULT_DT, lib=None):
     return W
 
 
-def kkt(n_d, n_xi, rho, n, n_obs, H, ws_hess=True, cost="projection", dt=DEFAULT_DT, lib=None):
-    """Explicit per-axis Hessian, P_eta and P_b of the xi_bar step."""
+def basis_d(H, n_xi, dt=DEFAULT_DT, lib=None):
+    """First time derivative of the basis, t = tau (H - 1) dt (initial-velocity rows)."""
+    lib = lib or load()
+    W = np.empty((H, n_xi))
+    _check(lib.sfo_basis_d(H, n_xi, float(dt), _p(W)), "basis_d")
+    return W
+
+
+def kkt(n_d, n_xi, rho, n, n_obs, H, ws_hess=True, cost="projection", dt=DEFAULT_DT, n_bc=2, lib=None):
+    """Explicit per-axis Hessian, P_eta and P_b of the xi_bar step (P_b columns robot-major:
+    start, goal[, initial velocity])."""
     lib = lib or load()
     N = n * n_xi
     Hm = np.empty((N, N))
     Pe = np.empty((N, N))
-    Pb = np.empty((N, 2 * n))
-    _check(lib.sfo_kkt(n_d, n_xi, rho, n, n_obs, H, int(ws_hess), COSTS[cost], float(dt), _p(Hm), _p(Pe),
-                       _p(Pb)), "kkt")
+    Pb = np.empty((N, n_bc * n))
+    _check(lib.sfo_kkt(n_d, n_xi, rho, n, n_obs, H, int(ws_hess), COSTS[cost], float(dt), int(n_bc), _p(Hm),
+                       _p(Pe), _p(Pb)), "kkt")
     return Hm, Pe, Pb
+
+
+def n_bc(inst):
+    """Boundary rows per robot and axis: 2 (start, goal) or 3 (with the initial velocity),
+    the last extent of the instance's boundary array."""
+    return int(np.shape(inst["bnd"])[-1])
 
 
 def _inst_args(inst, rho):
@@ -172,7 +188,7 @@ def solve(inst, iters, rho=DEFAULT_RHO, xi0=None, lam0=None, ws_hess=True, hist=
     tr = np.empty((iters + 1, 2) + xi.shape) if traj else None
     _check(lib.sfo_solve(*_inst_args(inst, rho), _p(pmin), _p(pmax), _p(obs_c), _p(obs_ab),
                          _p(_c(inst["bnd"])), _p(xi), _p(xi0), _p(lam0), int(iters), int(ws_hess),
-                         COSTS[cost], float(dt), _p(xo), _p(lo), _p(h), _p(tr)), "solve")
+                         COSTS[cost], float(dt), n_bc(inst), _p(xo), _p(lo), _p(h), _p(tr)), "solve")
     out = dict(xi=xo, lam=lo)
     if hist:
         out["hist"] = h
@@ -182,8 +198,10 @@ def solve(inst, iters, rho=DEFAULT_RHO, xi0=None, lam0=None, ws_hess=True, hist=
 
 
 def solve_backward(inst, iters, g_xi_out=None, g_lam_out=None, g_rp2=0.0, rho=DEFAULT_RHO,
-                   xi0=None, lam0=None, ws_hess=True, cost="projection", dt=DEFAULT_DT, lib=None):
-    """Reverse mode through ``iters`` SF iterations: (g_xi_cand, g_xi0, g_lam0)."""
+                   xi0=None, lam0=None, ws_hess=True, cost="projection", dt=DEFAULT_DT, g_fp=0.0, lib=None):
+    """Reverse mode through ``iters`` SF iterations: (g_xi_cand, g_xi0, g_lam0).  Seeds: the
+    outputs' cotangents, g_rp2 (weight of ||r_p(xi_out)||^2) and g_fp (weight of the
+    self-supervised fixed-point term sum_l ||z^{l+1} - z^l||^2 of eq. NN_loss)."""
     lib = lib or load()
     pmin, pmax, obs_c, obs_ab = _geom(inst)
     xi = _c(inst["xi"])
@@ -191,8 +209,8 @@ def solve_backward(inst, iters, g_xi_out=None, g_lam_out=None, g_rp2=0.0, rho=DE
     _check(lib.sfo_solve_backward(*_inst_args(inst, rho), _p(pmin), _p(pmax), _p(obs_c),
                                   _p(obs_ab), _p(_c(inst["bnd"])), _p(xi), _p(_c(xi0)),
                                   _p(_c(lam0)), int(iters), int(ws_hess), COSTS[cost], float(dt),
-                                  _p(_c(g_xi_out)),
-                                  _p(_c(g_lam_out)), float(g_rp2), _p(gx), _p(gx0), _p(gl0)),
+                                  n_bc(inst), _p(_c(g_xi_out)),
+                                  _p(_c(g_lam_out)), float(g_rp2), float(g_fp), _p(gx), _p(gx0), _p(gl0)),
            "solve_backward")
     return gx, gx0, gl0
 
@@ -229,7 +247,8 @@ def solve_batch(insts, iters, rho=DEFAULT_RHO, ws_hess=True, threads=None, cost=
     ll = lambda a: a.ctypes.data_as(_LL)
     _check(lib.sfo_solve_batch(B, nd, nxi, float(rho), shp.ctypes.data_as(_I), _p(ab), _p(box),
                                _p(obs_c), ll(o_obs), _p(obs_ab), ll(o_oab), _p(bnd), ll(o_bnd),
-                               _p(xi), ll(o_xi), int(iters), int(ws_hess), COSTS[cost], float(dt), _p(xo), None,
+                               _p(xi), ll(o_xi), int(iters), int(ws_hess), COSTS[cost], float(dt),
+                               n_bc(insts[0]), _p(xo), None,
                                _p(resid)), "solve_batch")
     outs = [xo[o_xi[k]:o_xi[k] + insts[k]["xi"].size].reshape(insts[k]["xi"].shape)
             for k in range(B)]

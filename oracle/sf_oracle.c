@@ -52,6 +52,15 @@
  *  R13 time scale: p'' is taken with respect to time t = tau (H - 1) dt, dt a parameter
  *      (the paper gives no time step); the smoothness mode needs the workspace terms in
  *      the Hessian (ws_hess = 1), which make it positive definite.
+ *  R14 initial-velocity boundary rows (Sec. V, hardware experiments: the planner is
+ *      conditioned on the robots' initial velocities): with nbc = 3 each robot and axis
+ *      adds the row p'(t = 0) = v_0 to A, the first time derivative of the basis at
+ *      tau = 0 in the time of R13; the boundary values per robot and axis are then
+ *      (start, goal, v_0).  For Bernstein the row fixes coefficient 1 as well.
+ *  R15 self-supervised loss (eq. NN_loss): sum over l = 0..L-1 of
+ *      L_FP = ||z^{l+1} - z^l||^2 with z = (xi_bar, lambda) (the fixed-point residual of
+ *      eq. fixed_point_residual read as in R8), weighted by g_fp in the reverse pass;
+ *      the term ||xi_bar^L - xi||^2 enters through the ordinary output seed.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -60,7 +69,7 @@
 #define SFO_NHIST 4 /* per-iteration history: ||r_p||, max residual, FP residual, kink margin */
 
 typedef struct {
-    int nd, nxi, n, nobs, H, dyn, ws_hess, cost;
+    int nd, nxi, n, nobs, H, dyn, ws_hess, cost, nbc;
     double rho, a, b, dt;
     const double *pmin, *pmax, *obs_c, *obs_ab, *bnd, *xi;
 } prob_t;
@@ -69,8 +78,9 @@ typedef struct {
     int N, npair, rows_pair, rows_obs, rows_F, rows_G;
     double *W;   /* H x nxi basis                                   */
     double *L;   /* Cholesky factor of the xi_bar-step Hessian, N x N */
-    double *Y;   /* H^-1 A^T, N x 2n                                 */
-    double *LS;  /* Cholesky factor of S = A H^-1 A^T, 2n x 2n      */
+    double *Y;   /* H^-1 A^T, N x nbc n                              */
+    double *LS;  /* Cholesky factor of S = A H^-1 A^T, nbc n square */
+    double *Wd0; /* first time derivative of the basis at tau = 0 (R14) */
     int *pi, *pj; /* pair list in F_r row order                     */
 } ctx_t;
 
@@ -114,6 +124,29 @@ int sfo_basis_dd(int H, int nxi, double dt, double *Wdd)
                 v += w * binom(deg - 2, j) * pow(tau, j) * pow(1.0 - tau, deg - 2 - j);
             }
             Wdd[k * nxi + c] = scale * v;
+        }
+    }
+    return 0;
+}
+
+/* Wd[k][c] = d/dt of the c-th basis polynomial at t_k = tau_k T, T = (H-1) dt: a
+   degree-d Bernstein polynomial's derivative is d times the first difference of the
+   degree-(d-1) polynomials, scaled by 1/T (readings R13, R14). */
+int sfo_basis_d(int H, int nxi, double dt, double *Wd)
+{
+    if (H < 2 || nxi < 2 || !(dt > 0.0)) return -1;
+    int deg = nxi - 1;
+    double T = (double)(H - 1) * dt;
+    for (int k = 0; k < H; k++) {
+        const double tau = k / (H - 1.0);
+        for (int c = 0; c < nxi; c++) {
+            double v = 0.0;
+            for (int j = c - 1; j <= c; j++) {
+                if (j < 0 || j > deg - 1) continue;
+                double w = j == c - 1 ? 1.0 : -1.0;
+                v += w * binom(deg - 1, j) * pow(tau, j) * pow(1.0 - tau, deg - 1 - j);
+            }
+            Wd[k * nxi + c] = (double)deg * v / T;
         }
     }
     return 0;
@@ -230,24 +263,31 @@ static double h_of(const prob_t *P, int ax, int g) /* h = [p_max; -p_min] */
     return g < P->n * P->H ? P->pmax[ax] : -P->pmin[ax];
 }
 
-/* A rows of one axis: row 2i = W[0] on robot i (start), row 2i+1 = W[H-1] on robot i (goal) */
+/* Boundary row s of one robot (eq. boundary_con): s = 0 the start W[0], s = 1 the goal
+   W[H-1], s = 2 the initial velocity p'(0) (reading R14). */
+static const double *A_row(const prob_t *P, const ctx_t *C, int s)
+{
+    return s == 2 ? C->Wd0 : C->W + (size_t)(s ? P->H - 1 : 0) * P->nxi;
+}
+
+/* A rows of one axis: row nbc i + s is boundary row s on robot i */
 static void A_apply(const prob_t *P, const ctx_t *C, const double *x, double *y)
 {
     for (int i = 0; i < P->n; i++)
-        for (int s = 0; s < 2; s++) {
-            int k = s ? P->H - 1 : 0;
+        for (int s = 0; s < P->nbc; s++) {
+            const double *w = A_row(P, C, s);
             double t = 0.0;
-            for (int c = 0; c < P->nxi; c++) t += C->W[k * P->nxi + c] * x[i * P->nxi + c];
-            y[2 * i + s] = t;
+            for (int c = 0; c < P->nxi; c++) t += w[c] * x[i * P->nxi + c];
+            y[P->nbc * i + s] = t;
         }
 }
 
 static void AT_apply(const prob_t *P, const ctx_t *C, const double *nu, double *out)
 {
     for (int i = 0; i < P->n; i++)
-        for (int s = 0; s < 2; s++) {
-            int k = s ? P->H - 1 : 0;
-            for (int c = 0; c < P->nxi; c++) out[i * P->nxi + c] += C->W[k * P->nxi + c] * nu[2 * i + s];
+        for (int s = 0; s < P->nbc; s++) {
+            const double *w = A_row(P, C, s);
+            for (int c = 0; c < P->nxi; c++) out[i * P->nxi + c] += w[c] * nu[P->nbc * i + s];
         }
 }
 
@@ -320,7 +360,7 @@ static const double *obs_at(const prob_t *P, int m, int k)
 /* ------------------------------------------------------------------ set-up */
 static void ctx_free(ctx_t *C)
 {
-    free(C->W); free(C->L); free(C->Y); free(C->LS); free(C->pi); free(C->pj);
+    free(C->W); free(C->L); free(C->Y); free(C->LS); free(C->pi); free(C->pj); free(C->Wd0);
     memset(C, 0, sizeof(*C));
 }
 
@@ -338,14 +378,22 @@ static int ctx_init(const prob_t *P, ctx_t *C)
     C->rows_obs = n * P->nobs * H;
     C->rows_F = C->rows_pair + C->rows_obs;
     C->rows_G = 2 * n * H;
+    const int m = P->nbc * n;
     C->W = malloc(sizeof(double) * H * nxi);
     C->L = calloc((size_t)N * N, sizeof(double));
-    C->Y = calloc((size_t)N * 2 * n, sizeof(double));
-    C->LS = calloc((size_t)4 * n * n, sizeof(double));
+    C->Y = calloc((size_t)N * m, sizeof(double));
+    C->LS = calloc((size_t)m * m, sizeof(double));
     C->pi = malloc(sizeof(int) * (C->npair + 1));
     C->pj = malloc(sizeof(int) * (C->npair + 1));
-    if (!C->W || !C->L || !C->Y || !C->LS || !C->pi || !C->pj) { ctx_free(C); return -2; }
+    C->Wd0 = calloc(nxi, sizeof(double));
+    if (!C->W || !C->L || !C->Y || !C->LS || !C->pi || !C->pj || !C->Wd0) { ctx_free(C); return -2; }
     sfo_basis(H, nxi, C->W);
+    if (P->nbc == 3) {
+        double *Wd = malloc(sizeof(double) * H * nxi);
+        if (!Wd || sfo_basis_d(H, nxi, P->dt, Wd)) { free(Wd); ctx_free(C); return -1; }
+        memcpy(C->Wd0, Wd, sizeof(double) * nxi);   /* row tau = 0 */
+        free(Wd);
+    }
     int p = 0;
     for (int i = 0; i < n; i++)
         for (int j = i + 1; j < n; j++) { C->pi[p] = i; C->pj[p] = j; p++; }
@@ -394,24 +442,24 @@ static int ctx_init(const prob_t *P, ctx_t *C)
 
     /* Y = H^-1 A^T, column by column */
     double *col = malloc(sizeof(double) * N);
-    double *unit = calloc(2 * n, sizeof(double));
-    for (int q = 0; q < 2 * n; q++) {
+    double *unit = calloc(m, sizeof(double));
+    for (int q = 0; q < m; q++) {
         memset(col, 0, sizeof(double) * N);
         unit[q] = 1.0;
         AT_apply(P, C, unit, col);
         unit[q] = 0.0;
         chol_solve(N, C->L, col);
-        for (int u = 0; u < N; u++) C->Y[u * 2 * n + q] = col[u];
+        for (int u = 0; u < N; u++) C->Y[u * m + q] = col[u];
     }
     /* S = A Y */
-    double *ay = malloc(sizeof(double) * 2 * n);
-    for (int q = 0; q < 2 * n; q++) {
-        for (int u = 0; u < N; u++) col[u] = C->Y[u * 2 * n + q];
+    double *ay = malloc(sizeof(double) * m);
+    for (int q = 0; q < m; q++) {
+        for (int u = 0; u < N; u++) col[u] = C->Y[u * m + q];
         A_apply(P, C, col, ay);
-        for (int r = 0; r < 2 * n; r++) C->LS[r * 2 * n + q] = ay[r];
+        for (int r = 0; r < m; r++) C->LS[r * m + q] = ay[r];
     }
     free(col); free(unit); free(ay);
-    if (cholesky(2 * n, C->LS)) { ctx_free(C); return -3; }
+    if (cholesky(m, C->LS)) { ctx_free(C); return -3; }
     return 0;
 }
 
@@ -419,7 +467,7 @@ static int ctx_init(const prob_t *P, ctx_t *C)
    bb may be NULL for b = 0. */
 static void kkt_solve(const prob_t *P, const ctx_t *C, const double *eta, const double *bb, double *x)
 {
-    int N = C->N, m = 2 * P->n;
+    int N = C->N, m = P->nbc * P->n;
     double *u = malloc(sizeof(double) * m);
     memcpy(x, eta, sizeof(double) * N);
     chol_solve(N, C->L, x);             /* t = H^-1 eta            */
@@ -527,7 +575,7 @@ static void T_apply(const prob_t *P, const ctx_t *C, const double *xib, const do
     /* xi_bar step (eq. xi_step): eta = xi + lambda' + rho F'e (+ rho G'(h - s)), KKT solve
        (the smoothness cost has no linear term: eta = lambda' + ...) */
     double *hs = malloc(sizeof(double) * RG);
-    double *bb = malloc(sizeof(double) * 2 * P->n);
+    double *bb = malloc(sizeof(double) * P->nbc * P->n);
     for (int ax = 0; ax < nd; ax++) {
         double *eta = B->v2 + (size_t)ax * N;
         for (int u = 0; u < N; u++)
@@ -540,10 +588,8 @@ static void T_apply(const prob_t *P, const ctx_t *C, const double *xib, const do
             GT_apply(P, C, hs, fe);
         }
         for (int u = 0; u < N; u++) eta[u] += P->rho * fe[u];
-        for (int i = 0; i < P->n; i++) {
-            bb[2 * i] = P->bnd[((size_t)ax * P->n + i) * 2 + 0];
-            bb[2 * i + 1] = P->bnd[((size_t)ax * P->n + i) * 2 + 1];
-        }
+        for (int i = 0; i < P->n; i++)
+            for (int s = 0; s < P->nbc; s++) bb[P->nbc * i + s] = P->bnd[((size_t)ax * P->n + i) * P->nbc + s];
         kkt_solve(P, C, eta, bb, xib_new + (size_t)ax * N);
     }
     free(hs);
@@ -554,11 +600,11 @@ static void T_apply(const prob_t *P, const ctx_t *C, const double *xib, const do
 static void fill_prob(prob_t *P, int nd, int nxi, double rho, int n, int nobs, int H, int dyn,
                       double a, double b, const double *pmin, const double *pmax, const double *obs_c,
                       const double *obs_ab, const double *bnd, const double *xi, int ws_hess, int cost,
-                      double dt)
+                      double dt, int nbc)
 {
     P->nd = nd; P->nxi = nxi; P->rho = rho; P->n = n; P->nobs = nobs; P->H = H; P->dyn = dyn;
     P->a = a; P->b = b; P->pmin = pmin; P->pmax = pmax; P->obs_c = obs_c; P->obs_ab = obs_ab;
-    P->bnd = bnd; P->xi = xi; P->ws_hess = ws_hess; P->cost = cost; P->dt = dt;
+    P->bnd = bnd; P->xi = xi; P->ws_hess = ws_hess; P->cost = cost; P->dt = dt; P->nbc = nbc;
 }
 
 static int check_prob(const prob_t *P)
@@ -566,23 +612,25 @@ static int check_prob(const prob_t *P)
     if (P->nd < 2 || P->nd > 3 || P->nxi < 2 || P->n < 1 || P->nobs < 0 || P->H < 2) return -1;
     if (!(P->rho > 0.0) || !(P->a > 0.0) || !(P->b > 0.0)) return -1;
     if (P->cost != 0 && (P->cost != 1 || !P->ws_hess || P->nxi < 3 || !(P->dt > 0.0))) return -1;
+    if (P->nbc != 2 && (P->nbc != 3 || P->nxi < 4 || !(P->dt > 0.0))) return -1;
     return 0;
 }
 
 /* Explicit pieces of the KKT system for one axis (pins only):
-   Hm = I + rho F'F (+ rho G'G)  (N x N), Peta (N x N) and Pb (N x 2n) with
+   Hm = I + rho F'F (+ rho G'G)  (N x N), Peta (N x N) and Pb (N x nbc n) with
    argmin_{Ax=b} 1/2 x'Hx - eta'x = Peta eta + Pb b. */
-int sfo_kkt(int nd, int nxi, double rho, int n, int nobs, int H, int ws_hess, int cost, double dt,
+int sfo_kkt(int nd, int nxi, double rho, int n, int nobs, int H, int ws_hess, int cost, double dt, int nbc,
             double *Hm, double *Peta, double *Pb)
 {
     prob_t P;
     double zeros[3] = {0, 0, 0};
-    fill_prob(&P, nd, nxi, rho, n, nobs, H, 0, 1.0, 1.0, zeros, zeros, NULL, NULL, NULL, NULL, ws_hess, cost, dt);
+    fill_prob(&P, nd, nxi, rho, n, nobs, H, 0, 1.0, 1.0, zeros, zeros, NULL, NULL, NULL, NULL, ws_hess, cost, dt,
+              nbc);
     if (check_prob(&P)) return -1;
     ctx_t C;
     int rc = ctx_init(&P, &C);
     if (rc) return rc;
-    int N = C.N, m = 2 * n;
+    int N = C.N, m = nbc * n;
     if (Hm) {
         /* reassemble H = L L^T */
         for (int u = 0; u < N; u++)
@@ -622,7 +670,7 @@ int sfo_residual(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, d
                  const double *xib, double *out, double *g)
 {
     prob_t P;
-    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, NULL, NULL, 1, 0, 0.0);
+    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, NULL, NULL, 1, 0, 0.0, 2);
     if (check_prob(&P)) return -1;
     ctx_t C;
     memset(&C, 0, sizeof(C));
@@ -667,11 +715,11 @@ int sfo_residual(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, d
 int sfo_solve(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, double a, double b,
               const double *pmin, const double *pmax, const double *obs_c, const double *obs_ab,
               const double *bnd, const double *xi, const double *xi0, const double *lam0,
-              int iters, int ws_hess, int cost, double dt, double *xi_out, double *lam_out,
+              int iters, int ws_hess, int cost, double dt, int nbc, double *xi_out, double *lam_out,
               double *hist, double *traj)
 {
     prob_t P;
-    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, bnd, xi, ws_hess, cost, dt);
+    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, bnd, xi, ws_hess, cost, dt, nbc);
     if (check_prob(&P) || iters < 0) return -1;
     ctx_t C;
     int rc = ctx_init(&P, &C);
@@ -712,18 +760,21 @@ int sfo_solve(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, doub
 }
 
 /* Reverse mode through `iters` applications of T (hand-written adjoint of each step,
-   conventions R9).  Seeds: g_xi_out, g_lam_out (nd x N, either may be NULL) and g_rp2,
-   the weight of ||r_p(xi_out)||^2 in the loss.  Outputs (nd x N each, any may be NULL):
-   gradients with respect to the candidate xi, the initial xi_bar and the initial lambda.
-   The candidate also enters through xi0 when xi0 is NULL; that path is added to g_xi. */
+   conventions R9).  Seeds: g_xi_out, g_lam_out (nd x N, either may be NULL); g_rp2, the
+   weight of ||r_p(xi_out)||^2 in the loss; g_fp, the weight of the self-supervised
+   fixed-point term sum_{l<iters} ||z^{l+1} - z^l||^2, z = (xi_bar, lambda) (reading R15).
+   Outputs (nd x N each, any may be NULL): gradients with respect to the candidate xi,
+   the initial xi_bar and the initial lambda.  The candidate also enters through xi0 when
+   xi0 is NULL; that path is added to g_xi. */
 int sfo_solve_backward(int nd, int nxi, double rho, int n, int nobs, int H, int dyn, double a, double b,
                        const double *pmin, const double *pmax, const double *obs_c, const double *obs_ab,
                        const double *bnd, const double *xi, const double *xi0, const double *lam0,
-                       int iters, int ws_hess, int cost, double dt, const double *g_xi_out,
-                       const double *g_lam_out, double g_rp2, double *g_xi, double *g_xi0, double *g_lam0)
+                       int iters, int ws_hess, int cost, double dt, int nbc, const double *g_xi_out,
+                       const double *g_lam_out, double g_rp2, double g_fp, double *g_xi, double *g_xi0,
+                       double *g_lam0)
 {
     prob_t P;
-    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, bnd, xi, ws_hess, cost, dt);
+    fill_prob(&P, nd, nxi, rho, n, nobs, H, dyn, a, b, pmin, pmax, obs_c, obs_ab, bnd, xi, ws_hess, cost, dt, nbc);
     if (check_prob(&P) || iters < 0) return -1;
     ctx_t C;
     int rc = ctx_init(&P, &C);
@@ -784,6 +835,12 @@ int sfo_solve_backward(int nd, int nxi, double rho, int n, int nobs, int H, int 
 
     for (int it = iters - 1; it >= 0; it--) {
         double st[3];
+        /* the fixed-point term's share of z^{it+1}: d/dz^{it+1} of g_fp ||z^{it+1} - z^it||^2 */
+        if (g_fp != 0.0)
+            for (size_t u = 0; u < NN; u++) {
+                xb[u] += 2.0 * g_fp * (X[NN * (it + 1) + u] - X[NN * it + u]);
+                lb[u] += 2.0 * g_fp * (Lm[NN * (it + 1) + u] - Lm[NN * it + u]);
+            }
         evaluate(&P, &C, X + NN * it, &B, st); /* recompute y, e, q, s of iterate it */
         for (int ax = 0; ax < nd; ax++) {
             /* eta_bar = Peta^T xi_bar'_bar (Peta symmetric: one KKT solve with b = 0) */
@@ -836,6 +893,12 @@ int sfo_solve_backward(int nd, int nxi, double rho, int n, int nobs, int H, int 
             FT_apply(&P, &C, yb + (size_t)ax * RF, xb + (size_t)ax * N);
             GT_apply(&P, &C, qb + (size_t)ax * RG, xb + (size_t)ax * N);
         }
+        /* and its share of z^it */
+        if (g_fp != 0.0)
+            for (size_t u = 0; u < NN; u++) {
+                xb[u] -= 2.0 * g_fp * (X[NN * (it + 1) + u] - X[NN * it + u]);
+                lb[u] -= 2.0 * g_fp * (Lm[NN * (it + 1) + u] - Lm[NN * it + u]);
+            }
     }
     if (g_xi) {
         memcpy(g_xi, gx, sizeof(double) * NN);
@@ -857,7 +920,7 @@ int sfo_solve_batch(int B, int nd, int nxi, double rho, const int *shp, const do
                     const double *box, const double *obs_c, const long long *off_obs,
                     const double *obs_ab, const long long *off_oab, const double *bnd,
                     const long long *off_bnd, const double *xi, const long long *off_xi,
-                    int iters, int ws_hess, int cost, double dt, double *xi_out, double *lam_out,
+                    int iters, int ws_hess, int cost, double dt, int nbc, double *xi_out, double *lam_out,
                     double *resid)
 {
     int status = 0;
@@ -866,7 +929,7 @@ int sfo_solve_batch(int B, int nd, int nxi, double rho, const int *shp, const do
         const int *s = shp + 4 * i;
         int rc = sfo_solve(nd, nxi, rho, s[0], s[1], s[2], s[3], ab[2 * i], ab[2 * i + 1],
                            box + 6 * i, box + 6 * i + 3, obs_c + off_obs[i], obs_ab + off_oab[i],
-                           bnd + off_bnd[i], xi + off_xi[i], NULL, NULL, iters, ws_hess, cost, dt,
+                           bnd + off_bnd[i], xi + off_xi[i], NULL, NULL, iters, ws_hess, cost, dt, nbc,
                            xi_out + off_xi[i], lam_out ? lam_out + off_xi[i] : NULL, NULL, NULL);
         if (rc == 0 && resid) {
             double out[3];

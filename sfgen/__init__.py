@@ -13,7 +13,8 @@ Every instance is a dict of float64 numpy arrays:
   obs_c       [n_obs][n_d]      static obstacle centres
               or [n_obs][H][n_d] when dyn_obs is true (per-timestep centres)
   obs_ab      [n_obs][2]        obstacle axes (a_o, b_o), inflated by the robot radius
-  bnd         [n_d][n][2]       boundary values (start, goal) per axis and robot
+  bnd         [n_d][n][2]       boundary values (start, goal) per axis and robot, or
+              [n_d][n][3]       (start, goal, initial velocity in m/s) with initial-velocity rows
   xi          [n_d][n][n_xi]    candidate coefficients, axis-major (Sec. III-A, coefficient stacking)
 
 Candidates are written directly in coefficient space.  The trajectory basis is
@@ -176,6 +177,17 @@ def custom_instance(n, n_obs, H, n_d=2, n_xi=N_XI_DEFAULT, seed=0, extent=10.0, 
     return make_instance(cfg, 0, n_xi=n_xi, dyn_obs=dyn_obs)
 
 
+def with_initial_velocity(inst, seed, vmax=0.5):
+    """A copy of ``inst`` with an initial velocity per robot and axis, uniform in
+    [-vmax, vmax] m/s (seeded), appended to the boundary values: bnd becomes
+    [n_d][n][3] = (start, goal, v_0).  The candidate is left as it is."""
+    rng = np.random.Generator(np.random.PCG64(7919 + seed))
+    v0 = rng.uniform(-vmax, vmax, size=inst["bnd"].shape[:2])
+    out = dict(inst)
+    out["bnd"] = np.ascontiguousarray(np.concatenate([inst["bnd"][..., :2], v0[..., None]], axis=-1))
+    return out
+
+
 def batch_stats(insts):
     """Counts of pair-timestep and robot-obstacle-timestep rows per iteration."""
     pairs = sum(i["n"] * (i["n"] - 1) // 2 * i["H"] for i in insts)
@@ -184,4 +196,4 @@ def batch_stats(insts):
 
 
 __all__ = ["CONFIGS", "SFConfig", "make_instance", "make_batch", "custom_instance",
-           "batch_stats", "rng_for", "N_XI_DEFAULT"]
+           "with_initial_velocity", "batch_stats", "rng_for", "N_XI_DEFAULT"]

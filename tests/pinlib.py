@@ -29,6 +29,15 @@ def bernstein_dd(H, n_xi, dt):
     return np.stack(cols, axis=1)
 
 
+def bernstein_d(H, n_xi, dt):
+    """First time derivative of the Bernstein basis at t_k = k dt on [0, (H-1) dt], via
+    scipy.BPoly.derivative (initial-velocity boundary rows)."""
+    T = (H - 1) * dt
+    t = np.linspace(0.0, T, H)
+    cols = [si.BPoly(np.eye(n_xi)[c][:, None], [0.0, T]).derivative(1)(t) for c in range(n_xi)]
+    return np.stack(cols, axis=1)
+
+
 def incidence(n):
     """Stacked F_{r,i} = [F_i, -I] of the Appendix: row (i, j>i) is e_i - e_j."""
     rows = []
@@ -39,14 +48,16 @@ def incidence(n):
     return np.vstack(rows) if rows else np.zeros((0, n))
 
 
-def dense_mats(n, n_obs, H, n_xi):
-    """Per-axis F (pair rows then obstacle rows), G, A for one instance."""
+def dense_mats(n, n_obs, H, n_xi, n_bc=2, dt=0.1):
+    """Per-axis F (pair rows then obstacle rows), G, A for one instance.  A's rows per robot:
+    start W[0], goal W[H-1] and, with n_bc = 3, the initial velocity p'(0) (time t = tau (H-1) dt)."""
     W = bernstein(H, n_xi)
     Fr = np.kron(incidence(n), W)
     Fo = np.kron(np.eye(n), np.vstack([W] * n_obs)) if n_obs else np.zeros((0, n * n_xi))
     F = np.vstack([Fr, Fo])
     G = np.vstack([np.kron(np.eye(n), W), -np.kron(np.eye(n), W)])
-    A = np.kron(np.eye(n), np.vstack([W[0], W[-1]]))
+    rows = [W[0], W[-1]] + ([bernstein_d(H, n_xi, dt)[0]] if n_bc == 3 else [])
+    A = np.kron(np.eye(n), np.vstack(rows))
     return W, F, G, A
 
 
@@ -93,7 +104,7 @@ def exterior_projection_bruteforce(delta, a):
     return cost_dir(res.x)[1]
 
 
-def one_step_reference(inst, xib, lam, rho, ws_hess=True, Q1=None):
+def one_step_reference(inst, xib, lam, rho, ws_hess=True, Q1=None, dt=0.1):
     """One AM sweep (alpha, beta, d, s, lambda, xi_bar) built from the augmented Lagrangian.
 
     Isotropic robots and obstacles only: the joint (alpha, beta, d) minimiser of
@@ -101,7 +112,7 @@ def one_step_reference(inst, xib, lam, rho, ws_hess=True, Q1=None):
     exterior of the ball, found by brute force row by row.
     """
     n, n_obs, H, nd, n_xi = inst["n"], inst["n_obs"], inst["H"], inst["n_d"], inst["n_xi"]
-    W, F, G, A = dense_mats(n, n_obs, H, n_xi)
+    W, F, G, A = dense_mats(n, n_obs, H, n_xi, inst["bnd"].shape[-1], dt)
     cen, rad = row_centres(inst)
     y = np.stack([F @ xib[ax].ravel() for ax in range(nd)])
     e = np.empty_like(y)
@@ -122,7 +133,7 @@ def one_step_reference(inst, xib, lam, rho, ws_hess=True, Q1=None):
         lin = (inst["xi"][ax].ravel() if Q1 is None else 0.0) + lam_new[ax].ravel() + rho * F.T @ e[ax]
         if ws_hess:
             lin = lin + rho * G.T @ (h - s)
-        b = inst["bnd"][ax].reshape(-1)  # (start, goal) per robot, robot-major
+        b = inst["bnd"][ax].reshape(-1)  # (start, goal[, v_0]) per robot, robot-major
         K = np.block([[Hm, A.T], [A, np.zeros((A.shape[0], A.shape[0]))]])
         sol = np.linalg.solve(K, np.concatenate([lin, b]))
         xi_new[ax] = sol[:n * n_xi].reshape(n, n_xi)

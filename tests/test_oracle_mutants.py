@@ -38,6 +38,13 @@ MUTANTS = {
                                    "eta[u] = P->xi[(size_t)ax * N + u] + lam_new"),
     "smooth_time_scale_not_squared": ("/ (T * T);", "/ T;"),
     "adjoint_smooth_candidate_gradient": ("if (P.cost == 0) gx[(size_t)ax * N + u] += etab", "gx[(size_t)ax * N + u] += etab"),
+    "velocity_basis_difference_sign": ("double w = j == c - 1 ? 1.0 : -1.0;", "double w = j == c - 1 ? -1.0 : 1.0;"),
+    "velocity_time_scale_dropped": ("Wd[k * nxi + c] = (double)deg * v / T;", "Wd[k * nxi + c] = (double)deg * v;"),
+    "velocity_row_is_goal_derivative": ("memcpy(C->Wd0, Wd, sizeof(double) * nxi);",
+                                        "memcpy(C->Wd0, Wd + (size_t)(H - 1) * nxi, sizeof(double) * nxi);"),
+    "fp_seed_sign_on_later_iterate": ("xb[u] += 2.0 * g_fp", "xb[u] -= 2.0 * g_fp"),
+    "fp_seed_lambda_dropped": ("lb[u] += 2.0 * g_fp * (Lm[NN * (it + 1) + u] - Lm[NN * it + u]);", ";"),
+    "fp_seed_earlier_iterate_dropped": ("xb[u] -= 2.0 * g_fp * (X[NN * (it + 1) + u] - X[NN * it + u]);", ";"),
 }
 
 

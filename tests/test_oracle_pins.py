@@ -533,3 +533,156 @@ def test_select_orders_feasible_by_secondary_then_the_rest():
     assert oracle.select(p, q, 1e-3, 6) == [3, 1, 5, 0, 4, 2]
     assert oracle.select(p, None, -np.inf, 3) == [1, 5, 3]
     assert oracle.select([1.0, 0.5], None, -np.inf, 4) == [1, 0, -1, -1]
+
+
+# ------------------------------------------- initial-velocity boundary rows (Sec. V, hardware)
+VDT = 0.1   # time step of the velocity rows' time scale
+
+
+def _vel_instance(cid=1, idx=0, seed=0):
+    return sfgen.with_initial_velocity(sfgen.make_batch(cid, B=idx + 1)[idx], seed)
+
+
+@pytest.mark.parametrize("H,nxi,dt", [(20, 6, 0.1), (50, 11, 0.05)])
+def test_velocity_basis_is_bernstein_first_derivative(H, nxi, dt):
+    np.testing.assert_allclose(oracle.basis_d(H, nxi, dt), pinlib.bernstein_d(H, nxi, dt), atol=1e-11)
+
+
+@pytest.mark.parametrize("n,n_obs,H,nxi", [(3, 2, 12, 6), (2, 0, 9, 5)])
+def test_velocity_kkt_matches_dense_kkt(n, n_obs, H, nxi):
+    """P_eta and P_b with the velocity rows against numpy's solve of the KKT system built
+    from the Appendix's matrices with A = I (x) [W_0; W_{H-1}; W'_0]."""
+    _, F, G, A = pinlib.dense_mats(n, n_obs, H, nxi, n_bc=3, dt=VDT)
+    Hm = np.eye(n * nxi) + RHO * (F.T @ F + G.T @ G)
+    K = np.block([[Hm, A.T], [A, np.zeros((A.shape[0], A.shape[0]))]])
+    Kinv = np.linalg.inv(K)
+    _, Pe, Pb = oracle.kkt(2, nxi, RHO, n, n_obs, H, dt=VDT, n_bc=3)
+    N = n * nxi
+    np.testing.assert_allclose(Pe, Kinv[:N, :N], atol=1e-11)
+    np.testing.assert_allclose(Pb, Kinv[:N, N:], atol=1e-11)
+
+
+def test_velocity_rows_hold_every_iterate():
+    """A xi_bar = b for all three rows per robot and axis after every xi_bar step, the
+    velocity row evaluated with scipy's derivative of the basis."""
+    inst = _vel_instance()
+    tr = oracle.solve(inst, 40, rho=RHO, dt=VDT, traj=True)["traj"]
+    wd0 = pinlib.bernstein_d(inst["H"], inst["n_xi"], VDT)[0]
+    for x in tr[1:, 0]:
+        np.testing.assert_allclose(x[..., 0], inst["bnd"][..., 0], atol=1e-12)
+        np.testing.assert_allclose(x[..., -1], inst["bnd"][..., 1], atol=1e-12)
+        np.testing.assert_allclose(x @ wd0, inst["bnd"][..., 2], atol=1e-10)
+
+
+@pytest.mark.parametrize("nd,seed", [(2, 3), (3, 4)])
+def test_velocity_one_sweep_is_block_argmin(nd, seed):
+    inst = pinlib.small_instance(n=3, n_obs=2, H=12, n_d=nd, n_xi=6, seed=seed)
+    inst = sfgen.with_initial_velocity(inst, seed)
+    rng = np.random.default_rng(seed)
+    xib = inst["xi"] + rng.normal(0, 0.2, size=inst["xi"].shape)
+    lam = rng.normal(0, 0.1, size=inst["xi"].shape)
+    got = oracle.solve(inst, 1, rho=RHO, xi0=xib, lam0=lam, dt=VDT)
+    ref_x, ref_l = pinlib.one_step_reference(inst, xib, lam, RHO, dt=VDT)
+    np.testing.assert_allclose(got["lam"], ref_l, atol=1e-8)
+    np.testing.assert_allclose(got["xi"], ref_x, atol=1e-8)
+
+
+def test_velocity_single_robot_affine_projection():
+    """1 robot, no obstacles, inside the box: the textbook affine projection onto the three
+    boundary rows, xi_bar = xi - A'(AA')^-1 (A xi - b)."""
+    nxi, H = 9, 30
+    rng = np.random.default_rng(6)
+    xi = np.cumsum(rng.normal(0, 0.3, size=(2, 1, nxi)), axis=-1)
+    bnd = np.stack([xi[:, :, 0] + 0.4, xi[:, :, -1] - 0.3, np.array([[0.7], [-0.4]])], axis=-1)
+    inst = dict(n=1, n_obs=0, H=H, n_d=2, n_xi=nxi, dyn_obs=False, a=0.5, b=0.5,
+                pmin=np.full(2, -10.0), pmax=np.full(2, 10.0), obs_c=np.zeros((0, 2)),
+                obs_ab=np.zeros((0, 2)), bnd=bnd, xi=xi)
+    _, _, _, A = pinlib.dense_mats(1, 0, H, nxi, n_bc=3, dt=VDT)
+    ref = np.empty_like(xi)
+    for ax in range(2):
+        x = xi[ax].ravel()
+        ref[ax] = (x - A.T @ np.linalg.solve(A @ A.T, A @ x - bnd[ax].ravel())).reshape(1, nxi)
+    got = oracle.solve(inst, 400, rho=RHO, dt=VDT)["xi"]
+    np.testing.assert_allclose(got, ref, atol=1e-10)
+
+
+def _torch_unroll(inst, iters, xi0, lam0, n_bc=2):
+    import torch
+    W, F, G, A = pinlib.dense_mats(inst["n"], inst["n_obs"], inst["H"], inst["n_xi"], n_bc=n_bc, dt=VDT)
+    T, rsq = pinlib.torch_T(inst, RHO, W, F, G, A)
+    xi_c = torch.tensor(inst["xi"], requires_grad=True)
+    x0 = torch.tensor(xi0, requires_grad=True)
+    l0 = torch.tensor(lam0, requires_grad=True)
+    zs = [(x0, l0)]
+    for _ in range(iters):
+        zs.append(T(zs[-1][0], zs[-1][1], xi_c))
+    return xi_c, x0, l0, zs, rsq
+
+
+def test_velocity_backward_matches_torch_autograd():
+    import torch
+    iters = 5
+    base = pinlib.small_instance(n=3, n_obs=2, H=10, n_d=2, n_xi=6, seed=21)
+    inst = sfgen.with_initial_velocity(base, 21)
+    rng = np.random.default_rng(3)
+    g_out = rng.normal(size=inst["xi"].shape)
+    xi0 = inst["xi"] + rng.normal(0, 0.05, size=inst["xi"].shape)
+    lam0 = rng.normal(0, 0.1, size=inst["xi"].shape)
+    xi_c, x0, l0, zs, rsq = _torch_unroll(inst, iters, xi0, lam0, n_bc=3)
+    loss = (zs[-1][0] * torch.tensor(g_out)).sum() + 0.4 * rsq(zs[-1][0])
+    loss.backward()
+    gx, gx0, gl0 = oracle.solve_backward(inst, iters, g_out, None, 0.4, rho=RHO, xi0=xi0, lam0=lam0, dt=VDT)
+    for got, ref in [(gx, xi_c.grad), (gx0, x0.grad), (gl0, l0.grad)]:
+        ref = ref.numpy()
+        np.testing.assert_allclose(got, ref, atol=1e-10 * max(1.0, np.abs(ref).max()))
+
+
+# ------------------------------------------- self-supervised loss (eq. NN_loss, Fig. unroll)
+@pytest.mark.parametrize("nd", [2, 3])
+def test_fixed_point_loss_gradient_matches_torch_autograd(nd):
+    """The loss of eq. NN_loss, sum_{l<L} ||z^{l+1} - z^l||^2 + ||xi_bar^L - xi||^2 (the
+    fixed-point residual read as the step of z = (xi_bar, lambda)), differentiated by
+    torch autograd through the unrolled restatement, against the reverse pass with
+    g_fp = 1 and g_xi_out = 2 (xi_bar^L - xi) (the candidate's own share of the last term
+    added by the caller)."""
+    import torch
+    iters = 6
+    inst = _grad_instance(nd, 70 + nd, iters)
+    rng = np.random.default_rng(9)
+    xi0 = inst["xi"] + rng.normal(0, 0.05, size=inst["xi"].shape)
+    lam0 = rng.normal(0, 0.1, size=inst["xi"].shape)
+    xi_c, x0, l0, zs, _ = _torch_unroll(inst, iters, xi0, lam0)
+    loss = sum(((zs[l + 1][0] - zs[l][0]) ** 2).sum() + ((zs[l + 1][1] - zs[l][1]) ** 2).sum()
+               for l in range(iters))
+    loss = loss + ((zs[-1][0] - xi_c) ** 2).sum()
+    loss.backward()
+    xL = oracle.solve(inst, iters, rho=RHO, xi0=xi0, lam0=lam0)["xi"]
+    gx, gx0, gl0 = oracle.solve_backward(inst, iters, 2 * (xL - inst["xi"]), None, 0.0, rho=RHO, xi0=xi0,
+                                         lam0=lam0, g_fp=1.0)
+    gx = gx - 2 * (xL - inst["xi"])
+    for got, ref in [(gx, xi_c.grad), (gx0, x0.grad), (gl0, l0.grad)]:
+        ref = ref.numpy()
+        np.testing.assert_allclose(got, ref, atol=1e-10 * max(1.0, np.abs(ref).max()))
+
+
+def test_fixed_point_loss_central_differences():
+    """Dot-product test of the fixed-point term alone: <grad, v> against central
+    differences (eps = 1e-6) of sum_l ||z^{l+1} - z^l||^2 along lambda^0 and xi_bar^0."""
+    iters = 7
+    inst = _grad_instance(2, 90, iters)
+    rng = np.random.default_rng(4)
+
+    def loss(xi0, lam0):
+        tr = oracle.solve(inst, iters, rho=RHO, xi0=xi0, lam0=lam0, traj=True)["traj"]
+        return float(np.sum(np.diff(tr, axis=0) ** 2))
+
+    xi0 = inst["xi"].copy()
+    lam0 = np.zeros_like(xi0)
+    _, gx0, gl0 = oracle.solve_backward(inst, iters, None, None, 0.0, rho=RHO, xi0=xi0, lam0=lam0, g_fp=1.0)
+    eps = 1e-6
+    for _ in range(2):
+        v = rng.normal(size=xi0.shape)
+        lhs = (loss(xi0 + eps * v, lam0) - loss(xi0 - eps * v, lam0)) / (2 * eps)
+        assert abs(lhs - float(np.sum(v * gx0))) <= 1e-6 * max(1.0, abs(lhs))
+        lhs = (loss(xi0, lam0 + eps * v) - loss(xi0, lam0 - eps * v)) / (2 * eps)
+        assert abs(lhs - float(np.sum(v * gl0))) <= 1e-6 * max(1.0, abs(lhs))
