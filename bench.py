@@ -35,6 +35,8 @@ import numpy as np  # noqa: E402
 
 import sfgen  # noqa: E402
 
+SF_NRES = 5   # columns of sf_solve's residual output (include/sf.h)
+
 RHO = 0.3
 SM_COUNT_B300 = 148
 FP32_LANES_PER_SM = 128
@@ -309,7 +311,7 @@ class Step:
         self.s, self.data, self.iters, self.fo, self.stream = solver, data, iters, forward_only, stream
         x = data["xi"]
         self.xo, self.lo = torch.empty_like(x), torch.empty_like(x)
-        self.res = torch.empty((solver.B, 4), dtype=torch.float64, device=x.device)
+        self.res = torch.empty((solver.B, SF_NRES), dtype=torch.float64, device=x.device)
         g = np.random.default_rng(7).normal(size=x.numel()) * 1e-2
         self.gxo = torch.as_tensor(g, dtype=x.dtype, device=x.device)
         self.grp2 = torch.ones(solver.B, dtype=torch.float64, device=x.device)

@@ -144,7 +144,9 @@ enum {
                            max over rows of ||r_1 row|| (penetration) and of r_2 entries   */
     SF_RES_FP = 2,      /* ||z^L - z^(L-1)||_2, last fixed-point step (eq. fixed_point_residual) */
     SF_RES_ITERS = 3,   /* first l whose iterate met max residual <= tol, or -1            */
-    SF_NRES = 4
+    SF_RES_FPSUM = 4,   /* sum over the iterations of ||z^{l+1} - z^l||_2^2, z = (xi_bar, lambda):
+                           the fixed-point term of the self-supervised loss (eq. NN_loss)    */
+    SF_NRES = 5
 };
 
 /*
@@ -195,14 +197,20 @@ int sf_solve(sf_handle *h, const sf_instance_data *data, const void *xi_cand, co
  * hand-written adjoint that recomputes each checkpoint segment.
  *  g_xi_out, g_lam_out  seeds dL/dxi_bar^L, dL/dlambda^L (either may be NULL = 0)
  *  g_rp2                device double [n_inst] or NULL: dL/d||r_p(xi_bar^L)||^2
+ *  g_fp                 device double [n_inst] or NULL: dL/dS with S = sum over the
+ *                       iterations l = 0..L-1 of ||z^{l+1} - z^l||^2, z = (xi_bar, lambda)
+ *                       (resid_out[SF_RES_FPSUM] of the solve): the fixed-point term of the
+ *                       self-supervised loss that trains an initialisation network through
+ *                       the solver (eq. NN_loss, Sec. IV-B); its second term
+ *                       ||xi_bar^L - xi||^2 is an ordinary g_xi_out seed
  *  g_xi_cand            out: dL/dxi_cand (through eta in every iteration; when that
  *                       solve had xi0 = NULL, also through xi_bar^0 = xi_cand)
  *  g_xi0, g_lam0        out: dL/dxi_bar^0, dL/dlambda^0 (either may be NULL)
  * Errors: SF_ESTATE (no preceding solve with checkpoints), SF_EINVAL, SF_ECUDA.
  */
 int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void *g_lam_out,
-                      const double *g_rp2, void *g_xi_cand, void *g_xi0, void *g_lam0,
-                      void *stream);
+                      const double *g_rp2, const double *g_fp, void *g_xi_cand, void *g_xi0,
+                      void *g_lam0, void *stream);
 
 /*
  * sf_get_status — copy the per-instance device status words (SF_OK, SF_ENONFINITE,

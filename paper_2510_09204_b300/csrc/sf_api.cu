@@ -283,13 +283,19 @@ static void destroy_all(sf_handle *h)
     for (DevBuf *b : bufs) b->release();
 }
 
-// Sizes the adjoint's segment scratch (a segment of recomputed iterates per cluster CTA)
-// for the current plan, so that sf_solve_backward never allocates and can be captured
-// in a CUDA graph.  Only grows.
+// Bytes of the adjoint's segment scratch: per cluster CTA, a segment of recomputed
+// iterates and their multipliers.
+static size_t seg_bytes_of(const sf_handle *h)
+{
+    return (size_t)h->xi_total * h->plan.csize * h->d.ckpt_every * 2 * h->esz;
+}
+
+// Sizes the adjoint's segment scratch for the current plan, so that sf_solve_backward
+// never allocates and can be captured in a CUDA graph.  Only grows.
 static int ensure_seg(sf_handle *h)
 {
     if (h->d.ckpt_every <= 0) return SF_OK;
-    const size_t need = (size_t)h->xi_total * h->plan.csize * h->d.ckpt_every * h->esz;
+    const size_t need = seg_bytes_of(h);
     if (h->seg.bytes >= need) return SF_OK;
     SF_TRY(cudaDeviceSynchronize());
     h->seg.release();
@@ -619,6 +625,7 @@ static int solve_t(sf_handle *h, const sf_instance_data *data, const void *xc, c
         r.obs = a.obs;
         r.oab = a.oab;
         r.resid = resid;
+        r.stride = SF_NRES;
         r.its = its;
         r.iters = iters;
         r.status = a.status;
@@ -661,15 +668,14 @@ extern "C" int sf_solve(sf_handle *h, const sf_instance_data *data, const void *
 }
 
 extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void *g_lam_out, const double *g_rp2,
-                                 void *g_xi_cand, void *g_xi0, void *g_lam0, void *stream)
+                                 const double *g_fp, void *g_xi_cand, void *g_xi0, void *g_lam0, void *stream)
 {
     NvtxRange nv("sf_solve_backward");
     if (!h || !g_xi_cand) return SF_EINVAL;
     if (!h->last.valid) return SF_ESTATE;
     if (!h->plan.smem_bwd) return SF_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t seg_bytes = (size_t)h->xi_total * h->plan.csize * h->d.ckpt_every * h->esz;
-    if (h->seg.bytes < seg_bytes) return SF_ESTATE;   // sized whenever the plan changes
+    if (h->seg.bytes < seg_bytes_of(h)) return SF_ESTATE;   // sized whenever the plan changes
     const bool prof = h->profile && !capturing(st);
     const SolveRecord &R = h->last;
     int rc;
@@ -681,6 +687,7 @@ extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void 
         b.gxo = (const T *)g_xi_out;
         b.glo = (const T *)g_lam_out;
         b.grp2 = g_rp2;
+        b.gfp = g_fp;
         b.gxc = (T *)g_xi_cand;
         b.gx0 = (T *)g_xi0;
         b.gl0 = (T *)g_lam0;
@@ -770,7 +777,7 @@ extern "C" int sf_autotune(sf_handle *h, const sf_instance_data *data, const voi
                 cudaEventRecord(e0, st);
                 ok = sf_solve(h, data, xi_cand, nullptr, nullptr, iters, xo.p, lo.p, nullptr, nullptr, st) == SF_OK;
                 if (ok && bwd)
-                    ok = sf_solve_backward(h, gxo.p, nullptr, nullptr, gxc.p, nullptr, nullptr, st) == SF_OK;
+                    ok = sf_solve_backward(h, gxo.p, nullptr, nullptr, nullptr, gxc.p, nullptr, nullptr, st) == SF_OK;
                 cudaEventRecord(e1, st);
                 if (ok && cudaEventSynchronize(e1) == cudaSuccess && q > 0) {
                     float ms = 0.f;
@@ -840,6 +847,7 @@ extern "C" int sf_metrics(sf_handle *h, const sf_instance_data *data, const void
         r.obs = (const T *)data->obs_c;
         r.oab = (const T *)data->obs_ab;
         r.resid = out;
+        r.stride = 4;   // sf_metrics' [n_inst][4] output
         r.status = (int32_t *)h->status_dev.p;
         r.smem_doubles = (int64_t)(h->plan.smem_res / sizeof(double));
         r.csize = h->plan.csize;

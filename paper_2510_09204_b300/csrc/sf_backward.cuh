@@ -21,6 +21,12 @@
 // with J = dr_1/dDelta = (1 - s) I + s^3 Delta (M^-2 Delta)' on active rows and 0 on
 // inactive ones (derivative conventions of the kinks: the clamped branch counts as
 // active, Delta = 0 has zero derivative).
+//
+// The self-supervised loss of eq. NN_loss adds w sum_l ||z^{l+1} - z^l||^2 (z = (xi_bar,
+// lambda), w = gfp per instance): reverse step l adds 2 w (z^{l+1} - z^l) to the adjoint
+// of z^{l+1} before the step and subtracts it from the adjoint of z^l after it, so each
+// step needs only its own pair of iterates (z^{l+1} carried in xq, lq from the step
+// before; lambda of the recomputed iterates kept beside them in the segment scratch).
 #pragma once
 #include "sf_iter.cuh"
 
@@ -56,6 +62,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *xs = sm + cv.xs, *ls = sm + cv.ls, *cs = sm + cv.cs, *xn = sm + cv.xn;
     T *xz = sm + cv.xz;   // xs with the end coefficients cleared: the next reverse step's x*
+    T *xq = sm + cv.xq, *lq = sm + cv.lq;   // z^{l+1} of the reverse step (fixed-point seed)
     VP *Rs = reinterpret_cast<VP *>(sm + cv.Rs);
     const int tid = X.tid, nt = X.nt, NN = X.NN, nxi = X.nxi, N = X.N, n = X.n;
     const int64_t off = X.I.off_xi;
@@ -66,8 +73,12 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
         cs[e] = T(0);
     }
     const int Lit = A.iters, ce = A.ck_every;
-    T *seg = B.seg + (off * C + (int64_t)cr * NN) * ce;   // this CTA's copy of a segment's iterates
+    T *seg = B.seg + (off * C + (int64_t)cr * NN) * ce * 2;   // this CTA's copy of a segment's iterates
+    T *segl = seg + (int64_t)ce * NN;                          // and of their multipliers
     int step = 0;                                         // parity of the all-reduce buffer
+    const T wfp = B.gfp ? T(B.gfp[ii]) : T(0);            // weight of the fixed-point loss
+    const bool fps = wfp != T(0);                         // block-uniform
+    const bool need_l = ce > 1 || fps;                    // lambda of each iterate is read
 
     // seed from dL/d||r_p(xi_bar^L)||^2: gradient w r_1-weighted rows (w = 2 dL/d||r_p||^2)
     const T wseed = B.grp2 ? T(2.0 * B.grp2[ii]) : T(0);
@@ -97,6 +108,10 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     for (int e = tid; e < NN; e += nt) {
         const int c = e - (e / nxi) * nxi;
         xz[e] = (c == 0 || c == nxi - 1) ? T(0) : xs[e];
+        if (fps) {
+            xq[e] = A.ck_x[(int64_t)A.ck_final * A.ck_slot + off + e];
+            lq[e] = A.ck_l[(int64_t)A.ck_final * A.ck_slot + off + e];
+        }
     }
 
     const int S = ce > 0 ? (Lit + ce - 1) / ce : 0;
@@ -105,7 +120,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     constexpr int kPF = 4;
     T pfx[kPF], pfl[kPF];
     auto fetch = [&](int sg) {
-        const bool wl = ce > 1;
+        const bool wl = need_l;
 #pragma unroll
         for (int q = 0; q < kPF; ++q) {
             const int e = tid + q * nt;
@@ -124,12 +139,12 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             const int e = tid + q * nt;
             if (e < NN) {
                 X.xb[e] = pfx[q];
-                if (ce > 1) X.lam[e] = pfl[q];
+                if (need_l) X.lam[e] = pfl[q];
             }
         }
         for (int e = tid + kPF * nt; e < NN; e += nt) {
             X.xb[e] = A.ck_x[(int64_t)sg * A.ck_slot + off + e];
-            if (ce > 1) X.lam[e] = A.ck_l[(int64_t)sg * A.ck_slot + off + e];
+            if (need_l) X.lam[e] = A.ck_l[(int64_t)sg * A.ck_slot + off + e];
         }
         if (sg > 0) fetch(sg - 1);
         if (sg == 0) X.boundary_gap();   // b - A xi_bar^0 for the first step's P_b term
@@ -138,7 +153,10 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
         // x^(l1-1) stays in xb, the earlier ones go to the segment scratch; with a checkpoint
         // every iteration nothing is recomputed)
         for (int l = l0; l + 1 < l1; ++l) {
-            for (int e = tid; e < NN; e += nt) seg[(int64_t)(l - l0) * NN + e] = X.xb[e];
+            for (int e = tid; e < NN; e += nt) {
+                seg[(int64_t)(l - l0) * NN + e] = X.xb[e];
+                if (fps) segl[(int64_t)(l - l0) * NN + e] = X.lam[e];
+            }
             T *gme = X.gp + (step & 1) * X.gstride;
             ++step;
             T rp2 = T(0), mx2 = T(0);
@@ -146,10 +164,21 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             cl.sync();
             X.update(cl, gme, X.need_b && l == 0);
         }
+        if (fps)   // lambda of the segment's last iterate (the reverse step uses X.lam as scratch)
+            for (int e = tid; e < NN; e += nt) segl[(int64_t)(l1 - 1 - l0) * NN + e] = X.lam[e];
         // reverse through the segment
         for (int l = l1 - 1; l >= l0; --l) {
             const T *xl = l + 1 == l1 ? X.xb : seg + (int64_t)(l - l0) * NN;
+            const T *ll = segl + (int64_t)(l - l0) * NN;   // lambda^l (fixed-point seed only)
             T *vs = X.dd, *gs = X.lam;
+            if (fps)   // the fixed-point term's share of z^{l+1}: + 2 w (z^{l+1} - z^l)
+                for (int e = tid; e < NN; e += nt) {
+                    const int c = e - (e / nxi) * nxi;
+                    const T x = xs[e] + T(2) * wfp * (xq[e] - xl[e]);
+                    xs[e] = x;
+                    xz[e] = (c == 0 || c == nxi - 1) ? T(0) : x;
+                    ls[e] += T(2) * wfp * (lq[e] - ll[e]);
+                }
             __syncthreads();   // xz of the previous step's gather (or the seed) complete
             X.project(cl, xz, vs, false);
             if (X.smooth) __syncthreads();   // the cost block mixes a row's coefficients
@@ -194,7 +223,13 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             for (int e = tid; e < NN; e += nt) {
                 T s = T(0);
                 for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, q)[e];
-                const T x = xn[e] + s;
+                T x = xn[e] + s;
+                if (fps) {   // and its share of z^l: - 2 w (z^{l+1} - z^l); z^l becomes the next z^{l+1}
+                    x -= T(2) * wfp * (xq[e] - xl[e]);
+                    ls[e] -= T(2) * wfp * (lq[e] - ll[e]);
+                    xq[e] = xl[e];
+                    lq[e] = ll[e];
+                }
                 const int c = e - (e / nxi) * nxi;
                 xs[e] = x;
                 xz[e] = (c == 0 || c == nxi - 1) ? T(0) : x;

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
 
     int its_tol = -1;
     T fp = T(0), fp_prev = T(0);
+    double fp_sum = 0.0;   // sum over the iterations of ||z^{l+1} - z^l||^2
     bool bad = false;
     for (int it = 0; it <= A.iters; ++it) {
         const bool last = it == A.iters;   // the final pass only reduces the last fixed-point step
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
             if ((tid & 31) == 0) {
                 if (it > 0) {
                     fp_prev = s_fp;
+                    fp_sum += (double)s_fp;
                     if (!isfinite(fp_prev)) bad = true;
                 }
                 if (!last) {
@@ -123,6 +125,7 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
             if (A.resid) {
                 A.resid[(int64_t)ii * SF_NRES + SF_RES_FP] = sqrt((double)fp_prev);
                 A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS] = (double)its_tol;
+                A.resid[(int64_t)ii * SF_NRES + SF_RES_FPSUM] = fp_sum;
             }
             if (A.its) A.its[ii] = its_tol;
             if (bad) A.status[ii] = SF_ENONFINITE;

@@ -136,7 +136,7 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int wrows, in
 // (dL/dxi_bar, dL/dlambda, dL/dxi_cand) and R* in the vector layout of the positions.
 struct BwdCarve {
     FwdCarve f;
-    int64_t xs, ls, cs, xn, xz, Rs, total;
+    int64_t xs, ls, cs, xn, xz, xq, lq, Rs, total;
 };
 
 __host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int wrows, int n, int nobs, int hc, int p_rows, int esz,
@@ -151,6 +151,8 @@ __host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int wrows, i
     b.cs = o; o += carve_round(NN, esz);
     b.xn = o; o += carve_round(NN, esz);
     b.xz = o; o += carve_round(NN, esz);
+    b.xq = o; o += carve_round(NN, esz);   // z^{l+1} of the reverse step (fixed-point loss seed)
+    b.lq = o; o += carve_round(NN, esz);
     b.Rs = o; o += carve_round((npad + 4) * hc * ndp, esz);
     b.total = o;
     return b;
@@ -194,8 +196,9 @@ struct BwdArgs {
     FwdArgs<T> f;               // instance data, operators, checkpoints, iteration count
     const T *gxo, *glo;         // seeds dL/dxi_bar^L, dL/dlambda^L (nullable)
     const double *grp2;         // dL/d||r_p(xi_bar^L)||^2 per instance (nullable)
+    const double *gfp;          // dL/d(sum_l ||z^{l+1} - z^l||^2) per instance (nullable)
     T *gxc, *gx0, *gl0;         // dL/dxi_cand, dL/dxi_bar^0, dL/dlambda^0 (gx0, gl0 nullable)
-    T *seg;                     // recomputed iterates of a segment, per instance and CTA
+    T *seg;                     // recomputed iterates (xi_bar, then lambda) of a segment, per instance and CTA
     int x0_null;                // the solve started from xi_bar^0 = xi_cand
 };
 
@@ -208,7 +211,8 @@ struct ResArgs {
     const double *W;            // the FP64 basis, whatever the solve precision
     const T *x;                 // coefficients to evaluate (packed xi)
     const T *obs, *oab;
-    double *resid;              // [n_inst][SF_NRES]
+    double *resid;              // [n_inst][stride]
+    int stride;                 // doubles per instance in resid (SF_NRES; 4 for sf_metrics)
     int32_t *its;
     int iters;                  // iteration count of the solve (its fix-up)
     int32_t *status;

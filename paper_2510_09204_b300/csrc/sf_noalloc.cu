@@ -251,6 +251,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
         r.obs = obs_c;
         r.oab = obs_ab;
         r.resid = resid_out;
+        r.stride = SF_NRES;
         r.iters = iters;
         r.status = S->status;
         r.smem_doubles = (int64_t)(plan.smem_res / sizeof(double));

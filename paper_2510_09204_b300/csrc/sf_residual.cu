@@ -132,11 +132,11 @@ __global__ void __launch_bounds__(512) k_residual(ResArgs<T> A)
             s_mx2 = fmax(s_mx2, rr[97]);
         }
         const double mx = sqrt(s_mx2);
-        A.resid[(int64_t)ii * SF_NRES + SF_RES_RP] = sqrt(s_rp2);
-        A.resid[(int64_t)ii * SF_NRES + SF_RES_MAX] = mx;
-        const double itv = A.its_fixup ? A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS] : 0.0;
+        A.resid[(int64_t)ii * A.stride + SF_RES_RP] = sqrt(s_rp2);
+        A.resid[(int64_t)ii * A.stride + SF_RES_MAX] = mx;
+        const double itv = A.its_fixup ? A.resid[(int64_t)ii * A.stride + SF_RES_ITERS] : 0.0;
         if (itv < 0.0 && mx <= A.tol) {
-            A.resid[(int64_t)ii * SF_NRES + SF_RES_ITERS] = (double)A.iters;
+            A.resid[(int64_t)ii * A.stride + SF_RES_ITERS] = (double)A.iters;
             if (A.its) A.its[ii] = A.iters;
         }
         if (!isfinite(s_rp2)) A.status[ii] = SF_ENONFINITE;

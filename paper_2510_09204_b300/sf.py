@@ -20,7 +20,7 @@ SF_NOALLOC_MAX_INST, SF_NOALLOC_MAX_H = 256, 1024
 SF_FP64, SF_FP32, SF_TF32, SF_BF16X3, SF_BF16 = range(5)
 SF_PROJ_DENSE, SF_PROJ_STRUCTURED = 0, 1
 SF_LAYOUT_XI, SF_LAYOUT_BND, SF_LAYOUT_OBS, SF_LAYOUT_OBS_AB = range(4)
-SF_RES_RP, SF_RES_MAX, SF_RES_FP, SF_RES_ITERS, SF_NRES = range(5)
+SF_RES_RP, SF_RES_MAX, SF_RES_FP, SF_RES_ITERS, SF_RES_FPSUM, SF_NRES = range(6)
 
 PRECISIONS = {"fp64": SF_FP64, "fp32": SF_FP32, "tf32": SF_TF32, "bf16x3": SF_BF16X3, "bf16": SF_BF16}
 PROJECTIONS = {"dense": SF_PROJ_DENSE, "structured": SF_PROJ_STRUCTURED}
@@ -73,7 +73,7 @@ def lib(path: str | None = None):
         L.sf_destroy.argtypes = [vp]
         L.sf_layout.argtypes = [vp, i32, i64p]
         L.sf_solve.argtypes = [vp, ct.POINTER(sf_instance_data), vp, vp, vp, i32, vp, vp, vp, vp, vp]
-        L.sf_solve_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.sf_solve_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.sf_get_status.argtypes = [vp, ct.POINTER(ct.c_int32)]
         L.sf_shape_operator.argtypes = [vp, i32, i32, ct.POINTER(ct.c_double)]
         L.sf_profile.argtypes = [vp, i32]
@@ -202,9 +202,12 @@ class SFSolver:
         self._keep = (data, xi_cand, xi0, lam0)
         return xi_out, lam_out, (resid if want_resid else None)
 
-    def backward(self, g_xi_out, g_lam_out=None, g_rp2=None, want_xi0=True, want_lam0=True, out=None, stream=None):
+    def backward(self, g_xi_out, g_lam_out=None, g_rp2=None, want_xi0=True, want_lam0=True, out=None, stream=None,
+                 g_fp=None):
         """sf_solve_backward: returns (g_xi_cand, g_xi0, g_lam0).  ``out``: optional
-        preallocated (g_xi_cand, g_xi0, g_lam0) tensors (None entries are skipped)."""
+        preallocated (g_xi_cand, g_xi0, g_lam0) tensors (None entries are skipped).
+        g_rp2, g_fp: per-instance float64 weights of ||r_p(xi_out)||^2 and of the fixed-point
+        sum resid[:, SF_RES_FPSUM] (None = 0)."""
         ref = g_xi_out
         if out is not None:
             g_xc, g_x0, g_l0 = out
@@ -212,14 +215,14 @@ class SFSolver:
             g_xc = torch.empty_like(ref)
             g_x0 = torch.empty_like(ref) if want_xi0 else None
             g_l0 = torch.empty_like(ref) if want_lam0 else None
-        _check(lib().sf_solve_backward(self.h, _ptr(g_xi_out), _ptr(g_lam_out), _ptr(g_rp2), _ptr(g_xc),
-                                       _ptr(g_x0), _ptr(g_l0), _stream(stream)), "sf_solve_backward")
+        _check(lib().sf_solve_backward(self.h, _ptr(g_xi_out), _ptr(g_lam_out), _ptr(g_rp2), _ptr(g_fp),
+                                       _ptr(g_xc), _ptr(g_x0), _ptr(g_l0), _stream(stream)), "sf_solve_backward")
         return g_xc, g_x0, g_l0
 
     def metrics(self, data, xi, stream=None):
         """sf_metrics: FP64 [B, 4] device tensor of (||r_p||, max residual in m, smoothness
         cost, path length) per instance of the coefficients ``xi``."""
-        out = torch.empty((self.B, 4), dtype=torch.float64, device=xi.device)
+        out = torch.empty((self.B, 4), dtype=torch.float64, device=xi.device)   # sf_metrics: 4 columns
         dd = self._data(data)
         _check(lib().sf_metrics(self.h, ct.byref(dd), _ptr(xi), _ptr(out), _stream(stream)), "sf_metrics")
         return out
@@ -341,10 +344,12 @@ def select(group_sizes, primary, secondary=None, threshold=float("-inf"), k=1, s
 
 
 class SFSolve(torch.autograd.Function):
-    """(xi_cand, xi0, lam0) -> (xi_out, lam_out, rp2) through ``iters`` SF iterations.
+    """(xi_cand, xi0, lam0) -> (xi_out, lam_out, rp2, fp_sum) through ``iters`` SF iterations.
 
-    rp2 is ||r_p(xi_out)||^2 per instance (FP64), differentiable.  Gradients come from
-    ``sf_solve_backward`` (the handle must have been created with ckpt_every > 0).
+    rp2 is ||r_p(xi_out)||^2 per instance (FP64), fp_sum the sum over the iterations of
+    ||z^{l+1} - z^l||^2 per instance (FP64; the fixed-point term of the self-supervised loss
+    of eq. NN_loss); both differentiable.  Gradients come from ``sf_solve_backward`` (the
+    handle must have been created with ckpt_every > 0).
     """
 
     @staticmethod
@@ -353,13 +358,14 @@ class SFSolve(torch.autograd.Function):
                                    lam0=lam0.contiguous())
         ctx.solver = solver
         rp2 = res[:, SF_RES_RP] ** 2
-        return xo, lo, rp2
+        return xo, lo, rp2, res[:, SF_RES_FPSUM].clone()
 
     @staticmethod
-    def backward(ctx, g_xo, g_lo, g_rp2):
+    def backward(ctx, g_xo, g_lo, g_rp2, g_fp):
         s = ctx.solver
         g_xo = torch.zeros_like(s._keep[1]) if g_xo is None else g_xo.contiguous()
         g_lo = None if g_lo is None else g_lo.contiguous()
         g_rp2 = None if g_rp2 is None else g_rp2.contiguous().to(torch.float64)
-        gx, gx0, gl0 = s.backward(g_xo, g_lo, g_rp2)
+        g_fp = None if g_fp is None else g_fp.contiguous().to(torch.float64)
+        gx, gx0, gl0 = s.backward(g_xo, g_lo, g_rp2, g_fp=g_fp)
         return gx, gx0, gl0, None, None, None

@@ -71,4 +71,4 @@ def test_create_rejects_bad_descriptors_without_touching_the_device():
     h = ct.c_void_p()
     assert L.sf_create(ct.byref(d), ct.byref(h)) == sf.SF_EINVAL
     assert L.sf_solve(None, None, None, None, None, 0, None, None, None, None, None) == sf.SF_EINVAL
-    assert L.sf_solve_backward(None, None, None, None, None, None, None, None) == sf.SF_EINVAL
+    assert L.sf_solve_backward(None, None, None, None, None, None, None, None, None) == sf.SF_EINVAL

@@ -163,7 +163,7 @@ def test_autograd_function_loss_of_config4_form():
     xc = data["xi"].clone().requires_grad_(True)
     x0 = xc.detach().clone().requires_grad_(True)
     l0 = torch.zeros_like(xc, requires_grad=True)
-    xo, lo, rp2 = SFSolve.apply(xc, x0, l0, s, data, iters)
+    xo, lo, rp2, _ = SFSolve.apply(xc, x0, l0, s, data, iters)
     loss = rp2.sum() + 0.1 * ((xo - xc) ** 2).sum()
     loss.backward()
     out = s.unpack(xo.detach(), 0).cpu().numpy()
@@ -173,6 +173,57 @@ def test_autograd_function_loss_of_config4_form():
     assert close(s.unpack(xc.grad, 0).cpu().numpy(), ref_xc, 1e-9)
     assert close(s.unpack(x0.grad, 0).cpu().numpy(), gx0, 1e-9)
     assert close(s.unpack(l0.grad, 0).cpu().numpy(), gl0, 1e-9)
+
+
+@pytest.mark.parametrize("ckpt,proj,nd", [(1, "dense", 2), (4, "structured", 2), (3, "dense", 3)])
+def test_self_supervised_loss_matches_oracle(ckpt, proj, nd):
+    """The loss of eq. NN_loss, sum_l ||z^{l+1} - z^l||^2 + ||xi_bar^L - xi||^2, through
+    SFSolve (its fp_sum output) against the oracle's reverse pass with g_fp = 1, FP64; with
+    checkpoints every iteration and with recomputed segments."""
+    iters = 10
+    inst = kink_free(lambda s: pinlib.small_instance(n=3, n_obs=2, H=12, n_d=nd, n_xi=6, seed=800 + s), iters)
+    rng = np.random.default_rng(ckpt)
+    xi0 = inst["xi"] + rng.normal(0, 0.05, size=inst["xi"].shape)
+    lam0 = rng.normal(0, 0.1, size=inst["xi"].shape)
+    s = SFSolver([inst], nd, inst["n_xi"], rho=RHO, precision="fp64", proj=proj, max_iters=iters, ckpt_every=ckpt)
+    data = s.pack([inst])
+    xc = data["xi"].clone().requires_grad_(True)
+    x0 = pack_list(s, [xi0]).requires_grad_(True)
+    l0 = pack_list(s, [lam0]).requires_grad_(True)
+    xo, lo, rp2, fps = SFSolve.apply(xc, x0, l0, s, data, iters)
+    loss = fps.sum() + ((xo - xc) ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    assert (s.status() == 0).all()
+    tr = oracle.solve(inst, iters, rho=RHO, xi0=xi0, lam0=lam0, traj=True)["traj"]
+    assert abs(float(fps[0]) - np.sum(np.diff(tr, axis=0) ** 2)) <= 1e-10 * np.sum(np.diff(tr, axis=0) ** 2)
+    xL = tr[-1, 0]
+    gx, gx0, gl0 = oracle.solve_backward(inst, iters, 2 * (xL - inst["xi"]), None, 0.0, rho=RHO, xi0=xi0,
+                                         lam0=lam0, g_fp=1.0)
+    assert close(s.unpack(xc.grad, 0).cpu().numpy(), gx - 2 * (xL - inst["xi"]), 1e-9)
+    assert close(s.unpack(x0.grad, 0).cpu().numpy(), gx0, 1e-9)
+    assert close(s.unpack(l0.grad, 0).cpu().numpy(), gl0, 1e-9)
+
+
+def test_self_supervised_loss_fp32_batch_against_fp64():
+    """The fixed-point seed on a 32-robot batch in FP32 against the same seed in FP64 (the
+    FP64 path is pinned to the oracle above): per instance within 1e-3 relative."""
+    insts = sfgen.make_batch(4, B=8)
+    iters = 20
+    out = {}
+    for prec in ("fp64", "fp32"):
+        s = SFSolver(insts, 2, 11, rho=RHO, precision=prec, proj="structured", max_iters=iters, ckpt_every=5)
+        d = s.pack(insts)
+        xo, _, res = s.solve(d, d["xi"], iters)
+        ones = torch.ones(len(insts), dtype=torch.float64, device="cuda")
+        gx, gx0, gl0 = s.backward(torch.zeros_like(xo), None, None, g_fp=ones)
+        torch.cuda.synchronize()
+        assert (s.status() == 0).all()
+        out[prec] = [[s.unpack(t, k).double().cpu().numpy() for k in range(len(insts))] for t in (gx, gx0, gl0)]
+        s.close()
+    for a, b in zip(out["fp32"], out["fp64"]):
+        for k in range(len(insts)):
+            assert rel(a[k], b[k]) <= 1e-3, (k, rel(a[k], b[k]))
 
 
 def test_backward_requires_checkpoints():

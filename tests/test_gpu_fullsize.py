@@ -15,7 +15,7 @@ import torch
 
 import oracle
 import sfgen
-from gpu_util import max_pos_err, rel
+from gpu_util import SENS_DRAWS, SENS_ULPS, check_adjoint_per_instance, max_pos_err, rel, ulp_perturbed
 from paper_2510_09204_b300 import SFSolve, SFSolver
 
 pytestmark = pytest.mark.gpu
@@ -75,6 +75,19 @@ def test_uneven_64_instances_fp32_structured():
     k = int(order[-1])
     rr = oracle.residual(rounded32(insts[k]), xs[k], rho=RHO)
     np.testing.assert_allclose(r[k, :2], rr[:2], rtol=1e-9, atol=1e-12)
+    # the two largest instances (up to 64 robots, 120 timesteps) against the oracle, 40
+    # iterations of the same launch (the oracle takes seconds per iteration there)
+    x40, _, r40 = s.solve(d, d["xi"], 40)
+    torch.cuda.synchronize()
+    for k in (int(order[-1]), int(order[-2])):
+        inst = rounded32(insts[k])
+        ref = oracle.solve(inst, 40, rho=RHO)
+        W = oracle.basis(inst["H"], 11)
+        err = max_pos_err(inst, s.unpack(x40, k).double().cpu().numpy(), ref["xi"], W)
+        print("\nconfig 3 instance %d (n %d, n_obs %d, H %d), 40 iterations: FP32 vs oracle %.2e m"
+              % (k, inst["n"], inst["n_obs"], inst["H"], err))
+        assert err <= 1e-4
+        assert abs(r40[k, 1].item() - oracle.residual(inst, ref["xi"], rho=RHO)[1]) <= 1e-3
 
 
 def test_differentiable_128_instances_fp64_autograd():
@@ -84,7 +97,7 @@ def test_differentiable_128_instances_fp64_autograd():
     xc = d["xi"].clone().requires_grad_(True)
     x0 = xc.detach().clone().requires_grad_(True)
     l0 = torch.zeros_like(xc, requires_grad=True)
-    xo, lo, rp2 = SFSolve.apply(xc, x0, l0, s, d, iters)
+    xo, lo, rp2, _ = SFSolve.apply(xc, x0, l0, s, d, iters)
     loss = rp2.sum() + 0.1 * ((xo - xc) ** 2).sum()
     loss.backward()
     torch.cuda.synchronize()
@@ -102,62 +115,64 @@ def test_differentiable_128_instances_fp64_autograd():
         assert rel(s.unpack(l0.grad, k).cpu().numpy(), gl0) <= 1e-9
 
 
+def adjoint_run(insts, prec, iters, ckpt, seed):
+    s, d = tuned(insts, prec, "structured", iters, ckpt=ckpt)
+    xo, _, res = s.solve(d, d["xi"], iters)
+    g = torch.as_tensor(np.random.default_rng(seed).normal(size=xo.numel()) * 1e-2, dtype=xo.dtype, device="cuda")
+    gx, _, _ = s.backward(g, None, torch.ones(len(insts), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert (s.status() == 0).all()
+    out = (unpack_all(s, xo, len(insts)), res.cpu().numpy(), unpack_all(s, gx, len(insts)))
+    s.close()
+    return out
+
+
 def test_differentiable_128_instances_fp32_against_fp64():
     """The FP32 differentiable step on the whole batch against the FP64 GPU step (itself
     pinned to the oracle above) on the same input as FP32 holds it: outputs within the
-    FP32 tolerance, gradients close in relative norm.  (Some instances here amplify
-    input perturbations by ~300 in 50 iterations even in exact arithmetic: rounding the
-    candidate to float32 alone moves the oracle's answer by up to 8e-5 m, which is why
-    the reference takes the rounded input.)"""
-    insts = sfgen.make_batch(4)
+    FP32 tolerance, gradients per instance within the bound of check_adjoint_per_instance.
+    (Some instances here amplify input perturbations by ~300 in 50 iterations even in
+    exact arithmetic: rounding the candidate to float32 alone moves the oracle's answer by
+    up to 8e-5 m, which is why the reference takes the rounded input.)"""
+    insts = [rounded32(i) for i in sfgen.make_batch(4)]
     iters = sfgen.CONFIGS[4].iters
-    outs = {}
-    for prec in ("fp64", "fp32"):
-        s, d = tuned([rounded32(i) for i in insts], prec, "structured", iters, ckpt=10)
-        xo, _, res = s.solve(d, d["xi"], iters)
-        g = torch.as_tensor(np.random.default_rng(4).normal(size=xo.numel()) * 1e-2, dtype=xo.dtype, device="cuda")
-        gx, _, _ = s.backward(g, None, torch.ones(len(insts), dtype=torch.float64, device="cuda"))
-        torch.cuda.synchronize()
-        assert (s.status() == 0).all()
-        outs[prec] = (unpack_all(s, xo, len(insts)), res.cpu().numpy(), unpack_all(s, gx, len(insts)))
+    outs = {p: adjoint_run(insts, p, iters, 10, 4) for p in ("fp64", "fp32")}
+    outs["fp64p"] = [adjoint_run([ulp_perturbed(i, 100 * s + k, SENS_ULPS) for k, i in enumerate(insts)], "fp64",
+                                 iters, 10, 4)[2] for s in range(SENS_DRAWS)]
     W = oracle.basis(100, 11)
     errs = [max_pos_err(i, a, b, W) for i, a, b in zip(insts, outs["fp32"][0], outs["fp64"][0])]
     print("\nconfig 4 FP32 vs FP64 (rounded input): max position error %.2e m (median %.2e)"
           % (max(errs), np.median(errs)))
     assert max(errs) <= 1e-4
     assert np.abs(outs["fp32"][1][:, 1] - outs["fp64"][1][:, 1]).max() <= 1e-3
-    grel = [rel(a, b) for a, b in zip(outs["fp32"][2], outs["fp64"][2])]
-    assert np.median(grel) <= 1e-3
+    check_adjoint_per_instance(outs["fp32"][2], outs["fp64"][2], outs["fp64p"], what="config 4")
 
 
 def test_benchmark_step_config2():
     """The benchmark's step exactly: all 32 instances of the 16-robot 2-D config, FP32,
     structured projection, autotuned geometry, a checkpoint every iteration, forward,
     FP64 residual check and adjoint of the 200 iterations.  Forward: sampled instances
-    against the oracle on the input as FP32 holds it.  Adjoint: against the FP64 GPU step
-    (pinned to the oracle's reverse pass elsewhere) on the same input."""
+    against the oracle on the input as FP32 holds it.  Adjoint: per instance against the
+    FP64 GPU step (pinned to the oracle's reverse pass elsewhere) on the same input, within
+    the bound of check_adjoint_per_instance."""
     insts = [rounded32(i) for i in sfgen.make_batch(2)]
     iters = sfgen.CONFIGS[2].iters
-    outs = {}
-    for prec in ("fp64", "fp32"):
-        s, d = tuned(insts, prec, "structured", iters, ckpt=1)
-        xo, _, res = s.solve(d, d["xi"], iters)
-        g = torch.as_tensor(np.random.default_rng(2).normal(size=xo.numel()) * 1e-2, dtype=xo.dtype, device="cuda")
-        gx, _, _ = s.backward(g, None, torch.ones(len(insts), dtype=torch.float64, device="cuda"))
-        torch.cuda.synchronize()
-        assert (s.status() == 0).all()
-        if prec == "fp32":
-            boundary_exact(s, xo, insts)
-        outs[prec] = (unpack_all(s, xo, len(insts)), res.cpu().numpy(), unpack_all(s, gx, len(insts)))
-        s.close()
+    outs = {p: adjoint_run(insts, p, iters, 1, 2) for p in ("fp64", "fp32")}
+    outs["fp64p"] = [adjoint_run([ulp_perturbed(i, 100 * s + k, SENS_ULPS) for k, i in enumerate(insts)], "fp64",
+                                 iters, 1, 2)[2] for s in range(SENS_DRAWS)]
+    s = SFSolver(insts, 2, 11, rho=RHO, precision="fp32", proj="structured", max_iters=iters)
+    d = s.pack(insts)
+    xo, _, _ = s.solve(d, d["xi"], iters)
+    torch.cuda.synchronize()
+    boundary_exact(s, xo, insts)
     W = oracle.basis(100, 11)
     for k in (0, 13, 31):
         ref = oracle.solve(insts[k], iters, rho=RHO)
         assert max_pos_err(insts[k], outs["fp32"][0][k], ref["xi"], W) <= 1e-4
         assert abs(outs["fp32"][1][k, 1] - oracle.residual(insts[k], ref["xi"], rho=RHO)[1]) <= 1e-3
-    grel = [rel(a, b) for a, b in zip(outs["fp32"][2], outs["fp64"][2])]
-    print("\nconfig 2 adjoint FP32 vs FP64: relative error median %.2e, max %.2e" % (np.median(grel), max(grel)))
-    assert np.median(grel) <= 1e-3
+    errs = [max_pos_err(i, a, b, W) for i, a, b in zip(insts, outs["fp32"][0], outs["fp64"][0])]
+    assert max(errs) <= 1e-4
+    check_adjoint_per_instance(outs["fp32"][2], outs["fp64"][2], outs["fp64p"], what="config 2")
 
 
 @pytest.mark.parametrize("proj", ["structured", "dense"])
@@ -187,11 +202,14 @@ def test_3d_64_robots_fp32(proj):
     assert np.abs(r32.cpu().numpy()[:, 1] - r64.cpu().numpy()[:, 1]).max() <= 1e-3
 
 
-@pytest.mark.parametrize("precision,n_refine", [("bf16x3", 1), ("tf32", 2), ("bf16", 3)])
-def test_3d_64_robots_tensor_core_error_reported(precision, n_refine):
-    """The mixed-precision configuration: the projection on tensor cores with refinement,
-    its error against FP64 on the whole batch reported; BF16 x3 with one pass and TF32
-    with two are held to the FP32 tolerance."""
+@pytest.mark.parametrize("precision,n_refine", [("bf16x3", 1), ("tf32", 3), ("bf16", 5)])
+def test_3d_64_robots_tensor_core_meets_the_fp32_tolerance(precision, n_refine):
+    """The mixed-precision configuration: the projection on tensor cores with refinement
+    against FP64 on the whole batch, every instance within the reduced-precision
+    tolerance (1e-4 m in position, 1e-3 m in the final residual).  The pass counts are the
+    ones each format needs here: BF16 gains about a factor 5-10 per pass (3 passes leave
+    4e-4 m, 4 leave 5e-5 m, 5 leave 2.5e-5 m), TF32 a factor 3, BF16 x3 is at FP32 accuracy
+    after one."""
     insts = sfgen.make_batch(5)
     iters = sfgen.CONFIGS[5].iters
     W = oracle.basis(100, 11)
@@ -208,5 +226,4 @@ def test_3d_64_robots_tensor_core_error_reported(precision, n_refine):
     rdiff = np.abs(rt.cpu().numpy()[:, 1] - r64.cpu().numpy()[:, 1]).max()
     print("\nconfig 5 %s + %d refinement: max position error %.2e m, residual difference %.2e m"
           % (precision, n_refine, max(errs), rdiff))
-    if precision != "bf16":
-        assert max(errs) <= 1e-4 and rdiff <= 1e-3
+    assert max(errs) <= 1e-4 and rdiff <= 1e-3

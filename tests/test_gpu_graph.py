@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import sfgen
-from paper_2510_09204_b300 import SFSolver
+from paper_2510_09204_b300 import SF_NRES, SFSolver
 
 pytestmark = pytest.mark.gpu
 RHO = 0.3
@@ -27,7 +27,7 @@ class Step:
         self.s, self.data = s, data
         x = data["xi"]
         self.xo, self.lo = torch.empty_like(x), torch.empty_like(x)
-        self.res = torch.empty((s.B, 4), dtype=torch.float64, device=x.device)
+        self.res = torch.empty((s.B, SF_NRES), dtype=torch.float64, device=x.device)
         g = np.random.default_rng(3).normal(size=x.numel()) * 1e-2
         self.gxo = torch.as_tensor(g, dtype=x.dtype, device=x.device)
         self.grp2 = torch.ones(s.B, dtype=torch.float64, device=x.device)

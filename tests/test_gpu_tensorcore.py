@@ -70,12 +70,12 @@ def test_tensor_core_3d_and_uneven(precision):
         assert rel(got["xi"][k] - xi0[k], ref["xi"][k] - xi0[k]) <= bound
 
 
-@pytest.mark.parametrize("precision,n_refine", [("tf32", 0), ("bf16", 0), ("bf16x3", 0), ("bf16x3", 1),
-                                                ("tf32", 2)])
+@pytest.mark.parametrize("precision,n_refine", [("bf16x3", 1), ("tf32", 2), ("bf16", 5)])
 def test_tensor_core_run_error_against_the_oracle(precision, n_refine):
-    """200 iterations of config 2 (3 instances): the maximum position error and the final
-    residual difference against the FP64 oracle, reported per precision.  With one
-    refinement pass BF16 x3 meets the FP32 tolerances (1e-4 m, 1e-3 m)."""
+    """200 iterations of config 2 (3 instances) with refinement: the maximum position error
+    and the final residual difference against the FP64 oracle within the reduced-precision
+    tolerances (1e-4 m, 1e-3 m).  Unrefined products are held to their format's one-step
+    bound above; over 200 iterations they drift by 2e-3 to 9e-2 m and carry no tolerance."""
     insts = sfgen.make_batch(2, B=3)
     out = gpu_solve(insts, 200, precision=precision, proj="dense", n_refine=n_refine)
     W = oracle.basis(100, 11)
@@ -86,10 +86,7 @@ def test_tensor_core_run_error_against_the_oracle(precision, n_refine):
         rdiff.append(abs(out["resid"][k, 1] - oracle.residual(inst, ref["xi"])[1]))
     print("\nTCRUN %s refine %d: max position error %.3e m, max final-residual difference %.3e m"
           % (precision, n_refine, max(errs), max(rdiff)))
-    if n_refine >= 1 and precision == "bf16x3":
-        assert max(errs) <= 1e-4 and max(rdiff) <= 1e-3
-    else:
-        assert max(errs) <= 0.5 and max(rdiff) <= 0.05
+    assert max(errs) <= 1e-4 and max(rdiff) <= 1e-3
 
 
 @pytest.mark.parametrize("precision", ["tf32", "bf16x3"])

@@ -54,7 +54,7 @@ def test_noalloc_matches_ordinary_solve_twice(cid, B, iters):
     for call in range(2):
         xo = torch.full_like(data["xi"], float("nan"))
         lo = torch.full_like(data["xi"], float("nan"))
-        res = torch.full((B, 4), float("nan"), dtype=torch.float64, device="cuda")
+        res = torch.full((B, sf.SF_NRES), float("nan"), dtype=torch.float64, device="cuda")
         assert _noalloc(insts, iters, data, xo, lo, res) == sf.SF_OK
         torch.cuda.synchronize()
         for k in range(B):
