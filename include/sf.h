@@ -122,14 +122,22 @@ typedef struct sf_desc {
     const sf_shape *shapes; /* host array [n_inst], copied by sf_create                    */
     void *stream;       /* cudaStream_t on which sf_create runs the factorisations         */
     int32_t cost;       /* SF_COST_PROJECTION (0) or SF_COST_SMOOTHNESS                    */
-    double dt;          /* time step in seconds of the smoothness cost (> 0 when used)     */
+    double dt;          /* time step in seconds of the smoothness cost and of the velocity
+                           rows (> 0 when either is used): t = tau (H - 1) dt               */
+    int32_t n_bc;       /* boundary rows of A per robot and axis (eq. boundary_con): 2 (or 0)
+                           start and goal; 3 adds the initial velocity p'(t = 0) = v_0, the
+                           planner conditioned on the robots' current velocities (Sec. V,
+                           hardware experiments); needs dt > 0 and n_xi >= 5.  For the
+                           Bernstein basis the rows fix coefficients 0, n_xi - 1 and, with
+                           the velocity row, 1 (xi_1 = start + v_0 (H - 1) dt / (n_xi - 1)) */
 } sf_desc;
 
 typedef struct sf_handle sf_handle;
 
 /* ---- instance data (device pointers, element type T) ---------------------- */
 typedef struct sf_instance_data {
-    const void *bnd;    /* [n_d][n][2] start and goal per axis and robot (eq. boundary_con) */
+    const void *bnd;    /* [n_d][n][n_bc] start, goal [, initial velocity in m/s] per axis
+                           and robot (eq. boundary_con)                                     */
     const void *obs_c;  /* obstacle centres, static [n_obs][n_d] or dynamic [n_obs][H][n_d]  */
     const void *obs_ab; /* [n_obs][2] obstacle axes (a_o, b_o), inflated by the robot size  */
 } sf_instance_data;
@@ -224,9 +232,9 @@ int sf_get_status(sf_handle *h, int32_t *per_instance_status);
  * to host memory `host_out`:
  *   which = 0: basis W [H][n_xi]
  *   which = 1: P_eta [N][N]            (N = n * n_xi)
- *   which = 2: P_b [N][2n]             (columns robot-major: start, goal)
+ *   which = 2: P_b [N][n_bc n]         (columns robot-major: start, goal[, velocity])
  *   which = 3: Kronecker blocks P_dev [n_xi][n_xi], P_mean [n_xi][n_xi],
- *              B_dev [n_xi][2], B_mean [n_xi][2], then the per-robot cost block
+ *              B_dev [n_xi][n_bc], B_mean [n_xi][n_bc], then the per-robot cost block
  *              [n_xi][n_xi] (the identity, or Wdd' Wdd of the smoothness cost with Wdd
  *              the basis' second time derivative), back to back
  * Synchronises the device.  Errors: SF_EINVAL, SF_ECUDA.
@@ -338,12 +346,17 @@ int sf_kernel_times(sf_handle *h, float *ms_out);
  * sizes return SF_ETOOBIG before anything is launched.  Other bad arguments return
  * SF_EINVAL; CUDA failures SF_ECUDA.
  * Set-up: the first call on each device looks up the device address of the fixed
- * array (with that device current); make that first call before any stream capture.
- * Sharing: every call, on every stream, uses the same array, which keeps the last
- * call's contents (each call rewrites what it reads and clears its status words),
- * so calls whose work overlaps on the GPU race with each other: serialise them.
- * Per-instance status words are not reported; a non-finite iterate shows as a
- * non-finite entry of resid_out.
+ * array (with that device current, under a mutex); make that first call before any
+ * stream capture.  Every call then hands its sizes to its own set-up kernel by value,
+ * which writes the instance table, basis and operators into the array; no host memory
+ * is read after the call returns.
+ * Sharing: every call on one device, on every stream, uses that device's array, which
+ * keeps the last call's contents (each call rewrites what it reads and clears its status
+ * words), so calls whose work overlaps on one GPU race with each other: serialise them.
+ * Calls on different devices use different copies and are independent.
+ * Per-instance status words are not reported; a non-finite iterate, or a singular
+ * boundary system (then every output is NaN), shows as a non-finite entry of resid_out.
+ * Only the two boundary rows (start, goal) are supported: bnd is [n_d][n][2].
  */
 #define SF_NOALLOC_MAX_INST 256
 #define SF_NOALLOC_MAX_H 1024

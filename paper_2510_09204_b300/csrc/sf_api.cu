@@ -65,6 +65,7 @@ struct sf_handle {
     sf_desc d{};
     std::vector<sf_shape> shp;
     int esz = 8;                       // sizeof(T)
+    int nbc = 2;                       // boundary rows per robot and axis (3 with the initial velocity)
     int n_shapes = 0;
     std::vector<int> inst_shape;
     std::vector<Shape> shapes_h;
@@ -101,7 +102,7 @@ static std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;
 
 static std::vector<int64_t> tune_key(const sf_desc &d, const std::vector<sf_shape> &shp)
 {
-    std::vector<int64_t> k = {d.n_d, d.n_xi, d.precision, d.proj, d.n_inst, d.ckpt_every > 0};
+    std::vector<int64_t> k = {d.n_d, d.n_xi, d.precision, d.proj, d.n_inst, d.ckpt_every > 0, d.n_bc == 3};
     for (const sf_shape &s : shp) {
         k.push_back(s.n);
         k.push_back(s.n_obs);
@@ -220,6 +221,8 @@ static int validate(const sf_desc *d)
     if (d->max_iters < 0 || d->ckpt_every < 0 || d->n_refine < 0 || d->n_refine > 8 || !(d->tol >= 0.0)) return SF_EINVAL;
     if (d->cost != SF_COST_PROJECTION && d->cost != SF_COST_SMOOTHNESS) return SF_EINVAL;
     if (d->cost == SF_COST_SMOOTHNESS && (!(d->dt > 0.0) || !isfinite(d->dt) || d->n_xi < 3)) return SF_EINVAL;
+    if (d->n_bc != 0 && d->n_bc != 2 && d->n_bc != 3) return SF_EINVAL;
+    if (d->n_bc == 3 && (!(d->dt > 0.0) || !isfinite(d->dt) || d->n_xi < 5)) return SF_EINVAL;
     for (int i = 0; i < d->n_inst; ++i) {
         const sf_shape &s = d->shapes[i];
         if (s.n < 1 || s.n > 256 || s.n_obs < 0 || s.n_obs > 4096 || s.H < 2 || s.H > 4096) return SF_EINVAL;
@@ -357,6 +360,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
     h->shp.assign(desc->shapes, desc->shapes + desc->n_inst);
     h->d.shapes = nullptr;
     h->esz = desc->precision == SF_FP64 ? 8 : 4;
+    h->nbc = desc->n_bc == 3 ? 3 : 2;
     h->tc_mode = desc->proj == SF_PROJ_DENSE ? tc_mode_of(desc->precision) : 0;
     const int nd = desc->n_d, nxi = desc->n_xi, B = desc->n_inst;
     cudaStream_t st = (cudaStream_t)desc->stream;
@@ -371,7 +375,7 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
     for (int i = 0; i < B; ++i) {
         const sf_shape &s = h->shp[i];
         h->off[SF_LAYOUT_XI][i + 1] = h->off[SF_LAYOUT_XI][i] + (int64_t)nd * s.n * nxi;
-        h->off[SF_LAYOUT_BND][i + 1] = h->off[SF_LAYOUT_BND][i] + (int64_t)nd * s.n * 2;
+        h->off[SF_LAYOUT_BND][i + 1] = h->off[SF_LAYOUT_BND][i] + (int64_t)nd * s.n * h->nbc;
         h->off[SF_LAYOUT_OBS][i + 1] = h->off[SF_LAYOUT_OBS][i] + (int64_t)s.n_obs * (s.dyn_obs ? s.H : 1) * nd;
         h->off[SF_LAYOUT_OBS_AB][i + 1] = h->off[SF_LAYOUT_OBS_AB][i] + (int64_t)s.n_obs * 2;
     }
@@ -391,14 +395,17 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
             S.n_obs = s.n_obs;
             S.H = s.H;
             S.N = s.n * nxi;
+            S.nbc = h->nbc;
+            S.pad_ = 0;
+            S.vsc = h->nbc == 3 ? (double)(nxi - 1) / ((double)(s.H - 1) * desc->dt) : 0.0;
             S.off_W = oW;
             S.off_P = oP;
             S.off_Pb = oPb;
             S.off_S = oS;
             oW += (int64_t)s.H * nxi;
             oP += (int64_t)S.N * S.N;
-            oPb += (int64_t)S.N * 2 * s.n;
-            oS += 3 * (int64_t)nxi * nxi + 4 * (int64_t)nxi;   // Kronecker blocks + cost block
+            oPb += (int64_t)S.N * h->nbc * s.n;
+            oS += kron_len(nxi, h->nbc);   // Kronecker blocks + cost block
             it = key.emplace(k, (int)h->shapes_h.size()).first;
             h->shapes_h.push_back(S);
         }
@@ -939,8 +946,8 @@ extern "C" int sf_shape_operator(const sf_handle *h, int32_t inst, int32_t which
     switch (which) {
     case 0: src = (const double *)h->W64.p + S.off_W; cnt = (size_t)S.H * nxi; break;
     case 1: src = (const double *)h->P64.p + S.off_P; cnt = (size_t)S.N * S.N; break;
-    case 2: src = (const double *)h->Pb64.p + S.off_Pb; cnt = (size_t)S.N * 2 * S.n; break;
-    default: src = (const double *)h->S64.p + S.off_S; cnt = 3 * (size_t)nxi * nxi + 4 * (size_t)nxi; break;
+    case 2: src = (const double *)h->Pb64.p + S.off_Pb; cnt = (size_t)S.N * S.nbc * S.n; break;
+    default: src = (const double *)h->S64.p + S.off_S; cnt = (size_t)kron_len(nxi, S.nbc); break;
     }
     SF_TRY(cudaDeviceSynchronize());
     SF_TRY(cudaMemcpy(host_out, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost));

@@ -11,13 +11,13 @@
 // P_b (b - A xi_bar) with v = xi - xi_bar + lambda - 2 rho g (projection cost; the
 // smoothness cost has -Q1 xi_bar per robot in place of xi - xi_bar) and lambda' =
 // lambda - rho g, g = W'R(p), p = W xi_bar, from (xi_bar'*, lambda'*):
-//   x*  = xi_bar'* with its end coefficients cleared (they are overwritten by b)
+//   x*  = xi_bar'* with the coefficients A fixes cleared (they are overwritten by b)
 //   v*  = P_eta x*                        (P_eta symmetric)
 //   xi*      += v* (projection only),   lambda* = lambda'* + v*,   g* = -rho lambda'* - 2 rho v*
 //   R*  = W g*;  p* = sum over active rows of J' (R*_i - R*_j) (pairs; J even, r_1 odd),
 //                J' R*_i (obstacles), mask R*_i (box)
 //   xi_bar*  = x* - v* (- Q1 v* per robot, smoothness) + W' p*
-//              [- A' P_b' x* at l = 0, the end coefficients of xi_bar^0]
+//              [- A' P_b' x* at l = 0: xi_bar^0 enters through b - A xi_bar^0]
 // with J = dr_1/dDelta = (1 - s) I + s^3 Delta (M^-2 Delta)' on active rows and 0 on
 // inactive ones (derivative conventions of the kinks: the clamped branch counts as
 // active, Delta = 0 has zero derivative).
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     }
     for (int e = tid; e < NN; e += nt) {
         const int c = e - (e / nxi) * nxi;
-        xz[e] = (c == 0 || c == nxi - 1) ? T(0) : xs[e];
+        xz[e] = X.fixed_c(c) ? T(0) : xs[e];
         if (fps) {
             xq[e] = A.ck_x[(int64_t)A.ck_final * A.ck_slot + off + e];
             lq[e] = A.ck_l[(int64_t)A.ck_final * A.ck_slot + off + e];
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
                     const int c = e - (e / nxi) * nxi;
                     const T x = xs[e] + T(2) * wfp * (xq[e] - xl[e]);
                     xs[e] = x;
-                    xz[e] = (c == 0 || c == nxi - 1) ? T(0) : x;
+                    xz[e] = X.fixed_c(c) ? T(0) : x;
                     ls[e] += T(2) * wfp * (lq[e] - ll[e]);
                 }
             __syncthreads();   // xz of the previous step's gather (or the seed) complete
@@ -196,13 +196,26 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
                 }
                 ls[e] += vst;
             }
-            if (l == 0) {   // - A' P_b' x*: the end coefficients of xi_bar^0
+            if (l == 0) {   // - A' P_b' x*: xi_bar^0 enters through b - A xi_bar^0
+                const int nbc = X.nbc, m = nbc * n;
+                T *t = X.v;   // P_b' x* per (axis, robot, boundary row); v is free in the reverse sweep
                 __syncthreads();
-                for (int q2 = tid; q2 < ND * 2 * n; q2 += nt) {
-                    const int ax = q2 / (2 * n), q = q2 - ax * 2 * n;
+                for (int q2 = tid; q2 < ND * m; q2 += nt) {
+                    const int ax = q2 / m, q = q2 - ax * m;
                     T s = T(0);
-                    for (int r = 0; r < N; ++r) s += X.Pbg[(int64_t)r * 2 * n + q] * xz[ax * N + r];
-                    xn[(ax * n + (q >> 1)) * nxi + ((q & 1) ? nxi - 1 : 0)] -= s;
+                    for (int r = 0; r < N; ++r) s += X.Pbg[(int64_t)r * m + q] * xz[ax * N + r];
+                    t[q2] = s;
+                }
+                __syncthreads();
+                for (int r = tid; r < ND * n; r += nt) {   // A' row by row: e_0, e_{n_xi - 1}, vsc (e_1 - e_0)
+                    const T *tr = t + (int64_t)r * nbc;
+                    T *x = xn + (int64_t)r * nxi;
+                    x[0] -= tr[0];
+                    x[nxi - 1] -= tr[1];
+                    if (nbc == 3) {
+                        x[1] -= X.vsc * tr[2];
+                        x[0] += X.vsc * tr[2];
+                    }
                 }
             }
             T *gme = X.gp + (step & 1) * X.gstride;
@@ -232,7 +245,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
                 }
                 const int c = e - (e / nxi) * nxi;
                 xs[e] = x;
-                xz[e] = (c == 0 || c == nxi - 1) ? T(0) : x;
+                xz[e] = X.fixed_c(c) ? T(0) : x;
             }
         }
     }

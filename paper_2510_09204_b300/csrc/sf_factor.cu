@@ -15,6 +15,7 @@
 #include <math.h>
 
 #include "sf_internal.cuh"
+#include "sf_kron.cuh"
 #include "sf_tc.cuh"
 
 #include <algorithm>
@@ -43,7 +44,7 @@ __global__ void k_basis(const Shape *sh, int nxi, double *W)
 __global__ void k_cost_block(const Shape *sh, int nxi, int cost, double dt, double *Sx)
 {
     const Shape S = sh[blockIdx.x];
-    double *Cb = Sx + S.off_S + 2 * nxi * nxi + 4 * nxi;
+    double *Cb = Sx + S.off_S + kron_cost_off(nxi, S.nbc);
     const int deg = nxi - 1, H = S.H;
     const double T = (double)(H - 1) * dt, scale = (double)deg * (double)(deg - 1) / (T * T);
     for (int e = threadIdx.x; e < nxi * nxi; e += blockDim.x) {
@@ -78,7 +79,7 @@ __global__ void k_build_H(const Shape *sh, int nxi, double rho, const double *W,
     const int N = S.N;
     double *Hm = Hs + S.off_P;
     const double *Ws = W + S.off_W;
-    const double *Cb = Sx + S.off_S + 2 * nxi * nxi + 4 * nxi;   // per-robot cost block
+    const double *Cb = Sx + S.off_S + kron_cost_off(nxi, S.nbc);   // per-robot cost block
     const double cdiag = (double)(S.n + S.n_obs + 2);
     const int64_t tot = (int64_t)N * N;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
@@ -155,19 +156,14 @@ __global__ void k_chol_inverse(const Shape *sh, const double *Ls_pool, double *X
     }
 }
 
-// A selects, per robot i, the basis rows k = 0 (start) and k = H-1 (goal): row q = 2i + s.
-__device__ __forceinline__ double arow(const double *Ws, int nxi, int H, int s, int c)
-{
-    return Ws[(s ? H - 1 : 0) * nxi + c];
-}
-
-// Per shape (one CTA): Y = Hinv A', S = A Y, Cholesky of S, Sinv, P_b = Y Sinv.
-// Y goes to Ypool (N x 2n), S / Sinv to Spool ((2n)^2 each, within the N^2 slot).
+// Per shape (one CTA): Y = Hinv A', S = A Y, Cholesky of S, Sinv, P_b = Y Sinv, with A's
+// row q = nbc i + s the boundary row s of robot i (a0_row).
+// Y goes to Ypool (N x nbc n), S / Sinv to Spool ((nbc n)^2 each, within the N^2 slot).
 __global__ void k_schur(const Shape *sh, int nxi, const double *W, const double *Hinv, double *Ypool,
                         double *Spool, double *Pb, int *info)
 {
     const Shape S = sh[blockIdx.x];
-    const int N = S.N, n = S.n, m = 2 * n, tid = threadIdx.x, nt = blockDim.x;
+    const int N = S.N, n = S.n, nbc = S.nbc, m = nbc * n, tid = threadIdx.x, nt = blockDim.x;
     const double *Ws = W + S.off_W;
     const double *Hi = Hinv + S.off_P;
     double *Y = Ypool + S.off_P;
@@ -175,16 +171,16 @@ __global__ void k_schur(const Shape *sh, int nxi, const double *W, const double 
     double *Si = Sm + (int64_t)m * m;
     double *B = Pb + S.off_Pb;
     for (int64_t e = tid; e < (int64_t)N * m; e += nt) {
-        const int r = (int)(e / m), q = (int)(e % m), i = q / 2, s = q % 2;
+        const int r = (int)(e / m), q = (int)(e % m), i = q / nbc, s = q % nbc;
         double acc = 0.0;
-        for (int c = 0; c < nxi; ++c) acc += Hi[(int64_t)r * N + i * nxi + c] * arow(Ws, nxi, S.H, s, c);
+        for (int c = 0; c < nxi; ++c) acc += Hi[(int64_t)r * N + i * nxi + c] * a0_row(Ws, nxi, S.H, s, c, S.vsc);
         Y[e] = acc;
     }
     __syncthreads();
     for (int e = tid; e < m * m; e += nt) {
-        const int q = e / m, q2 = e % m, i = q / 2, s = q % 2;
+        const int q = e / m, q2 = e % m, i = q / nbc, s = q % nbc;
         double acc = 0.0;
-        for (int c = 0; c < nxi; ++c) acc += arow(Ws, nxi, S.H, s, c) * Y[(int64_t)(i * nxi + c) * m + q2];
+        for (int c = 0; c < nxi; ++c) acc += a0_row(Ws, nxi, S.H, s, c, S.vsc) * Y[(int64_t)(i * nxi + c) * m + q2];
         Sm[e] = acc;
     }
     // Cholesky of S (m <= 2 * 64 * ... small), then Sinv column by column
@@ -238,7 +234,7 @@ __global__ void k_schur(const Shape *sh, int nxi, const double *W, const double 
 __global__ void k_peta(const Shape *sh, const double *Ypool, const double *Pb, double *P)
 {
     const Shape S = sh[blockIdx.y];
-    const int N = S.N, m = 2 * S.n;
+    const int N = S.N, m = S.nbc * S.n;
     const double *Y = Ypool + S.off_P;
     const double *B = Pb + S.off_Pb;
     double *Pe = P + S.off_P;
@@ -253,11 +249,11 @@ __global__ void k_peta(const Shape *sh, const double *Ypool, const double *Pb, d
 
 // Kronecker blocks of the dense operators: P_eta = (I - Q) (x) P_dev + Q (x) P_mean with
 // Q = 11'/n, read off robot blocks (0,0) and (0,1); the same for P_b with B_dev, B_mean.
-// Layout per shape at off_S: P_dev [nxi][nxi], P_mean [nxi][nxi], B_dev [nxi][2], B_mean [nxi][2].
+// Layout per shape at off_S: P_dev [nxi][nxi], P_mean [nxi][nxi], B_dev [nxi][nbc], B_mean [nxi][nbc].
 __global__ void k_structured(const Shape *sh, int nxi, const double *P, const double *Pb, double *Sx)
 {
     const Shape S = sh[blockIdx.x];
-    const int N = S.N, n = S.n, m = 2 * n;
+    const int N = S.N, n = S.n, nbc = S.nbc, m = nbc * n;
     const double *Pe = P + S.off_P;
     const double *B = Pb + S.off_Pb;
     double *o = Sx + S.off_S;
@@ -268,111 +264,33 @@ __global__ void k_structured(const Shape *sh, int nxi, const double *P, const do
         o[e] = n > 1 ? d0 - d1 : d0;
         o[nxi * nxi + e] = d0 + (n - 1) * d1;
     }
-    for (int e = threadIdx.x; e < nxi * 2; e += blockDim.x) {
-        const int u = e / 2, s = e % 2;
+    for (int e = threadIdx.x; e < nxi * nbc; e += blockDim.x) {
+        const int u = e / nbc, s = e % nbc;
         const double d0 = B[(int64_t)u * m + s];
-        const double d1 = n > 1 ? B[(int64_t)u * m + 2 + s] : 0.0;
+        const double d1 = n > 1 ? B[(int64_t)u * m + nbc + s] : 0.0;
         o[2 * nxi * nxi + e] = n > 1 ? d0 - d1 : d0;
-        o[2 * nxi * nxi + 2 * nxi + e] = d0 + (n - 1) * d1;
+        o[2 * nxi * nxi + nbc * nxi + e] = d0 + (n - 1) * d1;
     }
 }
 
 // The Kronecker blocks directly, without the dense factorisation (handles that project in
-// the structured form).  The Hessian I_n (x) C + rho ((n + n_obs + 2) I - 11') (x) W'W has
-// eigenvalue n + n_obs + 2 of its robot factor on the deviation from the robot mean and
-// n_obs + 2 on the mean, and A = I_n (x) A0 commutes with that split, so P_dev / P_mean and
-// B_dev / B_mean are the (x, x) and (x, b) blocks of the inverse of
-// [[C + rho c W'W, A0'], [A0, 0]] (A0: rows 0 and H - 1 of W) for the two values of c.
-// One CTA per shape; Gauss-Jordan elimination with partial pivoting; info = 0 or pivot + 1.
-constexpr int kKronMax = 32 + 2;
+// the structured form): kron_kkt_blocks per shape, one CTA each; info = 0 or pivot + 1.
 __global__ void k_kron_blocks(const Shape *sh, int nxi, double rho, const double *W, double *Sx, int *info)
 {
+    __shared__ KronSmem sm;
     const Shape S = sh[blockIdx.x];
-    const double *Ws = W + S.off_W;
-    const double *Cb = Sx + S.off_S + 2 * nxi * nxi + 4 * nxi;   // per-robot cost block
-    double *o = Sx + S.off_S;
-    const int tid = threadIdx.x, nt = blockDim.x, m = nxi + 2, H = S.H;
-    __shared__ double wtw[32 * 32];
-    __shared__ double K[kKronMax * kKronMax], X[kKronMax * kKronMax];
-    __shared__ int piv, bad;
-    if (tid == 0) bad = 0;
-    for (int e = tid; e < nxi * nxi; e += nt) {
-        const int u = e / nxi, v = e % nxi;
-        double acc = 0.0;
-        for (int k = 0; k < H; ++k) acc += Ws[k * nxi + u] * Ws[k * nxi + v];
-        wtw[e] = acc;
-    }
-    for (int pass = 0; pass < 2; ++pass) {
-        const double c = pass == 0 ? (double)(S.n + S.n_obs + 2) : (double)(S.n_obs + 2);
-        __syncthreads();
-        for (int e = tid; e < m * m; e += nt) {
-            const int r = e / m, q = e % m;
-            double val;
-            if (r < nxi && q < nxi) val = Cb[r * nxi + q] + rho * c * wtw[r * nxi + q];
-            else if (r < nxi) val = Ws[(q == nxi ? 0 : H - 1) * nxi + r];
-            else if (q < nxi) val = Ws[(r == nxi ? 0 : H - 1) * nxi + q];
-            else val = 0.0;
-            K[e] = val;
-            X[e] = r == q ? 1.0 : 0.0;
-        }
-        for (int p = 0; p < m; ++p) {
-            __syncthreads();
-            if (tid == 0) {
-                int best = p;
-                for (int r = p + 1; r < m; ++r)
-                    if (fabs(K[r * m + p]) > fabs(K[best * m + p])) best = r;
-                piv = best;
-                if (!(fabs(K[best * m + p]) > 0.0) && !bad) bad = p + 1;
-            }
-            __syncthreads();
-            if (bad) break;
-            const int b = piv;
-            if (b != p)
-                for (int q = tid; q < m; q += nt) {
-                    double t = K[p * m + q]; K[p * m + q] = K[b * m + q]; K[b * m + q] = t;
-                    t = X[p * m + q]; X[p * m + q] = X[b * m + q]; X[b * m + q] = t;
-                }
-            __syncthreads();
-            const double d = K[p * m + p];
-            __syncthreads();
-            for (int q = tid; q < m; q += nt) {
-                K[p * m + q] /= d;
-                X[p * m + q] /= d;
-            }
-            __syncthreads();
-            // eliminate column p from the other rows; column p itself is read by every
-            // update, so it is cleared only after a barrier
-            for (int e = tid; e < m * m; e += nt) {
-                const int r = e / m, q = e % m;
-                if (r == p || q == p) continue;
-                K[r * m + q] -= K[r * m + p] * K[p * m + q];
-            }
-            for (int e = tid; e < m * m; e += nt) {
-                const int r = e / m, q = e % m;
-                if (r == p) continue;
-                X[r * m + q] -= K[r * m + p] * X[p * m + q];
-            }
-            __syncthreads();
-            for (int r = tid; r < m; r += nt)
-                if (r != p) K[r * m + p] = 0.0;
-        }
-        __syncthreads();
-        if (bad) break;
-        double *Po = o + pass * nxi * nxi, *Bo = o + 2 * nxi * nxi + pass * 2 * nxi;
-        for (int e = tid; e < nxi * nxi; e += nt) Po[e] = X[(e / nxi) * m + e % nxi];
-        for (int e = tid; e < nxi * 2; e += nt) Bo[e] = X[(e / 2) * m + nxi + e % 2];
-    }
-    __syncthreads();
-    if (tid == 0 && bad) info[blockIdx.x] = bad;
+    const int bad = kron_kkt_blocks(S, nxi, rho, W + S.off_W, Sx + S.off_S + kron_cost_off(nxi, S.nbc), Sx + S.off_S, sm);
+    if (threadIdx.x == 0 && bad) info[blockIdx.x] = bad;
 }
 
 // Dense P_eta = (I - Q) (x) P_dev + Q (x) P_mean and P_b likewise (columns robot-major
-// (start, goal)), from the blocks: for the operator queries and the adjoint's P_b term.
+// (start, goal[, velocity])), from the blocks: for the operator queries and the adjoint's
+// P_b term.
 __global__ void k_kron_assemble(const Shape *sh, int nxi, const double *Sx, double *P, double *Pb)
 {
     const Shape S = sh[blockIdx.y];
-    const int N = S.N, n = S.n, m2 = 2 * n;
-    const double *Pd = Sx + S.off_S, *Pm = Pd + nxi * nxi, *Bd = Pd + 2 * nxi * nxi, *Bm = Bd + 2 * nxi;
+    const int N = S.N, n = S.n, nbc = S.nbc, m2 = nbc * n;
+    const double *Pd = Sx + S.off_S, *Pm = Pd + nxi * nxi, *Bd = Pd + 2 * nxi * nxi, *Bm = Bd + nbc * nxi;
     const double inv_n = 1.0 / (double)n;
     const int64_t totP = (int64_t)N * N, totB = (int64_t)N * m2;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < totP + totB; e += (int64_t)gridDim.x * blockDim.x) {
@@ -382,9 +300,9 @@ __global__ void k_kron_assemble(const Shape *sh, int nxi, const double *Sx, doub
             P[S.off_P + e] = (i == j ? dv : 0.0) + (Pm[u * nxi + v] - dv) * inv_n;
         } else {
             const int64_t f = e - totP;
-            const int r = (int)(f / m2), q = (int)(f % m2), i = r / nxi, u = r % nxi, j = q >> 1, sd = q & 1;
-            const double dv = Bd[u * 2 + sd];
-            Pb[S.off_Pb + f] = (i == j ? dv : 0.0) + (Bm[u * 2 + sd] - dv) * inv_n;
+            const int r = (int)(f / m2), q = (int)(f % m2), i = r / nxi, u = r % nxi, j = q / nbc, sd = q % nbc;
+            const double dv = Bd[u * nbc + sd];
+            Pb[S.off_Pb + f] = (i == j ? dv : 0.0) + (Bm[u * nbc + sd] - dv) * inv_n;
         }
     }
 }
@@ -469,7 +387,7 @@ cudaError_t factor_shapes(const Shape *shapes_dev, int n_shapes, const Shape *sh
         int64_t most = 0;
         for (int i = 0; i < n_shapes; ++i) {
             maxN = std::max(maxN, shapes_host[i].N);
-            most = std::max<int64_t>(most, (int64_t)shapes_host[i].N * (shapes_host[i].N + 2 * shapes_host[i].n));
+            most = std::max<int64_t>(most, (int64_t)shapes_host[i].N * (shapes_host[i].N + shapes_host[i].nbc * shapes_host[i].n));
         }
         k_basis<<<n_shapes, 256, 0, s>>>(shapes_dev, nxi, W64);
         k_cost_block<<<n_shapes, 128, 0, s>>>(shapes_dev, nxi, cost, dt, S64);

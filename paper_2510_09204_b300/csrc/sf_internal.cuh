@@ -31,11 +31,28 @@ struct Inst {
 // One distinct (n, n_obs, H) shape: basis and xi_bar-step operators.
 struct Shape {
     int n, n_obs, H, N;
+    int nbc;          // boundary rows per robot and axis: 2 (start, goal) or 3 (+ initial velocity)
+    int pad_;
+    double vsc;       // scale of the velocity row: p'(0) = vsc (xi_1 - xi_0), vsc = (n_xi - 1) / ((H - 1) dt)
     int64_t off_W;    // H x n_xi
     int64_t off_P;    // N x N, P_eta (symmetric)
-    int64_t off_Pb;   // N x 2n, P_b (columns: robot-major (start, goal))
-    int64_t off_S;    // structured form: P_dev, P_mean, B_dev, B_mean (n_xi x n_xi, n_xi x 2 each)
+    int64_t off_Pb;   // N x nbc n, P_b (columns: robot-major (start, goal[, velocity]))
+    int64_t off_S;    // structured form: P_dev, P_mean (n_xi x n_xi), B_dev, B_mean (n_xi x nbc), cost block
 };
+
+// Layout of a shape's Kronecker record: P_dev, P_mean, B_dev, B_mean, then the per-robot
+// cost block (n_xi x n_xi).
+__host__ __device__ inline int64_t kron_cost_off(int nxi, int nbc) { return 2 * (int64_t)nxi * nxi + 2 * (int64_t)nbc * nxi; }
+__host__ __device__ inline int64_t kron_len(int nxi, int nbc) { return kron_cost_off(nxi, nbc) + (int64_t)nxi * nxi; }
+
+// Boundary row s of one robot (eq. boundary_con) at coefficient c: the basis at tau = 0
+// (start, s = 0) and tau = 1 (goal, s = 1), and the initial velocity p'(0) (s = 2), which
+// for the Bernstein basis is vsc (xi_1 - xi_0).
+__host__ __device__ inline double a0_row(const double *Ws, int nxi, int H, int s, int c, double vsc)
+{
+    if (s == 2) return c == 1 ? vsc : c == 0 ? -vsc : 0.0;
+    return Ws[(s ? H - 1 : 0) * nxi + c];
+}
 
 // ---- tensor-core projection (dense P_eta on tcgen05) -----------------------------
 // Modes: 0 none (SIMT), 1 TF32, 2 BF16, 3 BF16 x3 (hi*hi + hi*lo + lo*hi).
@@ -72,7 +89,7 @@ __host__ __device__ inline int64_t tc_smem_bytes(int mode, int N, int stages)
 // Shared-memory carve of the forward kernel, in elements of T.  Every region starts on a
 // 32-byte boundary.  Host and kernel both call forward_carve, so they cannot disagree.
 struct FwdCarve {
-    int64_t W, xb, lam, xc, v, gp, dl, dd, rr, wtw, pb, Rb, ob, bd, db, sx, red, Ps, bb, os, lp, lo, lc, total;
+    int64_t W, xb, lam, xc, v, gp, dl, dd, rr, wtw, pb, Rb, ob, bd, db, bf, sx, red, Ps, bb, os, lp, lo, lc, total;
 };
 
 // Candidate lists of the culled row loops: per robot, the partners and obstacles whose
@@ -114,9 +131,10 @@ __host__ __device__ inline FwdCarve forward_carve(int nd, int nxi, int wrows, in
     c.pb = o;  o += carve_round((npad + 4) * hc * ndp, esz);      // positions [i][k] as vectors (+ far dummies)
     c.Rb = o;  o += carve_round((int64_t)nd * n * hc, esz);       // row sums R [ax][i][k]
     c.ob = o;  o += carve_round((opad + 4) * 8, esz);             // obstacle records (+ dummies)
-    c.bd = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b
-    c.db = o;  o += carve_round((int64_t)nd * n * 2, esz);        // b - A xi_bar^0
-    c.sx = o;  o += carve_round(3 * (int64_t)nxi * nxi + 4 * nxi + 2 * (int64_t)nd * nxi + 2 * nd, esz);
+    c.bd = o;  o += carve_round((int64_t)nd * n * 3, esz);        // b (up to three rows per robot and axis)
+    c.db = o;  o += carve_round((int64_t)nd * n * 3, esz);        // b - A xi_bar^0
+    c.bf = o;  o += carve_round((int64_t)nd * n * 3, esz);        // values of the coefficients A fixes
+    c.sx = o;  o += carve_round(3 * (int64_t)nxi * nxi + 6 * nxi + 2 * (int64_t)nd * nxi + 3 * nd, esz);
     c.red = o; o += carve_round(4 * 32, esz);
     c.Ps = o;  o += carve_round((int64_t)p_rows * N, esz);
     // culling, per segment of at most 32 timesteps: boxes [ax][lo, hi][segment][robot |

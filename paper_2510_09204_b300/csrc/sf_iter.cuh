@@ -153,8 +153,10 @@ struct Cta {
     T rho, invn;
     Inst<T> I;
     Shape S;
-    T *W, *xb, *lam, *xc, *v, *gp, *dl, *dd, *rr, *wtw, *Rb, *ob, *bd, *db, *sx, *red, *Ps;
+    T *W, *xb, *lam, *xc, *v, *gp, *dl, *dd, *rr, *wtw, *Rb, *ob, *bd, *db, *bf, *sx, *red, *Ps;
     int n_refine, n_obs_;
+    int nbc;          // boundary rows per robot and axis (2, or 3 with the initial velocity)
+    T vsc;            // velocity row p'(0) = vsc (xi_1 - xi_0)
     VP *P;
     const T *Prow, *Pbg, *obs_g;
     int64_t gstride;
@@ -235,14 +237,16 @@ struct Cta {
         oob = 0;
         esc = false;
         cdel = T(0.5) * fmax(I.a, I.b);
-        bd = sm + cv.bd; db = sm + cv.db; sx = sm + cv.sx; red = sm + cv.red; Ps = sm + cv.Ps;
+        bd = sm + cv.bd; db = sm + cv.db; bf = sm + cv.bf; sx = sm + cv.sx; red = sm + cv.red; Ps = sm + cv.Ps;
+        nbc = S.nbc;
+        vsc = T(S.vsc);
         P = reinterpret_cast<VP *>(sm + cv.pb);
         gstride = carve_round(NN + 4 + 3 * 32, (int)sizeof(T));
         Pbg = A.Pb + S.off_Pb;
         obs_g = A.obs + I.off_obs;
-        Pdev = sx; Pdif = sx + nxi * nxi; Bdev = sx + 2 * nxi * nxi; Bdif = Bdev + 2 * nxi;
-        mv = Bdif + 2 * nxi; pm = mv + ND * nxi; mb = pm + ND * nxi;
-        Qc = mb + 2 * ND;
+        Pdev = sx; Pdif = sx + nxi * nxi; Bdev = sx + 2 * nxi * nxi; Bdif = Bdev + nbc * nxi;
+        mv = Bdif + nbc * nxi; pm = mv + ND * nxi; mb = pm + ND * nxi;
+        Qc = mb + 3 * ND;
         smooth = MODE == 3 ? 1 : MODE ? 0 : A.cost == SF_COST_SMOOTHNESS;
         Prow = nullptr;
         need_b = 0;
@@ -329,6 +333,10 @@ struct Cta {
     }
 
 
+    // Coefficient c of a robot is fixed by A (eq. boundary_con): the first and last (start
+    // and goal of the Bernstein basis) and, with the velocity row, the second.
+    __device__ __forceinline__ bool fixed_c(int c) const { return c == 0 || c == nxi - 1 || (nbc == 3 && c == 1); }
+
     // Basis, candidate, boundary values, obstacle records and projection operators.
     __device__ __forceinline__ void load_constants(const FwdArgs<T> &A, int p_rows)
     {
@@ -336,7 +344,15 @@ struct Cta {
         for (int e = k_lo * nxi + tid; e < k_hi * nxi; e += nt) W[e] = Wg[e];
         const T *xcg = A.xc + I.off_xi;
         for (int e = tid; e < NN; e += nt) xc[e] = xcg[e];
-        for (int e = tid; e < ND * n * 2; e += nt) bd[e] = A.bnd[I.off_bnd + e];
+        for (int e = tid; e < ND * n * nbc; e += nt) bd[e] = A.bnd[I.off_bnd + e];
+        // the values A xi = b fixes, per (axis, robot) r: coefficient 0 (start), 1 (start +
+        // v_0 / vsc, with the velocity row) and n_xi - 1 (goal)
+        for (int r = tid; r < ND * n; r += nt) {
+            const T *b = A.bnd + I.off_bnd + (int64_t)r * nbc;
+            bf[3 * r] = b[0];
+            bf[3 * r + 1] = nbc == 3 ? b[0] + b[2] / vsc : T(0);
+            bf[3 * r + 2] = b[1];
+        }
         for (int m = nobs + tid; m < opad + 4; m += nt) {   // padding records: far away, zero radius
             T *o = ob + 8 * m;
             for (int q = 0; q < 8; ++q) o[q] = T(0);
@@ -363,7 +379,7 @@ struct Cta {
             for (int e = tid; e < (r_hi - r_lo) * N; e += nt) Ps[e] = Pg[(int64_t)r_lo * N + e];
         Prow = (dense && p_rows > 0) ? Ps - (int64_t)r_lo * N : Pg;   // Prow[r * N + c], r in [r_lo, r_hi)
         if (smooth) {
-            const T *Cg = A.Sx + S.off_S + 2 * nxi * nxi + 4 * nxi;
+            const T *Cg = A.Sx + S.off_S + kron_cost_off(nxi, nbc);
             for (int e = tid; e < nxi * nxi; e += nt) Qc[e] = Cg[e];
         }
         if (!dense) {
@@ -372,9 +388,9 @@ struct Cta {
                 Pdev[e] = Sg[e];
                 Pdif[e] = Sg[nxi * nxi + e] - Sg[e];
             }
-            for (int e = tid; e < 2 * nxi; e += nt) {
+            for (int e = tid; e < nbc * nxi; e += nt) {
                 Bdev[e] = Sg[2 * nxi * nxi + e];
-                Bdif[e] = Sg[2 * nxi * nxi + 2 * nxi + e] - Sg[2 * nxi * nxi + e];
+                Bdif[e] = Sg[2 * nxi * nxi + nbc * nxi + e] - Sg[2 * nxi * nxi + e];
             }
         }
     }
@@ -385,17 +401,19 @@ struct Cta {
     {
         __syncthreads();
         int nb = 0;
-        for (int e = tid; e < ND * n * 2; e += nt) {
-            const int r = e >> 1, s = e & 1;
-            db[e] = bd[e] - xb[r * nxi + (s ? nxi - 1 : 0)];
+        for (int e = tid; e < ND * n * nbc; e += nt) {
+            const int r = e / nbc, s = e - r * nbc;
+            const T *x = xb + r * nxi;
+            const T ax = s == 0 ? x[0] : s == 1 ? x[nxi - 1] : vsc * (x[1] - x[0]);
+            db[e] = bd[e] - ax;
             if (db[e] != T(0)) nb = 1;
         }
         need_b = __syncthreads_or(nb);
         if (need_b && !dense)
-            for (int e = tid; e < ND * 2; e += nt) {
-                const int ax = e >> 1, s = e & 1;
+            for (int e = tid; e < ND * nbc; e += nt) {
+                const int ax = e / nbc, s = e - ax * nbc;
                 T acc = T(0);
-                for (int i = 0; i < n; ++i) acc += db[(ax * n + i) * 2 + s];
+                for (int i = 0; i < n; ++i) acc += db[(ax * n + i) * nbc + s];
                 mb[e] = acc * invn;
             }
         __syncthreads();
@@ -1065,8 +1083,8 @@ struct Cta {
                         for (int ax = 0; ax < ND; ++ax) {
                             T a = (T)dv[ax];
                             if (corr_b)
-                                for (int q = 0; q < 2 * n; ++q)
-                                    a += Pbg[(int64_t)row * 2 * n + q] * db[(ax * n + (q >> 1)) * 2 + (q & 1)];
+                                for (int q = 0; q < nbc * n; ++q)
+                                    a += Pbg[(int64_t)row * nbc * n + q] * db[ax * n * nbc + q];
                             dl[ax * N + row] = a;
                         }
                     }
@@ -1119,7 +1137,7 @@ struct Cta {
                         if (smooth) cd += Qc[u * nxi + c] * dst[r * nxi + c];
                     }
                     const T res = src[e] - (cd + rho * hv);
-                    rr[e] = (u == 0 || u == nxi - 1) ? T(0) : res;
+                    rr[e] = fixed_c(u) ? T(0) : res;
                 }
                 __syncthreads();
                 tc_rows(rr, false);
@@ -1148,10 +1166,10 @@ struct Cta {
                         for (int ax = 0; ax < ND; ++ax) acc[ax] += pv * src[ax * N + c];
                     }
                     if (corr_b)
-                        for (int q = s; q < 2 * n; q += seg) {
-                            const T pbq = Pbg[(int64_t)r * 2 * n + q];
+                        for (int q = s; q < nbc * n; q += seg) {
+                            const T pbq = Pbg[(int64_t)r * nbc * n + q];
 #pragma unroll
-                            for (int ax = 0; ax < ND; ++ax) acc[ax] += pbq * db[(ax * n + (q >> 1)) * 2 + (q & 1)];
+                            for (int ax = 0; ax < ND; ++ax) acc[ax] += pbq * db[ax * n * nbc + q];
                         }
                 }
 #pragma unroll
@@ -1192,7 +1210,8 @@ struct Cta {
                 const int ax = e / nxi, u = e - ax * nxi;
                 T s = T(0);
                 for (int c = 0; c < nxi; ++c) s += Pdif[u * nxi + c] * mv[ax * nxi + c];
-                if (corr_b) s += Bdif[u * 2] * mb[ax * 2] + Bdif[u * 2 + 1] * mb[ax * 2 + 1];
+                if (corr_b)
+                    for (int q = 0; q < nbc; ++q) s += Bdif[u * nbc + q] * mb[ax * nbc + q];
                 pm[e] = s;
             }
             __syncthreads();
@@ -1207,7 +1226,8 @@ struct Cta {
                     s1 += pu[c + 1] * vr[c + 1];
                 }
                 if (c < nxi) s0 += pu[c] * vr[c];
-                if (corr_b) s1 += Bdev[u * 2] * db[r * 2] + Bdev[u * 2 + 1] * db[r * 2 + 1];
+                if (corr_b)
+                    for (int q = 0; q < nbc; ++q) s1 += Bdev[u * nbc + q] * db[r * nbc + q];
                 dst[e] = s0 + s1;
             }
         }
@@ -1317,8 +1337,9 @@ struct Cta {
         for (int e = tid; e < NN; e += nt) {
             const int r = e / nxi, c = e - r * nxi;
             T xn = xb[e] + dd[e];
-            if (c == 0) xn = bd[r * 2];                  // A xi_bar = b holds exactly
-            else if (c == nxi - 1) xn = bd[r * 2 + 1];
+            if (c == 0) xn = bf[3 * r];                  // A xi_bar = b holds exactly
+            else if (c == nxi - 1) xn = bf[3 * r + 2];
+            else if (nbc == 3 && c == 1) xn = bf[3 * r + 1];
             const T dx = xn - xb[e];
             fp += dx * dx;
             xb[e] = xn;

@@ -4,22 +4,25 @@
 //
 // The array holds the instance table, the shape record, the Bernstein basis, the
 // Kronecker blocks of the projection (P_dev, P_mean, B_dev, B_mean, computed here in
-// FP64 from the two n_xi x n_xi constrained inverses) and the status words.  The
-// forward and residual kernels are the library's ordinary ones, given pointers into
-// this array.
+// FP64 by the same routine as a handle's factorisation) and the status words.  One
+// set-up kernel writes all of it from arguments passed by value, so no host memory is
+// read after the call returns; the forward and residual kernels are the library's
+// ordinary ones, given pointers into this array.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "sf_internal.cuh"
+#include "sf_kron.cuh"
 
 namespace {
 
 constexpr int kNaMaxInst = SF_NOALLOC_MAX_INST;
 constexpr int kNaMaxH = SF_NOALLOC_MAX_H;
 constexpr int kNaMaxXi = 32;
-constexpr int kNaBlocks = 2 * kNaMaxXi * kNaMaxXi + 4 * kNaMaxXi;
+constexpr int kNaBlocks = 3 * kNaMaxXi * kNaMaxXi + 4 * kNaMaxXi;   // Kronecker record with two boundary rows
 constexpr int kNaMaxDevices = 64;
 
 struct NaScratch {
@@ -37,24 +40,62 @@ struct NaScratch {
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NaScratch)];
 
+// Device addresses of the array, looked up once per device under the mutex.
+std::mutex g_mu;
 void *g_addr[kNaMaxDevices];
 bool g_ready[kNaMaxDevices];
-sf::Inst<float> g_inst_host[kNaMaxInst];
-sf::Shape g_shape_host;
 
-constexpr int kKkt = kNaMaxXi + 2;
+// One call's set-up, passed by value (a captured launch carries its own copy).
+struct NaSetup {
+    sf_shape s;
+    int nd, nxi, n_inst, hc;
+    double rho;
+};
 
-// Basis and Kronecker blocks of one shape, FP64 then FP32 copies.  One CTA.
-// P_dev / P_mean are the x-blocks of the inverse of [[I + rho c W'W, A0'], [A0, 0]]
-// for c = n + n_obs + 2 and c = n_obs + 2 (A0 = rows 0 and H-1 of W); B_dev / B_mean
-// are its (x, b) blocks.  Gauss-Jordan elimination with partial pivoting.
-__global__ void k_na_operators(NaScratch *S, int nxi, int H, int n, int n_obs, double rho)
+// Instance table, shape record, basis and Kronecker blocks (FP64, then FP32 copies),
+// status words cleared.  One CTA.  A singular KKT system (a zero pivot) leaves NaN
+// blocks, so every iterate and residual of the call is NaN, and sets SF_EINVAL in the
+// status words.
+__global__ void k_na_setup(NaScratch *S, NaSetup u)
 {
-    __shared__ double wtw[kNaMaxXi * kNaMaxXi];
-    __shared__ double K[kKkt * kKkt];
-    __shared__ double X[kKkt * kKkt];
-    __shared__ int piv;
-    const int tid = threadIdx.x, nt = blockDim.x, deg = nxi - 1, m = nxi + 2;
+    __shared__ sf::KronSmem sm;
+    const int tid = threadIdx.x, nt = blockDim.x, nxi = u.nxi, nd = u.nd, H = u.s.H, deg = nxi - 1;
+    const int64_t N = (int64_t)u.s.n * nxi;
+    const int64_t per_xi = nd * N, per_bnd = (int64_t)nd * u.s.n * 2;
+    const int64_t per_obs = (int64_t)u.s.n_obs * (u.s.dyn_obs ? H : 1) * nd, per_oab = (int64_t)u.s.n_obs * 2;
+    for (int i = tid; i < u.n_inst; i += nt) {
+        sf::Inst<float> x;
+        memset(&x, 0, sizeof(x));
+        x.n = u.s.n;
+        x.n_obs = u.s.n_obs;
+        x.H = H;
+        x.dyn = u.s.dyn_obs;
+        x.N = (int)N;
+        x.shape = 0;
+        x.hc = u.hc;
+        x.a = (float)u.s.a;
+        x.b = (float)u.s.b;
+        x.ia2 = (float)(1.0 / (u.s.a * u.s.a));
+        x.ib2 = (float)(1.0 / (u.s.b * u.s.b));
+        for (int ax = 0; ax < 3; ++ax) {
+            x.pmin[ax] = (float)(ax < nd ? u.s.p_min[ax] : 0.0);
+            x.pmax[ax] = (float)(ax < nd ? u.s.p_max[ax] : 0.0);
+        }
+        x.off_xi = i * per_xi;
+        x.off_bnd = i * per_bnd;
+        x.off_obs = i * per_obs;
+        x.off_oab = i * per_oab;
+        S->inst[i] = x;
+        S->status[i] = SF_OK;
+    }
+    sf::Shape sh;
+    memset(&sh, 0, sizeof(sh));
+    sh.n = u.s.n;
+    sh.n_obs = u.s.n_obs;
+    sh.H = H;
+    sh.N = (int)N;
+    sh.nbc = 2;
+    if (tid == 0) S->shape = sh;
     for (int e = tid; e < H * nxi; e += nt) {
         const int k = e / nxi, c = e % nxi;
         const double tau = (double)k / (double)(H - 1);
@@ -62,69 +103,15 @@ __global__ void k_na_operators(NaScratch *S, int nxi, int H, int n, int n_obs, d
         for (int q = 1; q <= c; ++q) bin = bin * (double)(deg - c + q) / (double)q;
         S->W64[e] = bin * pow(tau, (double)c) * pow(1.0 - tau, (double)(deg - c));
     }
+    double *Cb = S->S64 + sf::kron_cost_off(nxi, 2);   // the projection cost's identity block
+    for (int e = tid; e < nxi * nxi; e += nt) Cb[e] = (e / nxi == e % nxi) ? 1.0 : 0.0;
     __syncthreads();
-    for (int e = tid; e < nxi * nxi; e += nt) {
-        const int u = e / nxi, v = e % nxi;
-        double s = 0.0;
-        for (int k = 0; k < H; ++k) s += S->W64[k * nxi + u] * S->W64[k * nxi + v];
-        wtw[e] = s;
-    }
-    for (int pass = 0; pass < 2; ++pass) {
-        const double c = pass == 0 ? (double)(n + n_obs + 2) : (double)(n_obs + 2);
-        __syncthreads();
-        for (int e = tid; e < m * m; e += nt) {
-            const int r = e / m, q = e % m;
-            double v;
-            if (r < nxi && q < nxi) v = (r == q ? 1.0 : 0.0) + rho * c * wtw[r * nxi + q];
-            else if (r < nxi) v = S->W64[(q == nxi ? 0 : H - 1) * nxi + r];
-            else if (q < nxi) v = S->W64[(r == nxi ? 0 : H - 1) * nxi + q];
-            else v = 0.0;
-            K[e] = v;
-            X[e] = r == q ? 1.0 : 0.0;
-        }
-        for (int p = 0; p < m; ++p) {
-            __syncthreads();
-            if (tid == 0) {
-                int best = p;
-                for (int r = p + 1; r < m; ++r)
-                    if (fabs(K[r * m + p]) > fabs(K[best * m + p])) best = r;
-                piv = best;
-            }
-            __syncthreads();
-            const int b = piv;
-            if (b != p)
-                for (int q = tid; q < m; q += nt) {
-                    double t = K[p * m + q]; K[p * m + q] = K[b * m + q]; K[b * m + q] = t;
-                    t = X[p * m + q]; X[p * m + q] = X[b * m + q]; X[b * m + q] = t;
-                }
-            __syncthreads();
-            const double d = K[p * m + p];
-            __syncthreads();
-            for (int q = tid; q < m; q += nt) {
-                K[p * m + q] /= d;
-                X[p * m + q] /= d;
-            }
-            __syncthreads();
-            for (int e = tid; e < m * m; e += nt) {
-                const int r = e / m, q = e % m;
-                if (r == p) continue;
-                const double f = K[r * m + p];
-                if (q != p) K[r * m + q] -= f * K[p * m + q];
-                X[r * m + q] -= f * X[p * m + q];
-            }
-            __syncthreads();
-            for (int r = tid; r < m; r += nt)
-                if (r != p) K[r * m + p] = 0.0;
-        }
-        __syncthreads();
-        double *Pout = S->S64 + pass * nxi * nxi;
-        double *Bout = S->S64 + 2 * nxi * nxi + pass * 2 * nxi;
-        for (int e = tid; e < nxi * nxi; e += nt) Pout[e] = X[(e / nxi) * m + e % nxi];
-        for (int e = tid; e < nxi * 2; e += nt) Bout[e] = X[(e / 2) * m + nxi + e % 2];
-    }
-    __syncthreads();
+    const int bad = sf::kron_kkt_blocks(sh, nxi, u.rho, S->W64, Cb, S->S64, sm);
     for (int e = tid; e < H * nxi; e += nt) S->W32[e] = (float)S->W64[e];
-    for (int e = tid; e < 2 * nxi * nxi + 4 * nxi; e += nt) S->S32[e] = (float)S->S64[e];
+    const int nb = (int)sf::kron_len(nxi, 2);
+    for (int e = tid; e < nb; e += nt) S->S32[e] = bad ? nanf("") : (float)S->S64[e];
+    if (bad)
+        for (int i = tid; i < u.n_inst; i += nt) S->status[i] = SF_EINVAL;
 }
 
 }  // namespace
@@ -147,11 +134,15 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return SF_ECUDA;
-    if (!g_ready[dev]) {
-        if (cudaGetSymbolAddress(&g_addr[dev], g_noalloc_scratch) != cudaSuccess) return SF_ECUDA;
-        g_ready[dev] = true;
+    NaScratch *S;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_ready[dev]) {
+            if (cudaGetSymbolAddress(&g_addr[dev], g_noalloc_scratch) != cudaSuccess) return SF_ECUDA;
+            g_ready[dev] = true;
+        }
+        S = static_cast<NaScratch *>(g_addr[dev]);  // device address: pointer arithmetic only
     }
-    NaScratch *S = static_cast<NaScratch *>(g_addr[dev]);  // device address: pointer arithmetic only
     cudaStream_t st = (cudaStream_t)stream;
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return SF_ECUDA;
@@ -159,7 +150,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
     // launch geometry of the forward kernel (structured projection, FP32)
     int num_sms = 0;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SF_ECUDA;
-    const int nd = n_d, nxi = n_xi, N = s.n * nxi;
+    const int nd = n_d, nxi = n_xi;
     Plan plan;
     int hc = 1;
     {
@@ -171,43 +162,15 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
     }
     const int threads = plan.threads;
 
-    // instance table and shape record, written into the fixed array
-    const int64_t per_xi = (int64_t)nd * s.n * nxi, per_bnd = (int64_t)nd * s.n * 2;
-    const int64_t per_obs = (int64_t)s.n_obs * (s.dyn_obs ? s.H : 1) * nd, per_oab = (int64_t)s.n_obs * 2;
-    for (int i = 0; i < n_inst; ++i) {
-        Inst<float> &x = g_inst_host[i];
-        memset(&x, 0, sizeof(x));
-        x.n = s.n;
-        x.n_obs = s.n_obs;
-        x.H = s.H;
-        x.dyn = s.dyn_obs;
-        x.N = N;
-        x.shape = 0;
-        x.hc = hc;
-        x.a = (float)s.a;
-        x.b = (float)s.b;
-        x.ia2 = (float)(1.0 / (s.a * s.a));
-        x.ib2 = (float)(1.0 / (s.b * s.b));
-        for (int ax = 0; ax < 3; ++ax) {
-            x.pmin[ax] = (float)(ax < nd ? s.p_min[ax] : 0.0);
-            x.pmax[ax] = (float)(ax < nd ? s.p_max[ax] : 0.0);
-        }
-        x.off_xi = i * per_xi;
-        x.off_bnd = i * per_bnd;
-        x.off_obs = i * per_obs;
-        x.off_oab = i * per_oab;
-    }
-    memset(&g_shape_host, 0, sizeof(g_shape_host));
-    g_shape_host.n = s.n;
-    g_shape_host.n_obs = s.n_obs;
-    g_shape_host.H = s.H;
-    g_shape_host.N = N;
-    // pageable host sources: each copy has read its source when the call returns
-    if (cudaMemcpyAsync(S->inst, g_inst_host, sizeof(Inst<float>) * n_inst, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(&S->shape, &g_shape_host, sizeof(Shape), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(S->status, 0, sizeof(int32_t) * n_inst, st) != cudaSuccess)
-        return SF_ECUDA;
-    k_na_operators<<<1, 256, 0, st>>>(S, nxi, s.H, s.n, s.n_obs, rho);
+    NaSetup u;
+    memset(&u, 0, sizeof(u));
+    u.s = s;
+    u.nd = nd;
+    u.nxi = nxi;
+    u.n_inst = n_inst;
+    u.hc = hc;
+    u.rho = rho;
+    k_na_setup<<<1, 256, 0, st>>>(S, u);
     if (cudaGetLastError() != cudaSuccess) return SF_ECUDA;
 
     FwdArgs<float> a;

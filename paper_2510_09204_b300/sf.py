@@ -44,7 +44,8 @@ class sf_desc(ct.Structure):
     _fields_ = [("n_d", ct.c_int32), ("n_xi", ct.c_int32), ("rho", ct.c_double), ("precision", ct.c_int32),
                 ("proj", ct.c_int32), ("n_refine", ct.c_int32), ("max_iters", ct.c_int32),
                 ("ckpt_every", ct.c_int32), ("tol", ct.c_double), ("n_inst", ct.c_int32),
-                ("shapes", ct.POINTER(sf_shape)), ("stream", ct.c_void_p), ("cost", ct.c_int32), ("dt", ct.c_double)]
+                ("shapes", ct.POINTER(sf_shape)), ("stream", ct.c_void_p), ("cost", ct.c_int32), ("dt", ct.c_double),
+                ("n_bc", ct.c_int32)]
 
 
 class sf_instance_data(ct.Structure):
@@ -118,11 +119,13 @@ class SFSolver:
     """A handle over a fixed batch of instance shapes (``sf_create`` .. ``sf_destroy``).
 
     ``shapes``: list of dicts with keys n, n_obs, H, a, b, pmin, pmax and optional dyn_obs
-    (the instance dicts of ``sfgen`` qualify).
+    (the instance dicts of ``sfgen`` qualify).  ``n_bc``: boundary rows per robot and axis,
+    2 (start, goal) or 3 (with the initial velocity, time step ``dt``); None takes it from
+    the first shape's ``bnd`` array when it has one, else 2.
     """
 
     def __init__(self, shapes, n_d, n_xi=11, rho=0.3, precision="fp32", proj="dense", max_iters=1000,
-                 ckpt_every=0, tol=1e-3, n_refine=0, stream=None, cost="projection", dt=0.1):
+                 ckpt_every=0, tol=1e-3, n_refine=0, stream=None, cost="projection", dt=0.1, n_bc=None):
         if not torch.cuda.is_available():
             raise RuntimeError("SFSolver needs a CUDA device; there is no CPU path")
         L = lib()
@@ -140,9 +143,12 @@ class SFSolver:
                 arr[k].p_max[ax] = float(s["pmax"][ax])
         self._shapes = [dict(n=int(s["n"]), n_obs=int(s["n_obs"]), H=int(s["H"]),
                              dyn_obs=bool(s.get("dyn_obs", False))) for s in shapes]
+        if n_bc is None:
+            n_bc = int(np.shape(shapes[0]["bnd"])[-1]) if "bnd" in shapes[0] else 2
+        self.n_bc = int(n_bc)
         d = sf_desc(self.n_d, self.n_xi, self.rho, PRECISIONS[precision], PROJECTIONS[proj], int(n_refine),
                     int(max_iters), int(ckpt_every), float(tol), self.B, arr, _stream(stream), COSTS[cost],
-                    float(dt))
+                    float(dt), self.n_bc)
         self.cost = cost
         h = ct.c_void_p()
         _check(L.sf_create(ct.byref(d), ct.byref(h)), "sf_create")
@@ -288,12 +294,13 @@ class SFSolver:
     def operator(self, k, which):
         s = self._shapes[k]
         N = s["n"] * self.n_xi
-        size = {0: s["H"] * self.n_xi, 1: N * N, 2: N * 2 * s["n"],
-                3: 3 * self.n_xi ** 2 + 4 * self.n_xi}[which]
+        nb = self.n_bc
+        size = {0: s["H"] * self.n_xi, 1: N * N, 2: N * nb * s["n"],
+                3: 3 * self.n_xi ** 2 + 2 * nb * self.n_xi}[which]
         out = np.empty(size)
         _check(lib().sf_shape_operator(self.h, k, which, out.ctypes.data_as(ct.POINTER(ct.c_double))),
                "sf_shape_operator")
-        shape = {0: (s["H"], self.n_xi), 1: (N, N), 2: (N, 2 * s["n"]), 3: (size,)}[which]
+        shape = {0: (s["H"], self.n_xi), 1: (N, N), 2: (N, nb * s["n"]), 3: (size,)}[which]
         return out.reshape(shape)
 
     def close(self):

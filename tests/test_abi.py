@@ -57,13 +57,14 @@ def test_create_rejects_bad_descriptors_without_touching_the_device():
     for ax in range(2):
         shapes[0].p_min[ax], shapes[0].p_max[ax] = -5.0, 5.0
     good = dict(n_d=2, n_xi=11, rho=0.3, precision=1, proj=0, n_refine=0, max_iters=10, ckpt_every=0, tol=1e-3,
-                n_inst=1)
+                n_inst=1, cost=0, dt=0.1, n_bc=2)
     bad_cases = [dict(n_d=4), dict(n_xi=1), dict(rho=0.0), dict(rho=float("nan")), dict(precision=9), dict(n_inst=0),
-                 dict(max_iters=-1)]
+                 dict(max_iters=-1), dict(n_bc=4), dict(n_bc=3, dt=0.0), dict(n_bc=3, n_xi=4)]
     for bad in bad_cases:
         kw = dict(good, **bad)
         d = sf.sf_desc(kw["n_d"], kw["n_xi"], kw["rho"], kw["precision"], kw["proj"], kw["n_refine"],
-                       kw["max_iters"], kw["ckpt_every"], kw["tol"], kw["n_inst"], shapes, None)
+                       kw["max_iters"], kw["ckpt_every"], kw["tol"], kw["n_inst"], shapes, None, kw["cost"], kw["dt"],
+                       kw["n_bc"])
         h = ct.c_void_p()
         assert L.sf_create(ct.byref(d), ct.byref(h)) == sf.SF_EINVAL, bad
     shapes[0].a = -1.0

@@ -79,3 +79,40 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     long_h = [dict(insts[0], H=sf.SF_NOALLOC_MAX_H + 1)]
     assert _noalloc(long_h, 1, data, xo, None, None) == sf.SF_ETOOBIG
     assert sf.lib().sf_strerror(sf.SF_ETOOBIG).startswith(b"size beyond")
+
+
+def _reference(cid, B, iters):
+    insts = sfgen.make_batch(cid, B=B)
+    ref = SFSolver(insts, insts[0]["n_d"], 11, rho=RHO, precision="fp32", proj="structured", max_iters=iters)
+    data = ref.pack(insts)
+    xr, _, _ = ref.solve(data, data["xi"], iters)
+    torch.cuda.synchronize()
+    return insts, data, xr
+
+
+def _call_and_compare(insts, data, xr, iters):
+    B = len(insts)
+    xo = torch.full_like(data["xi"], float("nan"))
+    res = torch.full((B, sf.SF_NRES), float("nan"), dtype=torch.float64, device="cuda")
+    assert _noalloc(insts, iters, data, xo, None, res) == sf.SF_OK
+    torch.cuda.synchronize()
+    W = torch.as_tensor(oracle.basis(insts[0]["H"], 11))
+    per = insts[0]["n_d"] * insts[0]["n"] * 11
+    for k in range(B):
+        a = xo[k * per:(k + 1) * per].view(insts[0]["n_d"], -1, 11).double().cpu()
+        b = xr[k * per:(k + 1) * per].view(insts[0]["n_d"], -1, 11).double().cpu()
+        assert torch.einsum("kc,dic->dik", W, a - b).abs().max().item() <= 1e-4
+    assert torch.isfinite(res).all()
+    return xo
+
+
+def test_noalloc_another_shape_in_between():
+    """A 3-D call with another shape (64 robots, 100 obstacles) between two 2-D calls: each
+    call rewrites the instance table, basis and operators of the shared array from its own
+    arguments, so each matches its ordinary solve and the two 2-D calls agree bit for bit."""
+    a = _reference(2, 4, 80)
+    b = _reference(5, 2, 30)
+    x1 = _call_and_compare(*a, 80)
+    _call_and_compare(*b, 30)
+    x2 = _call_and_compare(*a, 80)
+    assert torch.equal(x1, x2)
