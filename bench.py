@@ -15,7 +15,8 @@ line.
                   [--config C] [--precision P] [--proj dense|structured] [--forward-only]
 
 Under torchrun each rank solves its own batch (seeds offset by rank): weak scaling,
-no collective on the data path; the step time is the max over ranks.
+no collective on the data path; the step time is the max over ranks.  --shard-batch
+instead splits the one batch over the ranks with shard.balance (strong scaling).
 """
 from __future__ import annotations
 
@@ -38,8 +39,7 @@ import sfgen  # noqa: E402
 SF_NRES = 5   # columns of sf_solve's residual output (include/sf.h)
 
 RHO = 0.3
-SM_COUNT_B300 = 148
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128   # only for the fallback peak when the measurement fails
 
 
 def args_():
@@ -59,6 +59,9 @@ def args_():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 and tensor-core comparison solves")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-configs", action="store_true", help="skip the other workloads' summary (configs 3, 4, 5)")
+    p.add_argument("--shard-batch", action="store_true",
+                   help="under torchrun: split the one batch over the ranks (shard.balance) instead of one batch per rank")
     return p.parse_args()
 
 
@@ -66,47 +69,88 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def workload(cid, rank=0):
+def workload(cid, rank=0, world=1, shard_batch=False):
+    """The config's batch: one batch per rank (seeds offset by rank), or with shard_batch
+    this rank's share of the one batch (shard.balance by rows per iteration)."""
     cfg = sfgen.CONFIGS[cid]
-    insts = sfgen.make_batch(cid, start=rank * cfg.B)
+    if shard_batch:
+        from paper_2510_09204_b300.shard import shard
+        _, insts = shard(sfgen.make_batch(cid), rank, world)
+    else:
+        insts = sfgen.make_batch(cid, start=rank * cfg.B)
     pairs, obs = sfgen.batch_stats(insts)
     return cfg, insts, pairs, obs
 
 
+# Algorithmic work per pair or obstacle row in the algebraic form of the alpha/beta/d
+# closed forms (line of sight, scaled squared norm, activity test, r_1 = Delta (1 - s)
+# and its accumulation): 14 FP operations and one reciprocal square root in 2-D, 19 and
+# one in 3-D.
+ROW_FLOPS = {2: 14, 3: 19}
+
+
 def _per_iter(i, proj):
-    """Algorithmic FP32 operations of one forward iteration of one instance: per pair or
-    obstacle row 2 n_d + 1 (line of sight, scaled squared norm), per (robot, timestep)
-    2 n_d box tests, positions and W' aggregation 2 n_d n H n_xi each, lambda and the
-    correction 6 n_d N, projection 2 n_d N^2 (dense) or 4 n_d n n_xi^2 (structured)."""
+    """Algorithmic FP operations of one forward iteration of one instance: ROW_FLOPS per
+    pair or obstacle row, 2 n_d per (robot, timestep) box test, positions W xi_bar once and
+    the W' aggregation twice (of e and of r_1) at 2 n_d n H n_xi each, lambda and the
+    right-hand side 6 n_d N, projection 2 n_d N^2 (dense) or 4 n_d n n_xi^2 (Kronecker
+    form).  Returns (flops, rows, projection flops); rows is also the count of reciprocal
+    square roots."""
     nd, n, H, nxi, no = i["n_d"], i["n"], i["H"], i["n_xi"], i["n_obs"]
     N = n * nxi
     rows = (n * (n - 1) // 2 + n * no) * H
-    per = rows * (2 * nd + 1) + 2 * nd * n * H + 4 * nd * n * H * nxi + 6 * nd * N
+    per = rows * ROW_FLOPS[nd] + 2 * nd * n * H + 3 * (2 * nd * n * H * nxi) + 6 * nd * N
     proj_f = 2 * nd * N * N if proj == "dense" else 4 * nd * n * nxi * nxi
     return per + proj_f, rows, proj_f
 
 
 def algorithmic_flops(insts, iters, proj, kernel="k_forward", ckpt_every=1):
-    """Operations of one launch of ``kernel`` at the algorithmic minimum.
-    k_forward: iters forward iterations.  k_backward: the recomputation inside the
-    checkpoint segments (c - 1 forward iterations per segment of c) plus the reverse
-    sweep, per iteration the activity test of every row (2 n_d + 1) and box entry
-    (2 n_d), positions, R* = W g* and W' p* (2 n_d n H n_xi each), the projection and
-    8 n_d N elementwise.  k_residual: one FP64 pass over the rows and the positions."""
+    """(FP operations, reciprocal square roots) of one launch of ``kernel`` at the
+    algorithmic minimum.  k_forward: iters forward iterations.  k_backward: the
+    recomputation inside the checkpoint segments (c - 1 forward iterations per segment of
+    c) plus the reverse sweep, per iteration ROW_FLOPS per row (the line of sight,
+    activity test and the active row's Jacobian product), 2 n_d per box entry, positions,
+    R* = W g* and W' p* (2 n_d n H n_xi each), the projection and 8 n_d N elementwise.
+    k_residual: one FP64 pass over the rows and the positions."""
     c = max(1, ckpt_every)
     recompute = iters - (iters + c - 1) // c
-    tot = 0.0
+    tot, mufu = 0.0, 0.0
     for i in insts:
         fwd, rows, proj_f = _per_iter(i, proj)
         nd, n, H, nxi = i["n_d"], i["n"], i["H"], i["n_xi"]
         if kernel == "k_forward":
             tot += fwd * iters
+            mufu += rows * iters
         elif kernel == "k_backward":
-            rev = rows * (2 * nd + 1) + 2 * nd * n * H + 6 * nd * n * H * nxi + proj_f + 8 * nd * n * nxi
+            rev = rows * ROW_FLOPS[nd] + 2 * nd * n * H + 6 * nd * n * H * nxi + proj_f + 8 * nd * n * nxi
             tot += fwd * recompute + rev * iters
+            mufu += rows * (recompute + iters)
         else:
-            tot += rows * (2 * nd + 1) + 2 * nd * n * H + 2 * nd * n * H * nxi
-    return tot
+            tot += rows * ROW_FLOPS[nd] + 2 * nd * n * H + 2 * nd * n * H * nxi
+            mufu += rows
+    return tot, mufu
+
+
+def alu_peaks(dev, seconds=1.0):
+    """Measured pipe throughputs of this GPU (sf_alu_peaks: FP32 FMA, FP64 FMA, MUFU rsqrt,
+    each a timed loop of about a second), and the SM count; falls back to the FP32 lanes x
+    clock product when the measurement fails."""
+    import torch
+
+    from paper_2510_09204_b300.sf import alu_peaks as measure
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    try:
+        f32, f64, mufu = measure(seconds)
+        return {"fp32_tflops": f32 / 1e12, "fp64_tflops": f64 / 1e12, "mufu_tops": mufu / 1e12, "sms": sms,
+                "source": "measured on this GPU by sf_alu_peaks (FMA / rsqrt dependency chains on every SM, "
+                          "CUDA events, best of 3 launches of ~%.2f s)" % (seconds / 3)}
+    except Exception as e:  # reported, never hidden
+        sm_max = float(measured_peaks().get("sm_max_mhz", 2032.0))
+        return {"fp32_tflops": sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12, "fp64_tflops": None,
+                "mufu_tops": None, "sms": sms,
+                "source": "derived (%d SMs x 128 FP32 lanes x 2 x %.0f MHz): measurement failed: %s"
+                          % (sms, sm_max, str(e)[:120])}
 
 
 class ClockSampler:
@@ -291,9 +335,10 @@ def run_reference(a):
     desc = _oracle_desc(len(sample), len(insts), iters, a.forward_only) + " per step"
     line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "pair-timestep updates/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": 1e3 * tot / a.steps * len(insts) / len(sample), "higher_is_better": True,
+            "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(cfg, insts, iters, a, {"precision": "fp64 (oracle)"}),
+            "config": _config(cfg, insts, iters, a, {"precision": "fp64 (oracle)",
+                                                     "instances_timed_per_step": len(sample)}),
             "cpu_baseline": {"value": value, "unit": "pair-timestep updates/s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "pair-timestep updates/s", "h2d_bytes_per_step": 0,
@@ -512,6 +557,119 @@ def _pipeline(a, dev, stream, problems=50, per=10, keep=5, iters=500):
             "paper": "< 300 ms to refine 250 trajectories (RTX 5090, JAX; robots and iterations not stated)"}
 
 
+def rounded32(inst):
+    """The instance as an FP32 handle holds it: every array and shape parameter rounded to
+    float32 (an FP32 solve cannot see finer input than that)."""
+    p = dict(inst)
+    for key in ("xi", "bnd", "obs_c", "obs_ab", "pmin", "pmax"):
+        p[key] = np.asarray(inst[key], dtype=np.float32).astype(np.float64)
+    for key in ("a", "b"):
+        p[key] = float(np.float32(inst[key]))
+    return p
+
+
+def _config_step(cid, precision, proj, n_refine, dev, stream, flush, reps=5, graph=False, round_input=False):
+    """One workload's step on the GPU (the config's own iteration count; the
+    differentiable config 4 also runs the adjoint, checkpoints every 10): autotuned
+    geometry, CUDA events, L2 flushed between steps; optionally replayed from a CUDA
+    graph.  Returns (record, positions, residuals)."""
+    import torch
+
+    from paper_2510_09204_b300 import SFSolver
+    cfg = sfgen.CONFIGS[cid]
+    insts = sfgen.make_batch(cid)
+    if round_input:
+        insts = [rounded32(i) for i in insts]
+    iters, nd = cfg.iters, cfg.n_d
+    ck = int(cfg.extra.get("ckpt_every", 0))
+    fwd_only = ck == 0
+    s = SFSolver(insts, nd, 11, rho=RHO, precision=precision, proj=proj, max_iters=iters, ckpt_every=ck,
+                 n_refine=n_refine)
+    d = s.pack(insts, device=dev)
+    s.autotune(d, d["xi"], iters, reps=1, stream=stream)
+    st = Step(s, d, iters, fwd_only, stream)
+    for _ in range(2):
+        st()
+    torch.cuda.synchronize()
+    run = st
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            gst = Step(s, d, iters, fwd_only, side)
+            gst()
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            gst.stream = torch.cuda.current_stream()
+            gst()
+        run, st = g.replay, gst
+    times, _ = _time_steps(run, reps, stream, flush)
+    ok = bool((s.status() == 0).all())
+    pos, res = _positions(s, st.xo, insts), st.res.cpu().numpy()
+    rec = {"precision": precision, "projection": proj, "n_refine": n_refine, "ms_per_step": statistics.median(times),
+           "launch": list(s.launch()[:2]), "status_ok": ok, "cuda_graph": graph}
+    s.close()
+    return rec, pos, res, insts, iters, fwd_only
+
+
+def other_configs(dev, stream, flush, peaks):
+    """The other workloads of the benchmark set, each against the plain FP64 GPU path (time
+    on the same batch; max position error and final residual difference against FP64 on
+    the same input as FP32 holds it, i.e. rounded to float32, and the position difference
+    to FP64 on the unrounded input beside it) and against the measured FP32 peak
+    (algorithmic flops of its step / time):
+      3  64 uneven instances, FP32 structured, replayed from a CUDA graph
+      4  128 x 32 robots, FP32 differentiable step (forward + adjoint, checkpoints every 10)
+      5  16 x 64 robots in 3-D: FP32 (structured, dense SIMT) and the tensor-core projection
+         in BF16 (+5 refinement passes), TF32 (+3) and BF16 x3 (+1)"""
+    out = {}
+    plan = {3: [("fp32", "structured", 0, True)], 4: [("fp32", "structured", 0, False)],
+            5: [("fp32", "structured", 0, False), ("fp32", "dense", 0, False), ("bf16", "dense", 5, False),
+                ("tf32", "dense", 3, False), ("bf16x3", "dense", 1, False)]}
+    for cid, runs in plan.items():
+        ref, praw, _, insts, iters, fwd_only = _config_step(cid, "fp64", "structured", 0, dev, stream, flush, reps=3)
+        _, pref, rref, _, _, _ = _config_step(cid, "fp64", "structured", 0, dev, stream, flush, reps=1,
+                                              round_input=True)
+        recs = []
+        for prec, proj, nr, gr in runs:
+            rec, pos, res, _, _, _ = _config_step(cid, prec, proj, nr, dev, stream, flush, graph=gr)
+            fl = algorithmic_flops(insts, iters, proj, "k_forward")[0]
+            if not fwd_only:
+                fl += algorithmic_flops(insts, iters, proj, "k_backward", 10)[0]
+            rec["max_position_error_vs_fp64_m"] = _max_pos_err(pos, pref)
+            rec["max_position_diff_vs_fp64_unrounded_input_m"] = _max_pos_err(pos, praw)
+            rec["max_final_residual_diff_vs_fp64_m"] = float(np.abs(res[:, 1] - rref[:, 1]).max())
+            rec["achieved_tflops"] = fl / (rec["ms_per_step"] * 1e-3) / 1e12
+            rec["frac_of_measured_fp32"] = rec["achieved_tflops"] / peaks["fp32_tflops"]
+            rec["speedup_vs_fp64"] = ref["ms_per_step"] / rec["ms_per_step"]
+            recs.append(rec)
+        cfg = sfgen.CONFIGS[cid]
+        out[cfg.name] = {"iterations": iters, "step": "forward" if fwd_only else "forward + adjoint",
+                         "fp64_gpu_ms": ref["ms_per_step"], "runs": recs}
+    return out
+
+
+def summary_of(line, configs):
+    """The few numbers a reader needs, last in the line: the chosen step against plain
+    FP64 on the GPU, and per other workload its fastest run's time, error and fraction."""
+    s = {"chosen_ms": line["ms_per_step"], "roofline_frac": line["roofline"]["frac"]}
+    f = line.get("fp64_gpu")
+    if f:
+        s.update(fp64_gpu_ms=f["ms_per_step"], chosen_speedup_vs_fp64=f["chosen_speedup"],
+                 chosen_max_position_error_vs_fp64_m=f["chosen_max_position_error_m"])
+    for name, c in (configs or {}).items():
+        best = min(c["runs"], key=lambda r: r["ms_per_step"])
+        s[name] = {"fp64_gpu_ms": c["fp64_gpu_ms"],
+                   "runs_ms": {"%s/%s+%d" % (r["precision"], r["projection"], r["n_refine"]): round(r["ms_per_step"], 3)
+                               for r in c["runs"]},
+                   "best": "%s/%s" % (best["precision"], best["projection"]), "best_ms": best["ms_per_step"],
+                   "best_frac": best["frac_of_measured_fp32"],
+                   "max_position_error_vs_fp64_m": max(r["max_position_error_vs_fp64_m"] for r in c["runs"])}
+    return s
+
+
 def main():
     a = args_()
     if a.impl == "reference":
@@ -528,7 +686,10 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg, insts, pairs, obs = workload(a.config, rank)
+    cfg, insts, pairs, obs = workload(a.config, rank, world, a.shard_batch)
+    # work of the whole job: every rank's batch, or the one batch split over the ranks
+    pairs_job = sfgen.batch_stats(sfgen.make_batch(a.config))[0] if a.shard_batch else pairs * world
+    peaks = alu_peaks(dev)   # before the timed region
     iters = cfg.iters
     nd = cfg.n_d
     stream = torch.cuda.current_stream()
@@ -573,7 +734,7 @@ def main():
     clk = clocks.stop()
     tot_ms = max_over_ranks(sum(times), dev)
     ms_step = tot_ms / a.steps
-    value = pairs * iters * world / (ms_step * 1e-3)
+    value = pairs_job * iters / (ms_step * 1e-3)
     r = step.res.cpu().numpy()
     chosen_pos = _positions(solver, step.xo, insts)
 
@@ -630,7 +791,7 @@ def main():
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         h2d += 0 if a.forward_only else hg.numel() * hg.element_size()
         d2h = sum(o.numel() * o.element_size() for o in outs)
-        e2e = {"value": pairs * iters * world / e2e_s, "unit": "pair-timestep updates/s",
+        e2e = {"value": pairs_job * iters / e2e_s, "unit": "pair-timestep updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
     # plain FP64 GPU solve of the same step, and the tensor-core / structured variants
@@ -647,45 +808,56 @@ def main():
         pipeline = _pipeline(a, dev, stream)
         convergence = _convergence(insts, nd, a, dev, stream)
         for prec, proj, nr in [("fp32", "structured" if a.proj == "dense" else "dense", 0), ("tf32", "dense", 2),
-                               ("bf16x3", "dense", 1), ("bf16", "dense", 3)]:
+                               ("bf16x3", "dense", 1), ("bf16", "dense", 5)]:
             if (prec, proj, nr) == (a.precision, a.proj, a.n_refine):
                 continue
             v = _variant(insts, nd, iters, a, prec, proj, nr, dev, stream, flush, p64, r64)
             v.pop("_pos"), v.pop("_res")
             variants.append(v)
 
+    configs = None
+    if not a.no_compare and not a.no_configs and rank == 0:
+        configs = other_configs(dev, stream, flush, peaks)
+
     if rank == 0:
-        peaks = measured_peaks()
-        sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-        peak_alu = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        peak_alu = peaks["fp32_tflops"]
         names = ["k_forward", "k_residual", "k_backward"]
         kernels = {}
         for k, nm in enumerate(names):
             if a.forward_only and nm == "k_backward":
                 continue
             ms = statistics.mean(x[k] for x in kts)
-            fl = algorithmic_flops(insts, iters, a.proj, nm, a.ckpt_every)
+            fl, mufu = algorithmic_flops(insts, iters, a.proj, nm, a.ckpt_every)
             ach = fl / (ms * 1e-3) / 1e12
             kernels[nm] = {"ms": ms, "share": ms / ms_step, "algorithmic_gflop": fl / 1e9, "achieved_tflops": ach,
-                           "frac": ach / peak_alu}
+                           "frac": ach / peak_alu, "rsqrt_g": mufu / 1e9,
+                           "mufu_frac": (mufu / (ms * 1e-3) / 1e12 / peaks["mufu_tops"]) if peaks["mufu_tops"] else None}
         dom = max(kernels, key=lambda k: kernels[k]["ms"])
         traffic, traffic_src = profiled_traffic(dom, cfg.name, a.precision, a.proj)
         line = {
             "metric": METRIC,
             "value": value, "unit": "pair-timestep updates/s", "n_gpus": world, "steps": a.steps,
-            "warmup": max(a.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": max(a.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "strong" if a.shard_batch else "weak",
             "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32", "data": "synthetic",
             "config": _config(cfg, insts, iters, a, {
                 "precision": a.precision, "projection": a.proj, "n_refine": a.n_refine,
                 "l2": "flushed between steps (256 MB write)",
                 "cluster_ctas_per_instance": solver.launch()[0], "threads_per_cta": solver.launch()[1],
                 "autotune": tune,
-                "parallelism": "instances sharded by rank" if world > 1 else "single GPU"}),
+                "parallelism": ("one batch split over the ranks (shard.balance)" if a.shard_batch else
+                                "one batch per rank") if world > 1 else "single GPU"}),
             "roofline": {"bound": "alu", "achieved": kernels[dom]["achieved_tflops"], "peak": peak_alu,
                          "unit": "TFLOP/s", "frac": kernels[dom]["frac"], "traffic": traffic,
                          "traffic_source": traffic_src, "kernel": dom,
                          "kernel_ms": kernels[dom]["ms"],
-                         "peak_source": "148 SMs x 128 FP32 lanes x 2 x sm_max_mhz %.0f (derived ALU peak)" % sm_max},
+                         "algorithmic": "per pair or obstacle row %d flops (2-D) / %d (3-D) + 1 rsqrt; positions once "
+                                        "and the W' aggregation twice at 2 n_d n H n_xi; 2 n_d per box entry; "
+                                        "6 n_d N; projection 4 n_d n n_xi^2 (Kronecker) or 2 n_d N^2 (dense)"
+                                        % (ROW_FLOPS[2], ROW_FLOPS[3]),
+                         "peak_source": peaks["source"], "sms": peaks["sms"],
+                         "measured_peaks": {"fp32_tflops": peaks["fp32_tflops"], "fp64_tflops": peaks["fp64_tflops"],
+                                            "mufu_trsqrt_per_s": peaks["mufu_tops"]}},
             "kernels": kernels,
             "clocks": clk,
             "gpu_launches": step.launches() * a.steps,
@@ -709,8 +881,11 @@ def main():
             line["pipeline"] = pipeline
         if convergence:
             line["convergence"] = convergence
-        if not a.no_cpu_baseline:
+        if configs:
+            line["configs"] = configs
+        if not a.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(insts, iters, a.forward_only)
+        line["summary"] = summary_of(line, configs)   # last, so a truncated tail still shows it
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -364,6 +364,17 @@ int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_shape *shap
                      const float *bnd, const float *obs_c, const float *obs_ab, const float *xi_cand,
                      int32_t iters, float *xi_out, float *lam_out, double *resid_out, void *stream);
 
+/*
+ * sf_alu_peaks — measured throughput of the arithmetic pipes the solver's row kernels run
+ * on, for their roofline (a diagnostic; the paper has no counterpart): out[0] FP32 FMA
+ * (flop/s, 2 per FMA), out[1] FP64 FMA (flop/s), out[2] MUFU reciprocal square roots per
+ * second.  Each is a kernel that keeps every SM of the current device busy with
+ * independent dependency chains, timed with CUDA events (best of three launches of about
+ * seconds / 3 each, after a warm-up).  Allocates and frees 64 bytes of device memory and
+ * synchronises `stream`.  seconds in (0, 60].  Errors: SF_EINVAL, SF_ENOMEM, SF_ECUDA.
+ */
+int sf_alu_peaks(double seconds, double *out, void *stream);
+
 /* sf_strerror — static description of a status code. */
 /*
  * sf_fit_positions — least-squares Bernstein coefficients of sampled trajectories, with

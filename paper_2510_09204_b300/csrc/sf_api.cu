@@ -561,6 +561,7 @@ static FwdArgs<T> fwd_args(const sf_handle *h, const void *bnd, const void *obs,
     memset(&a, 0, sizeof(a));
     a.nd = h->d.n_d;
     a.nxi = h->d.n_xi;
+    a.nbc = h->nbc;
     a.iters = iters;
     a.n_inst = h->d.n_inst;
     a.csize = h->plan.csize;

@@ -274,12 +274,12 @@ static cudaError_t go_backward(const BwdArgs<T> &a, int nxi, int ni, int cs, int
 {
     constexpr bool f32 = sizeof(T) == 4;
     const auto &f = a.f;
-    if (f32 && nxi == 11 && f.cull && f.cost == SF_COST_PROJECTION) {
+    if (f32 && nxi == 11 && f.nbc == 2 && f.cull && f.cost == SF_COST_PROJECTION) {
         if (f.proj == SF_PROJ_DENSE)
             return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 2 : 0>, a, ni, cs, threads, smem, s);
         if (!TC) return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 1 : 0>, a, ni, cs, threads, smem, s);
     }
-    if (f32 && !TC && nxi == 11 && f.cull && f.cost == SF_COST_SMOOTHNESS && f.proj == SF_PROJ_STRUCTURED)
+    if (f32 && !TC && nxi == 11 && f.nbc == 2 && f.cull && f.cost == SF_COST_SMOOTHNESS && f.proj == SF_PROJ_STRUCTURED)
         return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 3 : 0>, a, ni, cs, threads, smem, s);
     return launch_cluster(k_backward<T, ND, MAXT, TC, 0, 0>, a, ni, cs, threads, smem, s);
 }

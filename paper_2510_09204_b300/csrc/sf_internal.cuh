@@ -179,6 +179,7 @@ __host__ __device__ inline BwdCarve backward_carve(int nd, int nxi, int wrows, i
 template <typename T>
 struct FwdArgs {
     int nd, nxi, iters, n_inst;
+    int nbc;          // boundary rows per robot and axis (every shape of the handle)
     int csize;        // CTAs per instance (thread-block cluster), 1..kMaxCluster
     int p_rows;       // rows of P_eta per CTA staged in shared memory (dense; 0 = global)
     int tc_mode;      // tensor-core projection: 0 none, 1 TF32, 2 BF16, 3 BF16 x3

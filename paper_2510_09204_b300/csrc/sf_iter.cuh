@@ -238,7 +238,7 @@ struct Cta {
         esc = false;
         cdel = T(0.5) * fmax(I.a, I.b);
         bd = sm + cv.bd; db = sm + cv.db; bf = sm + cv.bf; sx = sm + cv.sx; red = sm + cv.red; Ps = sm + cv.Ps;
-        nbc = S.nbc;
+        nbc = MODE ? 2 : S.nbc;   // the compile-time modes serve the two-row boundary only
         vsc = T(S.vsc);
         P = reinterpret_cast<VP *>(sm + cv.pb);
         gstride = carve_round(NN + 4 + 3 * 32, (int)sizeof(T));

@@ -177,6 +177,7 @@ extern "C" int sf_solve_noalloc(int32_t n_d, int32_t n_xi, double rho, const sf_
     memset(&a, 0, sizeof(a));
     a.nd = nd;
     a.nxi = nxi;
+    a.nbc = 2;
     a.iters = iters;
     a.n_inst = n_inst;
     a.csize = plan.csize;

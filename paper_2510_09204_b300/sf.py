@@ -30,7 +30,7 @@ COSTS = {"projection": 0, "smoothness": 1}
 EXPORTS = ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
            "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch",
            "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions", "sf_metrics",
-           "sf_select", "sf_strerror", "sf_version")
+           "sf_select", "sf_alu_peaks", "sf_strerror", "sf_version")
 SF_OPT_CULL, SF_OPT_TEST_TIMEOUT, SF_OPT_TC_RESIDENT = 1, 2, 3
 SF_KT_FORWARD, SF_KT_RESIDUAL, SF_KT_BACKWARD, SF_NKT = range(4)
 
@@ -90,11 +90,14 @@ def lib(path: str | None = None):
         L.sf_metrics.argtypes = [vp, ct.POINTER(sf_instance_data), vp, vp, vp]
         L.sf_select.argtypes = [i32, ct.POINTER(i32), vp, vp, ct.c_double, i32, vp, vp]
         L.sf_get_option.argtypes = [vp, i32, ct.POINTER(i32)]
+        L.sf_alu_peaks.argtypes = [ct.c_double, ct.POINTER(ct.c_double), vp]
         L.sf_strerror.argtypes = [i32]
         L.sf_strerror.restype = ct.c_char_p
         L.sf_version.restype = i32
         for f in ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backward", "sf_get_status",
-                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch", "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions", "sf_metrics", "sf_select"):
+                  "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch",
+                  "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions", "sf_metrics",
+                  "sf_select", "sf_alu_peaks"):
             getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -313,6 +316,13 @@ class SFSolver:
             self.close()
         except Exception:
             pass
+
+
+def alu_peaks(seconds=1.0, stream=None):
+    """sf_alu_peaks: measured (FP32 flop/s, FP64 flop/s, MUFU rsqrt/s) of the current device."""
+    out = (ct.c_double * 3)()
+    _check(lib().sf_alu_peaks(float(seconds), out, _stream(stream)), "sf_alu_peaks")
+    return tuple(out)
 
 
 def fit_positions(positions, n_xi=11, stream=None):
