@@ -284,9 +284,19 @@ enum {
                          wait of each CTA gives up at once, no MMA is issued, the copies
                          in flight are still drained before the CTA exits, and every
                          instance reports SF_ETIMEOUT; 0 (default) restores the budget */
-    SF_OPT_TC_RESIDENT = 3  /* read-only: 1 when the plan keeps each CTA's tensor-core
+    SF_OPT_TC_RESIDENT = 3, /* read-only: 1 when the plan keeps each CTA's tensor-core
                          projector rows resident in shared memory (loaded once per solve),
                          0 when they stream through a two-stage ring every projection   */
+    SF_OPT_TC_BATCH = 4  /* the batched tensor-core projection of eq. batch_comp: 1 (default)
+                         lets the plan run G instances of one shape in one thread-block
+                         cluster of G x (CTAs per instance) <= 16 CTAs, when the precision
+                         is SF_BF16 or SF_BF16X3 with SF_PROJ_DENSE, every instance has the
+                         same shape and G divides the batch: each CTA keeps its rows of
+                         P_eta in tensor memory (BF16; with SF_BF16X3 the low parts beneath
+                         the high ones) and one tcgen05.mma chain multiplies them by the
+                         right-hand sides of all G instances (G n_d <= 16 columns); 0 keeps
+                         one instance per cluster.  sf_get_option gives G (0: not used).
+                         Results agree with the per-instance product to rounding order   */
 };
 
 /*

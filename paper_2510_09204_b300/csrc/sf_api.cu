@@ -82,6 +82,7 @@ struct sf_handle {
     DevBuf tcA, tcoff;                 // tensor-core chunks of P_eta for the current cluster size
     int tc_mode = 0, tc_c = 0;
     int cull_req = 1;                  // culled row loops (sf_set_option SF_OPT_CULL)
+    int tcb_req = 1;                   // batched tensor-core projection when eligible (SF_OPT_TC_BATCH)
     int test_timeout = 0;              // SF_OPT_TEST_TIMEOUT: zero polling budget
     int n_slots = 0;
     int64_t xi_total = 0;
@@ -112,6 +113,9 @@ static std::vector<int64_t> tune_key(const sf_desc &d, const std::vector<sf_shap
     return k;
 }
 
+static int plan_with_groups(const sf_handle *h, int B, const int *vn, const int *vo, const int *vH, int cluster,
+                            int threads, Plan *p, int *hc);
+
 static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SF_OK : (e == cudaErrorMemoryAllocation ? SF_ENOMEM : SF_ECUDA); }
 
 #define SF_TRY(expr)                                  \
@@ -121,9 +125,28 @@ static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SF_OK : (e == 
     } while (0)
 
 
+// Instances per cluster of the batched tensor-core projection for C CTAs per instance: the
+// largest G >= 2 that divides the batch, with G C <= 16 CTAs, G n_d <= 16 MMA columns, at
+// most 64 rows of P_eta per CTA, G n_d Lb <= n_d N (the rows fit the CTA's projection
+// buffer) and the operator in tensor memory; 0 when none (BF16 and BF16 x3 with every
+// instance of one shape only).
+static int tcb_groups(int nd, int nxi, int esz, int tc_mode, int n_inst, const int *n, const int *nobs, const int *H, int C)
+{
+    if (esz != 4 || (tc_mode != 2 && tc_mode != 3) || n_inst < 2) return 0;
+    for (int i = 1; i < n_inst; ++i)
+        if (n[i] != n[0] || nobs[i] != nobs[0] || H[i] != H[0]) return 0;
+    const int N = n[0] * nxi;
+    if (tcb_tmem_cols(N) > 512) return 0;
+    for (int G = std::min(n_inst, std::min(kMaxGroupCluster / C, 16 / nd)); G >= 2; --G) {
+        const int Lb = tcb_rows(N, G * C);
+        if (n_inst % G == 0 && Lb <= 64 && G * nd * Lb <= nd * N) return G;
+    }
+    return 0;
+}
+
 int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
                      int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode,
-                     int cull_req, int need_bwd)
+                     int cull_req, int need_bwd, int tcb_req)
 {
     if (proj != SF_PROJ_DENSE) tc_mode = 0;
     Plan p;
@@ -133,32 +156,37 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     int C = csize_req > 0 ? csize_req : std::max(1, num_sms / std::max(1, n_inst));
     C = std::max(1, std::min(std::min(C, kMaxCluster), minH));
     p.csize = C;
+    const int tcb = tcb_req ? tcb_groups(nd, nxi, esz, tc_mode, n_inst, n, nobs, H, C) : 0;
+    p.tcb = tcb;
+    const int st2 = tcb ? -1 : 2;   // the carves' A ring argument: two streaming stages, or groups
     // culled row loops when the candidate lists fit beside a chunk of at least 8 timesteps
+    // (in the adjoint's carve too when the handle keeps checkpoints)
     int cull = cull_req ? 1 : 0;
     for (int i = 0; i < n_inst && cull; ++i) {
         const int h8 = std::min((H[i] + C - 1) / C, 8);
-        const size_t b = (size_t)std::max(forward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h8, 0, esz, tc_mode, 2, 1).total,
-                                          backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h8, 0, esz, tc_mode, 2, 1).total) * esz;
+        const int64_t fb = forward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h8, 0, esz, tc_mode, st2, 1).total;
+        const int64_t bb = need_bwd ? backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h8, 0, esz, tc_mode, st2, 1).total : 0;
+        const size_t b = (size_t)std::max(fb, bb) * esz;
         if (b > (size_t)optin || n[i] > 65535 - 8 || nobs[i] > 65535 - 8) cull = 0;
     }
     p.cull = cull;
     size_t need = 0, need_r = 0;
     int maxL = 0;
-    bool res_ok = tc_mode != 0;
+    bool res_ok = tc_mode != 0 && !tcb;
     std::vector<int> hc_res(n_inst, 1);
     for (int i = 0; i < n_inst; ++i) {
         const int own = (H[i] + C - 1) / C;
         int hc = own;
-        if (tc_mode && tc_ntiles(n[i] * nxi, C) > 8) return SF_EUNSUPPORTED;   // 8 x 128 rows per CTA at most
+        if (tc_mode && !tcb && tc_ntiles(n[i] * nxi, C) > 8) return SF_EUNSUPPORTED;   // 8 x 128 rows per CTA at most
         // the forward's carve, or the larger adjoint carve when the handle keeps checkpoints
         auto bytes = [&](int h, int rows) {
-            const int64_t f = forward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total;
-            const int64_t b = need_bwd ? backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h, rows, esz, tc_mode, 2, cull).total : 0;
+            const int64_t f = forward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h, rows, esz, tc_mode, st2, cull).total;
+            const int64_t b = need_bwd ? backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], h, rows, esz, tc_mode, st2, cull).total : 0;
             return (size_t)std::max(f, b) * esz;
         };
         while (hc > 1 && bytes(hc, 0) > (size_t)optin) --hc;
         if (bytes(hc, 0) > (size_t)optin) return SF_EUNSUPPORTED;
-        if (tc_mode) {   // resident projector chunks, if they fit with a chunk of at least 8 timesteps
+        if (tc_mode && !tcb) {   // resident projector chunks, if they fit with a chunk of at least 8 timesteps
             const int st = tc_stages(tc_mode, n[i] * nxi, C, 1);
             int hr = own;
             auto rbytes = [&](int h) {
@@ -205,7 +233,7 @@ int sf::plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *
     size_t need_b = 0;
     for (int i = 0; i < n_inst; ++i)
         need_b = std::max(need_b, (size_t)backward_carve(nd, nxi, cta_rows(H[i], C), n[i], nobs[i], hc_out[i], p.p_rows, esz, tc_mode,
-                                                         tc_stages(tc_mode, n[i] * nxi, C, p.tc_res), cull).total * esz);
+                                                         tc_stage_arg(tc_mode, tcb, n[i] * nxi, C, p.tc_res), cull).total * esz);
     p.smem_bwd = need_b <= (size_t)optin ? need_b : 0;
     *out = p;
     return SF_OK;
@@ -431,10 +459,8 @@ extern "C" int sf_create(const sf_desc *desc, sf_handle **out)
                 t0 = it->second.second;
             }
         }
-        int prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                               h->smem_optin, c0, t0, &h->plan, h->hc.data(), h->tc_mode, h->cull_req, h->d.ckpt_every > 0);
-        if (prc && c0) prc = plan_forward(nd, nxi, h->esz, desc->proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                                          h->smem_optin, 0, kDefaultThreads, &h->plan, h->hc.data(), h->tc_mode, h->cull_req, h->d.ckpt_every > 0);
+        int prc = plan_with_groups(h, B, vn.data(), vo.data(), vH.data(), c0, t0, &h->plan, h->hc.data());
+        if (prc && c0) prc = plan_with_groups(h, B, vn.data(), vo.data(), vH.data(), 0, kDefaultThreads, &h->plan, h->hc.data());
         if (prc) { destroy_all(h); delete h; return prc; }
     }
 
@@ -585,6 +611,7 @@ static FwdArgs<T> fwd_args(const sf_handle *h, const void *bnd, const void *obs,
     a.status = (int32_t *)h->status_dev.p;
     a.tc_mode = h->tc_mode;
     a.tc_res = h->plan.tc_res;
+    a.tcb = h->plan.tcb;
     a.cost = h->d.cost;
     a.wait_budget = h->test_timeout ? 0u : kWaitLimit;
     a.cull = h->plan.cull;
@@ -715,6 +742,66 @@ extern "C" int sf_solve_backward(sf_handle *h, const void *g_xi_out, const void 
     return SF_OK;
 }
 
+// An empty kernel that only occupies what a CTA of the solver occupies (its threads and
+// shared memory), for asking whether a cluster of that many CTAs can be resident at once.
+__global__ void k_cluster_probe() {}
+
+// True when a cluster of cdim CTAs of `threads` threads and `smem` bytes of shared memory
+// each fits on the device (clusters above 8 CTAs are a non-portable size that the device
+// may not offer).
+static bool cluster_fits(int cdim, int threads, size_t smem)
+{
+    if (cdim <= kMaxCluster) return true;
+    if (cudaFuncSetAttribute(k_cluster_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_cluster_probe, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cdim, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cdim;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_cluster_probe, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n >= 1;
+}
+
+// Plans with instance groups when they are asked for, eligible and fit on the device,
+// else without them.
+static int plan_with_groups(const sf_handle *h, int B, const int *vn, const int *vo, const int *vH, int cluster,
+                            int threads, Plan *p, int *hc)
+{
+    int rc = plan_forward(h->d.n_d, h->d.n_xi, h->esz, h->d.proj, B, vn, vo, vH, h->num_sms, h->smem_optin, cluster,
+                          threads, p, hc, h->tc_mode, h->cull_req, h->d.ckpt_every > 0, h->tcb_req);
+    if (rc == SF_OK && p->tcb) {
+        // tcgen05.alloc waits while the SM lacks free columns, so the CTAs that can share an
+        // SM must not ask for more than its 512 together (else two CTAs of one cluster could
+        // wait on each other): the shared-memory request bounds the CTAs per SM.
+        int dev = 0, smem_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        const int per_sm = 512 / (int)tcb_tmem_cols(vn[0] * h->d.n_xi);
+        const size_t floor_b = (size_t)smem_sm / (size_t)(per_sm + 1) + 1;
+        p->smem_fwd = std::max(p->smem_fwd, floor_b);
+        if (p->smem_bwd) p->smem_bwd = std::max(p->smem_bwd, floor_b);
+        if (smem_sm <= 0 || p->smem_fwd > (size_t)h->smem_optin || p->smem_bwd > (size_t)h->smem_optin ||
+            !cluster_fits(p->tcb * p->csize, p->threads, std::max(p->smem_fwd, p->smem_bwd)))
+            rc = plan_forward(h->d.n_d, h->d.n_xi, h->esz, h->d.proj, B, vn, vo, vH, h->num_sms, h->smem_optin, cluster,
+                              threads, p, hc, h->tc_mode, h->cull_req, h->d.ckpt_every > 0, 0);
+    }
+    return rc;
+}
+
 extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
 {
     if (!h || cluster < 0 || cluster > kMaxCluster || threads < 0 || threads > max_threads(h->esz) || threads % 32 ||
@@ -728,8 +815,8 @@ extern "C" int sf_set_launch(sf_handle *h, int32_t cluster, int32_t threads)
         vH[i] = h->shp[i].H;
     }
     Plan p;
-    int rc = plan_forward(h->d.n_d, h->d.n_xi, h->esz, h->d.proj, B, vn.data(), vo.data(), vH.data(), h->num_sms,
-                          h->smem_optin, cluster, threads ? threads : kDefaultThreads, &p, hc.data(), h->tc_mode, h->cull_req, h->d.ckpt_every > 0);
+    int rc = plan_with_groups(h, B, vn.data(), vo.data(), vH.data(), cluster, threads ? threads : kDefaultThreads, &p,
+                              hc.data());
     if (rc) return rc;
     SF_TRY(cudaDeviceSynchronize());
     h->plan = p;
@@ -884,6 +971,14 @@ extern "C" int sf_set_option(sf_handle *h, int32_t option, int32_t value)
         if (rc) h->cull_req = keep;
         return rc;
     }
+    if (option == SF_OPT_TC_BATCH) {
+        if (value != 0 && value != 1) return SF_EINVAL;
+        const int keep = h->tcb_req;
+        h->tcb_req = value;
+        const int rc = sf_set_launch(h, h->plan.csize, h->plan.threads);
+        if (rc) h->tcb_req = keep;
+        return rc;
+    }
     return SF_EINVAL;
 }
 
@@ -900,6 +995,10 @@ extern "C" int sf_get_option(const sf_handle *h, int32_t option, int32_t *value)
     }
     if (option == SF_OPT_TC_RESIDENT) {
         *value = h->plan.tc_res;
+        return SF_OK;
+    }
+    if (option == SF_OPT_TC_BATCH) {
+        *value = h->plan.tcb;
         return SF_OK;
     }
     return SF_EINVAL;

@@ -39,12 +39,14 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     const FwdArgs<T> &A = B.f;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
-    const int C = A.csize, cr = (int)cl.block_rank();
-    const int w = blockIdx.x / C;
+    // C CTAs per instance; with instance groups a cluster of G C CTAs serves G instances
+    const int C = A.csize, G = A.tcb > 0 ? A.tcb : 1, CC = G * C, crc = (int)cl.block_rank();
+    const int grp = crc / C, cr = crc - grp * C;
+    const int w = (blockIdx.x / CC) * G + grp;
     const int ii = A.order ? A.order[w] : w;
     const Inst<T> I0 = A.inst[ii];
     const BwdCarve cv = backward_carve(ND, NXI > 0 ? NXI : A.nxi, cta_rows(I0.H, A.csize), I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
-                                    tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
+                                    tc_stage_arg(A.tc_mode, A.tcb, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
 #ifdef SF_BOUNDS_CHECK
     {   // the carve must fit the launch's dynamic shared memory (the same in every CTA)
         uint32_t dsm;
@@ -57,6 +59,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
 #endif
     Cta<T, ND, TC, NXI, MODE> X;
     X.init(A, smem_raw, cv.f, ii, cr, C);
+    X.set_group(grp, G, crc, CC);
     X.load_constants(A, A.p_rows);
     X.tc_setup(A, smem_raw);
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -80,9 +83,11 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
     const bool fps = wfp != T(0);                         // block-uniform
     const bool need_l = ce > 1 || fps;                    // lambda of each iterate is read
 
-    // seed from dL/d||r_p(xi_bar^L)||^2: gradient w r_1-weighted rows (w = 2 dL/d||r_p||^2)
+    // seed from dL/d||r_p(xi_bar^L)||^2: gradient w r_1-weighted rows (w = 2 dL/d||r_p||^2);
+    // with instance groups every instance of the cluster takes this branch (its barriers)
+    // whenever the seed array is given, whatever its own weight
     const T wseed = B.grp2 ? T(2.0 * B.grp2[ii]) : T(0);
-    if (wseed != T(0)) {
+    if (wseed != T(0) || (G > 1 && B.grp2)) {
         for (int e = tid; e < NN; e += nt) X.xb[e] = A.ck_x[(int64_t)A.ck_final * A.ck_slot + off + e];
         T *gme = X.gp + (step & 1) * X.gstride;
         ++step;
@@ -94,14 +99,14 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             X.positions(k0, hcc, X.xb);
             X.sync_lists();
             X.cull_lists(k0, hcc);
-            X.rows_adjoint(k0, hcc, Rs, wseed);
+            X.rows_adjoint(k0, hcc, Rs, wseed, true);
             __syncthreads();
             X.wt_acc(k0, hcc, X.Rb, gme);
         }
         cl.sync();
         for (int e = tid; e < NN; e += nt) {
             T s = T(0);
-            for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, q)[e];
+            for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, X.gb + q)[e];
             xs[e] += s;
         }
     }
@@ -228,14 +233,14 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
                 X.positions2(k0, hcc, xl, gs, Rs);
                 X.sync_lists();
                 X.cull_lists(k0, hcc);
-                X.rows_adjoint(k0, hcc, Rs, T(0));
+                X.rows_adjoint(k0, hcc, Rs, T(0), false);
                 __syncthreads();
                 X.wt_acc(k0, hcc, X.Rb, gme);
             }
             cl.sync();
             for (int e = tid; e < NN; e += nt) {
                 T s = T(0);
-                for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, q)[e];
+                for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, X.gb + q)[e];
                 T x = xn[e] + s;
                 if (fps) {   // and its share of z^l: - 2 w (z^{l+1} - z^l); z^l becomes the next z^{l+1}
                     x -= T(2) * wfp * (xq[e] - xl[e]);
@@ -276,12 +281,12 @@ static cudaError_t go_backward(const BwdArgs<T> &a, int nxi, int ni, int cs, int
     const auto &f = a.f;
     if (f32 && nxi == 11 && f.nbc == 2 && f.cull && f.cost == SF_COST_PROJECTION) {
         if (f.proj == SF_PROJ_DENSE)
-            return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 2 : 0>, a, ni, cs, threads, smem, s);
-        if (!TC) return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 1 : 0>, a, ni, cs, threads, smem, s);
+            return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 2 : 0>, a, ni, cs, a.f.tcb, threads, smem, s);
+        if (!TC) return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 1 : 0>, a, ni, cs, a.f.tcb, threads, smem, s);
     }
     if (f32 && !TC && nxi == 11 && f.nbc == 2 && f.cull && f.cost == SF_COST_SMOOTHNESS && f.proj == SF_PROJ_STRUCTURED)
-        return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 3 : 0>, a, ni, cs, threads, smem, s);
-    return launch_cluster(k_backward<T, ND, MAXT, TC, 0, 0>, a, ni, cs, threads, smem, s);
+        return launch_cluster(k_backward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 3 : 0>, a, ni, cs, a.f.tcb, threads, smem, s);
+    return launch_cluster(k_backward<T, ND, MAXT, TC, 0, 0>, a, ni, cs, a.f.tcb, threads, smem, s);
 }
 
 // Launch for one dimension: tensor-core projection or not, 512- or 1024-thread CTAs.

@@ -33,12 +33,14 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
-    const int C = A.csize, cr = (int)cl.block_rank();
-    const int w = blockIdx.x / C;
+    // C CTAs per instance; with instance groups a cluster of G C CTAs serves G instances
+    const int C = A.csize, G = A.tcb > 0 ? A.tcb : 1, CC = G * C, crc = (int)cl.block_rank();
+    const int grp = crc / C, cr = crc - grp * C;
+    const int w = (blockIdx.x / CC) * G + grp;
     const int ii = A.order ? A.order[w] : w;
     const Inst<T> I0 = A.inst[ii];
     const FwdCarve cv = forward_carve(ND, NXI > 0 ? NXI : A.nxi, cta_rows(I0.H, A.csize), I0.n, I0.n_obs, I0.hc, A.p_rows, (int)sizeof(T), A.tc_mode,
-                                    tc_stages(A.tc_mode, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
+                                    tc_stage_arg(A.tc_mode, A.tcb, I0.n * A.nxi, A.csize, A.tc_res), A.cull);
 #ifdef SF_BOUNDS_CHECK
     {   // the carve must fit the launch's dynamic shared memory (the same in every CTA)
         uint32_t dsm;
@@ -51,6 +53,7 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
 #endif
     Cta<T, ND, TC, NXI, MODE> X;
     X.init(A, smem_raw, cv, ii, cr, C);
+    X.set_group(grp, G, crc, CC);
     X.load_constants(A, A.p_rows);
     X.tc_setup(A, smem_raw);
     const int tid = X.tid, nt = X.nt, NN = X.NN;
@@ -151,12 +154,12 @@ static cudaError_t go_forward(const FwdArgs<T> &a, int nxi, int ni, int cs, int 
     const auto &f = a;
     if (f32 && nxi == 11 && f.nbc == 2 && f.cull && f.cost == SF_COST_PROJECTION) {
         if (f.proj == SF_PROJ_DENSE)
-            return launch_cluster(k_forward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 2 : 0>, a, ni, cs, threads, smem, s);
-        if (!TC) return launch_cluster(k_forward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 1 : 0>, a, ni, cs, threads, smem, s);
+            return launch_cluster(k_forward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 2 : 0>, a, ni, cs, a.tcb, threads, smem, s);
+        if (!TC) return launch_cluster(k_forward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 1 : 0>, a, ni, cs, a.tcb, threads, smem, s);
     }
     if (f32 && !TC && nxi == 11 && f.nbc == 2 && f.cull && f.cost == SF_COST_SMOOTHNESS && f.proj == SF_PROJ_STRUCTURED)
-        return launch_cluster(k_forward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 3 : 0>, a, ni, cs, threads, smem, s);
-    return launch_cluster(k_forward<T, ND, MAXT, TC, 0, 0>, a, ni, cs, threads, smem, s);
+        return launch_cluster(k_forward<T, ND, MAXT, TC, f32 ? 11 : 0, f32 ? 3 : 0>, a, ni, cs, a.tcb, threads, smem, s);
+    return launch_cluster(k_forward<T, ND, MAXT, TC, 0, 0>, a, ni, cs, a.tcb, threads, smem, s);
 }
 
 // Launch for one dimension: tensor-core projection or not, 512- or 1024-thread CTAs.

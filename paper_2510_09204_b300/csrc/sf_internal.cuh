@@ -12,6 +12,7 @@ constexpr int kDefaultThreads = 512;
 // Largest CTA of the forward kernel for element size esz: FP64 keeps 128 registers per thread.
 __host__ __device__ constexpr int max_threads(int esz) { return esz == 8 ? 512 : 1024; }
 constexpr int kMaxCluster = 8;     // CTAs per instance (portable cluster size)
+constexpr int kMaxGroupCluster = 16;   // CTAs of a cluster that serves several instances (non-portable size)
 constexpr int kRedDoubles = 100;   // block-reduction scratch of the residual kernel
 
 // One instance as the kernels see it.  Offsets are in elements of T.
@@ -68,6 +69,24 @@ __host__ __device__ inline int tc_ntiles(int N, int C) { return (((N + C - 1) / 
 constexpr int kTcChunkBytes = 128 * 128;   // one 128-row x 128-byte A chunk
 constexpr uint32_t kWaitLimit = 1u << 20;   // polls of a bounded mbarrier wait (tens of ms)
 
+// ---- batched tensor-core projection (instance groups) ------------------------------
+// G instances of one shape share a cluster of G x C CTAs (C per instance for the rows).
+// Each CTA of the cluster keeps Lb = ceil(N / (G C)) rows of P_eta in tensor memory as
+// BF16 (with BF16 x3 the low parts in lanes 64..127 beneath the high parts in 0..63), and
+// one product multiplies them by the right-hand sides of all G instances (G n_d <= 16
+// columns of B: the BF16 high parts; with BF16 x3 the low parts in columns 16..31 of the
+// same operand, so one MMA of N = 32 takes both).
+__host__ __device__ inline int tcb_kpad(int N) { return (N + 15) / 16 * 16; }              // K padded to the MMA's 16
+__host__ __device__ inline int64_t tcb_bbytes(int N) { return 16 * (int64_t)tcb_kpad(N) * 2; }   // 16 columns of B
+__host__ __device__ inline int tcb_dcol(int N) { return (tcb_kpad(N) / 2 + 31) / 32 * 32; }   // accumulator column
+__host__ __device__ inline uint32_t tcb_tmem_cols(int N)
+{
+    uint32_t c = 32;
+    while (c < (uint32_t)(tcb_dcol(N) + 32)) c <<= 1;
+    return c;
+}
+__host__ __device__ inline int tcb_rows(int N, int CC) { return (N + CC - 1) / CC; }
+
 // A ring stages of a CTA: every chunk of its rows when they stay resident in shared
 // memory for the whole launch (res), else two stages that stream from global memory.
 __host__ __device__ inline int tc_stages(int mode, int N, int C, int res)
@@ -81,6 +100,8 @@ __host__ __device__ inline int tc_stages(int mode, int N, int C, int res)
 __host__ __device__ inline int64_t tc_smem_bytes(int mode, int N, int stages)
 {
     if (!mode) return 0;
+    if (stages < 0)   // instance groups: B (high and low parts), the low lanes' staging, barriers
+        return tc_na(mode) * tcb_bbytes(N) + 64 * 16 * 4 + 1024 + 128;
     const int64_t kpad = (int64_t)tc_nk(mode, N) * tc_kc(mode);
     const int64_t b = 16 * kpad * tc_es(mode);
     return (int64_t)stages * kTcChunkBytes * tc_na(mode) + b * tc_na(mode) + b + 1024 + 128;
@@ -181,6 +202,7 @@ struct FwdArgs {
     int nd, nxi, iters, n_inst;
     int nbc;          // boundary rows per robot and axis (every shape of the handle)
     int csize;        // CTAs per instance (thread-block cluster), 1..kMaxCluster
+    int tcb;          // instances per cluster of the batched tensor-core projection (0: one per cluster)
     int p_rows;       // rows of P_eta per CTA staged in shared memory (dense; 0 = global)
     int tc_mode;      // tensor-core projection: 0 none, 1 TF32, 2 BF16, 3 BF16 x3
     int tc_res;       // the CTA's projector chunks stay resident in shared memory
@@ -244,6 +266,7 @@ struct ResArgs {
 // Launch geometry shared by every entry point that runs the forward kernel.
 struct Plan {
     int csize = 1;        // CTAs per instance
+    int tcb = 0;          // instances per cluster of the batched tensor-core projection (0: off)
     int threads = kDefaultThreads;
     int p_rows = 0;       // rows of P_eta staged per CTA (dense projection), 0 = read from global
     int tc_res = 0;       // tensor-core projector chunks resident in shared memory
@@ -258,7 +281,13 @@ struct Plan {
 // instance cannot fit in `optin` bytes of shared memory.
 int plan_forward(int nd, int nxi, int esz, int proj, int n_inst, const int *n, const int *nobs, const int *H,
                  int num_sms, int optin, int csize_req, int threads, Plan *out, int *hc_out, int tc_mode = 0,
-                 int cull_req = 1, int need_bwd = 0);
+                 int cull_req = 1, int need_bwd = 0, int tcb_req = 0);
+
+// The A ring stages argument of the carves for a launch (-1: instance groups)
+__host__ __device__ inline int tc_stage_arg(int tc_mode, int tcb, int N, int C, int res)
+{
+    return tcb ? -1 : tc_stages(tc_mode, N, C, res);
+}
 
 // Arranges every shape's P_eta (FP64 pool) into the tensor-core chunk layout for cluster
 // size C: per shape [C][tiles][K chunks][128 x 128 bytes] (x 2 for the BF16 x3 low part).

@@ -185,6 +185,14 @@ struct Cta {
     // scalars, not arrays, so that a runtime stage index keeps the object in registers
     uint32_t tmem_base, tmem_cols, tc_done, tc_seen, tc_fw0, tc_fw1, tc_ld0, tc_ld1, tc_ec0, tc_ec1;
     const unsigned char *tc_src;
+    // instance groups (batched tensor-core projection): gb is the cluster rank of this
+    // instance's first CTA (0 outside groups), crc this CTA's rank among the cluster's CC
+    // CTAs, G the instances per cluster, grp this instance's group; the CTA keeps rows
+    // [tb_rl, tb_rh) of P_eta (Lb per CTA) in tensor memory
+    int gb, CC, crc, G, grp, tcb, Lb, tb_rl, tb_rh, tb_kp, tb_dcol;
+    unsigned char *tb_Bh;
+    float *tb_stage;
+    FDiv fLb;
 
     __device__ __forceinline__ void init(const FwdArgs<T> &A, unsigned char *smem_raw, const FwdCarve &cv, int inst, int rank, int csize)
     {
@@ -251,6 +259,23 @@ struct Cta {
         Prow = nullptr;
         need_b = 0;
         tcm = 0;
+        gb = 0;
+        CC = C;
+        crc = cr;
+        G = 1;
+        grp = 0;
+        tcb = 0;
+    }
+
+    // This CTA serves instance group g of a cluster of ccount CTAs (ngroups instances, C
+    // CTAs each) as cluster rank crank.
+    __device__ __forceinline__ void set_group(int g, int ngroups, int crank, int ccount)
+    {
+        gb = g * C;
+        grp = g;
+        G = ngroups;
+        crc = crank;
+        CC = ccount;
     }
 
     // Tensor-core projection set-up: barriers, the zeroed B operand and a tensor-memory
@@ -260,6 +285,10 @@ struct Cta {
         if constexpr (TC && sizeof(T) == 4) {
             tcm = dense ? A.tc_mode : 0;
             if (!tcm) return;
+            if (A.tcb) {
+                tcb_setup(A, smem_raw);
+                return;
+            }
             tc_es = sf::tc_es(tcm);
             tc_nK = tc_nk(tcm, N);
             tc_nT = tc_ntiles(N, C);
@@ -863,11 +892,11 @@ struct Cta {
 
     // Adjoint of rows(): with R* (vector layout Rs[i][kl]) the adjoint of R, writes
     // p* = sum over active rows of J' (R*_i - R*_j) (pairs), J' R*_i (obstacles) and the
-    // box mask times R*_i, to Rb[ax][i][kl].  seed_w > 0 instead differentiates
-    // seed_w / 2 * ||r_p||^2: y = seed_w r_1 on every active row and seed_w (u+ - l+) on the box.
-    __device__ __forceinline__ void rows_adjoint(int k0, int hcc, const VP *Rs, T seed_w)
+    // box mask times R*_i, to Rb[ax][i][kl].  seed instead differentiates
+    // seed_w / 2 * ||r_p||^2: y = seed_w r_1 on every active row and seed_w (u+ - l+) on the box
+    // (Rs is not read; seed_w = 0 gives zeros).
+    __device__ __forceinline__ void rows_adjoint(int k0, int hcc, const VP *Rs, T seed_w, bool seed)
     {
-        const bool seed = seed_w != T(0);
         const int items = n * hcc, segS = seg_len(hcc);
         FDiv fh, fS;
         fh.set(hcc);
@@ -1095,6 +1124,261 @@ struct Cta {
         }
     }
 
+    // Instance-group set-up: B (high and low BF16 parts, zeroed once: the K padding and the
+    // unused columns must hold finite values), W'W for the refinement, the commit barrier,
+    // tensor memory, and this CTA's rows of P_eta written into it: row r of [tb_rl, tb_rh)
+    // in lane r (BF16 high part) and, with BF16 x3, lane 64 + r (the low part, the
+    // remainder rounded to BF16), two K elements per 32-bit column.  All threads call it.
+    __device__ __forceinline__ void tcb_setup(const FwdArgs<T> &A, unsigned char *smem_raw)
+    {
+        if constexpr (TC && sizeof(T) == 4) {
+            tcb = 1;
+            tc_na = sf::tc_na(tcm);
+            wbud = A.wait_budget;
+            Lb = tcb_rows(N, CC);
+            fLb.set(Lb);
+            tb_rl = min(N, crc * Lb);
+            tb_rh = min(N, tb_rl + Lb);
+            tb_kp = tcb_kpad(N);
+            tb_dcol = tcb_dcol(N);
+            const int64_t bb = tcb_bbytes(N);
+            tb_Bh = smem_raw;
+            tb_stage = reinterpret_cast<float *>(smem_raw + tc_na * bb);
+            unsigned char *bars = smem_raw + tc_na * bb + 64 * 16 * 4;
+            tc_bar = reinterpret_cast<uint64_t *>(bars);
+            tc_flag = reinterpret_cast<int *>(bars + 40);
+            tc_slot = reinterpret_cast<uint32_t *>(bars + 44);
+            for (int e = tid; e < (int)(tc_na * bb / 4); e += nt) reinterpret_cast<uint32_t *>(smem_raw)[e] = 0u;
+            for (int e = tid; e < nxi * nxi; e += nt) {   // W'W for the refinement's Hessian products
+                const int u = e / nxi, vv = e - u * nxi;
+                float acc = 0.f;
+                const T *Wg = A.W + S.off_W;
+                for (int k = 0; k < H; ++k) acc += Wg[k * nxi + u] * Wg[k * nxi + vv];
+                wtw[e] = acc;
+            }
+            tc_fw0 = tc_fw1 = tc_ld0 = tc_ld1 = tc_ec0 = tc_ec1 = 0;
+            if (tid == 0) {
+                for (int b = 0; b < 5; ++b) tc::mbar_init(tc_bar + b, 1);
+                *tc_flag = 0;
+                tc::fence_barrier_init();
+            }
+            tmem_cols = tcb_tmem_cols(N);
+            if ((tid >> 5) == 0) {
+                tc::tmem_alloc(tc_slot, tmem_cols);
+                tc::tmem_relinquish();
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            tmem_base = *tc_slot;
+            if (tid < 128) {   // warps 0-3: each writes its own quarter of the lanes
+                const int lane = tid, row = lane & 63, grow = tb_rl + row;
+                const bool lo = lane >= 64, valid = grow < tb_rh && (!lo || tc_na == 2);
+                const T *Pr = A.P + S.off_P + (int64_t)(valid ? grow : 0) * N;
+                const uint32_t taddr = tmem_base + ((uint32_t)(lane & ~31) << 16);
+                for (int j = 0; j < tb_kp / 2; j += 32) {   // 32 columns = 64 K elements per store
+                    uint32_t v[32];
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        uint32_t h2 = 0u;
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int k = 2 * (j + c) + q;
+                            const float p = (valid && k < N) ? (float)Pr[k] : 0.f;
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(p);
+                            const __nv_bfloat16 part = lo ? __float2bfloat16_rn(p - __bfloat162float(hi)) : hi;
+                            h2 |= (uint32_t)__bfloat16_as_ushort(part) << (16 * q);
+                        }
+                        v[c] = h2;
+                    }
+                    tc::tmem_st_x32(taddr + (uint32_t)j, v);
+                }
+                tc::tmem_wait_st();
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            tc_done = tc_seen = 0;
+        }
+    }
+
+    // One batched product: for every instance g of the cluster, rows [tb_rl, tb_rh) of
+    // P~ src_g into dl[(g n_d + ax) Lb + r - tb_rl].  src is every CTA's own instance's
+    // vector (all CTAs of an instance hold the same values); the CTA reads instance g's from
+    // the CTA of group g with its own in-group rank.  Begins and ends with a cluster
+    // barrier (the sources complete; every CTA's rows complete).  A wait that runs out sets
+    // the sticky flag; the control flow of every thread stays the same.  hi_b: B as its BF16
+    // high parts only (a refinement's residual, already 2^-16 of the right-hand side, needs
+    // no more: its product then carries about 2^-24 of the result's size).
+    __device__ __forceinline__ void tcb_product(cg::cluster_group &cl, const T *src, bool hi_b = false)
+    {
+        if constexpr (TC && sizeof(T) == 4) {
+            cl.sync();
+            const int SBO = tb_kp * 16;   // bytes between groups of 8 B columns
+            const int na = hi_b ? 1 : tc_na, lo_off = 2 * SBO;   // the low parts: columns 16.. (two groups on)
+            // the sources as 16-byte remote loads, kU of them in flight per thread before any
+            // is converted (src is 32-byte aligned and padded to 8 floats, so the last vector
+            // stays inside it)
+            constexpr int kU = 4;
+            if ((N & 3) == 0) {   // four consecutive k of one axis per vector: 8-byte stores
+                const int NV = N >> 2, tot = G * ND * NV;
+                for (int b0 = tid; b0 < tot; b0 += nt * kU) {
+                    float4 x4[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int idx = b0 + u * nt;
+                        if (idx < tot) {
+                            const int g = idx / (ND * NV), r = idx - g * ND * NV;
+                            x4[u] = reinterpret_cast<const float4 *>(cl.map_shared_rank(src, g * C + cr))[r];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int idx = b0 + u * nt;
+                        if (idx >= tot) continue;
+                        const int gc = idx / NV, q = idx - gc * NV, k0 = 4 * q;   // gc = g n_d + ax: the B column
+                        const int off = (gc >> 3) * SBO + (k0 >> 3) * 128 + (gc & 7) * 16 + (k0 & 7) * 2;
+                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(x4[u].x, x4[u].y);
+                        const __nv_bfloat162 h23 = __floats2bfloat162_rn(x4[u].z, x4[u].w);
+                        uint2 hv;
+                        hv.x = *reinterpret_cast<const uint32_t *>(&h01);
+                        hv.y = *reinterpret_cast<const uint32_t *>(&h23);
+                        *reinterpret_cast<uint2 *>(tb_Bh + off) = hv;
+                        if (na == 2) {
+                            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                            const __nv_bfloat162 l01 = __floats2bfloat162_rn(x4[u].x - f01.x, x4[u].y - f01.y);
+                            const __nv_bfloat162 l23 = __floats2bfloat162_rn(x4[u].z - f23.x, x4[u].w - f23.y);
+                            uint2 lv;
+                            lv.x = *reinterpret_cast<const uint32_t *>(&l01);
+                            lv.y = *reinterpret_cast<const uint32_t *>(&l23);
+                            *reinterpret_cast<uint2 *>(tb_Bh + lo_off + off) = lv;
+                        }
+                    }
+                }
+            } else {
+                for (int e = tid; e < G * NN; e += nt) {
+                    const int g = e / NN, rem = e - g * NN, ax = fN.q(rem), k = rem - ax * N, col = g * ND + ax;
+                    const float x = (float)cl.map_shared_rank(src, g * C + cr)[rem];
+                    const int off = (col >> 3) * SBO + (k >> 3) * 128 + (col & 7) * 16 + (k & 7) * 2;
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                    *reinterpret_cast<__nv_bfloat16 *>(tb_Bh + off) = hi;
+                    if (na == 2)
+                        *reinterpret_cast<__nv_bfloat16 *>(tb_Bh + lo_off + off) = __float2bfloat16_rn(x - __bfloat162float(hi));
+                }
+            }
+            tc::fence_async_shared();
+            __syncthreads();
+            const bool failed = *tc_flag != 0;
+            if (!failed && tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t idesc = tc::instr_desc(1u, 128, na == 2 ? 32 : 16);
+                const uint32_t bh = tc::smem_u32(tb_Bh), d = tmem_base + (uint32_t)tb_dcol;
+                for (int j = 0; j < tb_kp / 16; ++j)   // K = 16 per MMA: 8 columns of A, 256 bytes of B
+                    tc::mma_bf16_ta(d, tmem_base + 8u * j, tc::smem_desc(bh + 256u * j, 128, SBO), idesc, j > 0 ? 1u : 0u);
+                tc::mma_commit(tc_bar + 4);
+            }
+            bool ok = !failed;
+            if (!failed) {
+                ok = tc::mbar_wait(tc_bar + 4, tc_done & 1, wbud);
+                ++tc_done;
+                if (ok) tc_seen = tc_done;
+            }
+            ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+            if (!ok && (tid & 31) == 0) *tc_flag = 1;
+            tc::fence_after_sync();
+            // D: lanes 0..63 hold A's high parts' rows, 64..127 its low parts' (BF16 x3);
+            // columns 0..15 the products with B's high parts, 16..31 with its low parts
+            const int wp = tid >> 5, rows = tb_rh - tb_rl, ncol = G * ND, la = tc_na;
+            float dv[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) dv[q] = 0.f;
+            if (wp < 4 && ok) {
+                const uint32_t ta = tmem_base + ((uint32_t)(32 * wp) << 16) + (uint32_t)tb_dcol;
+                tc::tmem_ld_x16(ta, dv);
+                if (na == 2) {
+                    float dl2[16];
+                    tc::tmem_ld_x16(ta + 16u, dl2);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) dv[q] += dl2[q];
+                }
+            }
+            if (la == 2 && (wp == 2 || wp == 3))   // A's low parts' rows, tid - 64
+                for (int q = 0; q < 16; ++q) tb_stage[(tid - 64) * 16 + q] = dv[q];
+            __syncthreads();
+            if (wp < 2 && tid < rows)
+                for (int q = 0; q < ncol; ++q) dl[q * Lb + tid] = (T)(dv[q] + (la == 2 ? tb_stage[tid * 16 + q] : 0.f));
+            tc::fence_before_sync();
+            cl.sync();
+        }
+    }
+
+    // dst = this instance's P~ src (rows gathered from the CTAs of the cluster that own
+    // them), then P_b (b - A xi_bar) when corr_b, then n_refine passes of
+    // dst += P~ (src - H dst).  Ends with a barrier: every element of dst is valid for
+    // every thread.
+    __device__ __forceinline__ void tcb_project(cg::cluster_group &cl, const T *src, T *dst, bool corr_b)
+    {
+        if constexpr (TC && sizeof(T) == 4) {
+            auto gather = [&](bool add) {
+                if ((N & 3) == 0 && (Lb & 3) == 0) {   // four rows of one owner per 16-byte remote load
+                    constexpr int kU = 4;
+                    const int tot = NN >> 2;
+                    for (int b0 = tid; b0 < tot; b0 += nt * kU) {
+                        float4 x4[kU];
+#pragma unroll
+                        for (int u = 0; u < kU; ++u) {
+                            const int idx = b0 + u * nt;
+                            if (idx < tot) {
+                                const int e = 4 * idx, ax = fN.q(e), row = e - ax * N, own = fLb.q(row);
+                                x4[u] = *reinterpret_cast<const float4 *>(cl.map_shared_rank(dl, own) + (grp * ND + ax) * Lb +
+                                                                          row - own * Lb);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kU; ++u) {
+                            const int idx = b0 + u * nt;
+                            if (idx >= tot) continue;
+                            float4 *o = reinterpret_cast<float4 *>(dst) + idx;
+                            if (add) {
+                                float4 y = *o;
+                                y.x += x4[u].x; y.y += x4[u].y; y.z += x4[u].z; y.w += x4[u].w;
+                                *o = y;
+                            } else {
+                                *o = x4[u];
+                            }
+                        }
+                    }
+                    return;
+                }
+                for (int e = tid; e < NN; e += nt) {
+                    const int ax = fN.q(e), row = e - ax * N, own = fLb.q(row);
+                    const T x = cl.map_shared_rank(dl, own)[(grp * ND + ax) * Lb + row - own * Lb];
+                    dst[e] = add ? dst[e] + x : x;
+                }
+            };
+            tcb_product(cl, src);
+            gather(false);
+            __syncthreads();
+            if (corr_b) {   // the first step from an iterate that misses A xi = b
+                const int m = nbc * n;
+                for (int e = tid; e < NN; e += nt) {
+                    const int ax = fN.q(e), row = e - ax * N;
+                    T a = T(0);
+                    for (int q = 0; q < m; ++q) a += Pbg[(int64_t)row * m + q] * db[ax * n * nbc + q];
+                    dst[e] += a;
+                }
+            }
+            for (int pass = 0; pass < n_refine; ++pass) {
+                __syncthreads();
+                refine_residual(src, dst);
+                __syncthreads();
+                tcb_product(cl, rr, true);
+                gather(true);
+            }
+            __syncthreads();   // the vector gathers write elements other threads own
+        }
+    }
+
     // true when a bounded wait of the tensor-core pipeline ran out in this CTA
     __device__ __forceinline__ bool tc_timed_out() const
     {
@@ -1102,49 +1386,59 @@ struct Cta {
         return false;
     }
 
+    // The refinement residual rr = src - H dst on the coefficients A leaves free, in FP32
+    // through H = I (x) C + rho ((n + n_obs + 2) I - 11') (x) W'W, C the cost block (the
+    // Kronecker structure of eq. batch_comp's matrix).  Barriers between its two phases only.
+    __device__ __forceinline__ void refine_residual(const T *src, const T *dst)
+    {
+        T *sums = wtw + nxi * nxi;   // [ND][nxi] robot sums of dst
+        const int lane = tid & 31, nw = nt >> 5;
+        for (int pq = tid >> 5; pq < ND * nxi; pq += nw) {
+            const int ax = pq / nxi, c = pq - ax * nxi;
+            T sacc = T(0);
+            for (int i = lane; i < n; i += 32) sacc += dst[(ax * n + i) * nxi + c];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            if (lane == 0) sums[pq] = sacc;
+        }
+        __syncthreads();
+        const T cn = T(n + n_obs_ + 2);
+        for (int e = tid; e < NN; e += nt) {
+            const int r = e / nxi, u = e - r * nxi, ax = fn.q(r);
+            T hv = T(0), cd = smooth ? T(0) : dst[e];   // C dst: identity or the smoothness block
+            for (int c = 0; c < nxi; ++c) {
+                hv += wtw[u * nxi + c] * (cn * dst[r * nxi + c] - sums[ax * nxi + c]);
+                if (smooth) cd += Qc[u * nxi + c] * dst[r * nxi + c];
+            }
+            const T res = src[e] - (cd + rho * hv);
+            rr[e] = fixed_c(u) ? T(0) : res;
+        }
+    }
+
     // dst = P_eta src (+ P_b db when corr_b); dst[e] is valid for the elements e this
     // thread owns (e = tid + j nt).  src and dst must differ from each other and from dl.
     __device__ __forceinline__ void project(cg::cluster_group &cl, const T *src, T *dst, bool corr_b)
     {
-        if (TC && dense && tcm) {
+        if (TC && dense && tcm && tcb) {
+            tcb_project(cl, src, dst, corr_b);
+        } else if (TC && dense && tcm) {
             tc_rows(src, corr_b);
             cl.sync();
             for (int e = tid; e < NN; e += nt) {
                 const int row = e - fN.q(e) * N;
-                dst[e] = cl.map_shared_rank(dl, fL.q(row))[e];
+                dst[e] = cl.map_shared_rank(dl, gb + fL.q(row))[e];
             }
             // refinement: dst += P~ (src - H dst) on the interior coefficients, the residual in
             // FP32 through H = I (x) C + rho ((n + n_obs + 2) I - 11') (x) W'W, C the cost block
             for (int pass = 0; pass < n_refine; ++pass) {
                 __syncthreads();
-                T *sums = wtw + nxi * nxi;   // [ND][nxi] robot sums of dst
-                const int lane = tid & 31, nw = nt >> 5;
-                for (int pq = tid >> 5; pq < ND * nxi; pq += nw) {
-                    const int ax = pq / nxi, c = pq - ax * nxi;
-                    T sacc = T(0);
-                    for (int i = lane; i < n; i += 32) sacc += dst[(ax * n + i) * nxi + c];
-#pragma unroll
-                    for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-                    if (lane == 0) sums[pq] = sacc;
-                }
-                __syncthreads();
-                const T cn = T(n + n_obs_ + 2);
-                for (int e = tid; e < NN; e += nt) {
-                    const int r = e / nxi, u = e - r * nxi, ax = fn.q(r);
-                    T hv = T(0), cd = smooth ? T(0) : dst[e];   // C dst: identity or the smoothness block
-                    for (int c = 0; c < nxi; ++c) {
-                        hv += wtw[u * nxi + c] * (cn * dst[r * nxi + c] - sums[ax * nxi + c]);
-                        if (smooth) cd += Qc[u * nxi + c] * dst[r * nxi + c];
-                    }
-                    const T res = src[e] - (cd + rho * hv);
-                    rr[e] = fixed_c(u) ? T(0) : res;
-                }
+                refine_residual(src, dst);
                 __syncthreads();
                 tc_rows(rr, false);
                 cl.sync();
                 for (int e = tid; e < NN; e += nt) {
                     const int row = e - fN.q(e) * N;
-                    dst[e] += cl.map_shared_rank(dl, fL.q(row))[e];
+                    dst[e] += cl.map_shared_rank(dl, gb + fL.q(row))[e];
                 }
             }
         } else if (dense) {
@@ -1184,7 +1478,7 @@ struct Cta {
             cl.sync();
             for (int e = tid; e < NN; e += nt) {
                 const int row = e - fN.q(e) * N;
-                dst[e] = cl.map_shared_rank(dl, fL.q(row))[e];
+                dst[e] = cl.map_shared_rank(dl, gb + fL.q(row))[e];
             }
         } else {
             // Kronecker form, per axis with robot mean m of src:
@@ -1297,7 +1591,7 @@ struct Cta {
         T a = T(0), b = T(0), c = T(0);
         for (int idx = lane; idx < C * nw; idx += 32) {
             const int q = idx / nw, w = idx - q * nw;
-            const T *g = cl.map_shared_rank(gme, q) + NN + 4 + 3 * w;
+            const T *g = cl.map_shared_rank(gme, gb + q) + NN + 4 + 3 * w;
             a += g[0];
             b = fmax(b, g[1]);
             if (q == cr) c += g[2];
@@ -1324,7 +1618,7 @@ struct Cta {
         T fp = T(0);
         for (int e = tid; e < NN; e += nt) {
             T gg = T(0);
-            for (int q = 0; q < C; ++q) gg += cl.map_shared_rank(gme, q)[e];
+            for (int q = 0; q < C; ++q) gg += cl.map_shared_rank(gme, gb + q)[e];
             const T ln = lam[e] - rho * gg;
             const T dlam = ln - lam[e];
             fp += dlam * dlam;
@@ -1348,13 +1642,20 @@ struct Cta {
     }
 };
 
-// Launches n_inst clusters of csize CTAs of `kernel` with `smem` bytes of dynamic shared memory.
+// Launches n_inst instances of csize CTAs each of `kernel` with `smem` bytes of dynamic
+// shared memory, in clusters of group instances (group csize CTAs; above 8 a non-portable
+// cluster size).
 template <typename K, typename Arg>
-inline cudaError_t launch_cluster(K kernel, const Arg &a, int n_inst, int csize, int threads, size_t smem,
+inline cudaError_t launch_cluster(K kernel, const Arg &a, int n_inst, int csize, int group, int threads, size_t smem,
                                   cudaStream_t s)
 {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    const int cdim = csize * (group > 1 ? group : 1);
+    if (cdim > kMaxCluster) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(n_inst * csize), 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -1362,7 +1663,7 @@ inline cudaError_t launch_cluster(K kernel, const Arg &a, int n_inst, int csize,
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)csize;
+    attr[0].val.clusterDim.x = (unsigned)cdim;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;

@@ -148,8 +148,8 @@ template <typename T>
 static cudaError_t launch_residual_t(const ResArgs<T> &a, int threads, size_t smem, cudaStream_t s)
 {
     if (a.n_inst < 1 || a.csize < 1 || a.csize > kMaxCluster) return cudaErrorInvalidValue;
-    if (a.nd == 2) return launch_cluster(k_residual<T, 2>, a, a.n_inst, a.csize, threads, smem, s);
-    return launch_cluster(k_residual<T, 3>, a, a.n_inst, a.csize, threads, smem, s);
+    if (a.nd == 2) return launch_cluster(k_residual<T, 2>, a, a.n_inst, a.csize, 1, threads, smem, s);
+    return launch_cluster(k_residual<T, 3>, a, a.n_inst, a.csize, 1, threads, smem, s);
 }
 
 cudaError_t launch_residual(const ResArgs<double> &a, int threads, size_t smem, cudaStream_t s)

@@ -68,6 +68,7 @@ SCRIPT = textwrap.dedent("""
         run(uneven, "fp32", proj, 40)
     run(c2, "tf32", "dense", 40)
     run(aniso, "bf16x3", "dense", 30)
+    run(c2, "bf16x3", "dense", 30, cluster=4)   # four instances in one cluster: the batched product
     print("bounds-checked runs: no violation")
 """)
 

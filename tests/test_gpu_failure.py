@@ -18,7 +18,7 @@ import torch
 
 import sfgen
 from paper_2510_09204_b300 import SFSolver, SFError
-from paper_2510_09204_b300.sf import (SF_OPT_TEST_TIMEOUT, SF_OPT_TC_RESIDENT, SF_ENOMEM, SF_ETIMEOUT,
+from paper_2510_09204_b300.sf import (SF_OPT_TEST_TIMEOUT, SF_OPT_TC_RESIDENT, SF_OPT_TC_BATCH, SF_ENOMEM, SF_ETIMEOUT,
                                       SF_ENONFINITE, lib, sf_desc, sf_shape, PRECISIONS, PROJECTIONS, COSTS)
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +47,8 @@ CASES = {
     "resident": (lambda: [sfgen.custom_instance(n=4, n_obs=2, H=20, seed=s, extent=6.0) for s in range(3)], 0),
     # 32 robots on one CTA: the 352 x 352 projector streams through the ring
     "streaming": (lambda: [sfgen.custom_instance(n=32, n_obs=8, H=40, seed=s, extent=10.0) for s in range(2)], 1),
+    # four instances of one shape in a 16-CTA cluster: the batched product, P_eta in tensor memory
+    "batched": (lambda: sfgen.make_batch(2, B=4), 4),
 }
 
 
@@ -59,8 +61,10 @@ def test_zero_wait_budget_reports_timeout_and_the_handle_recovers(case, precisio
                  max_iters=8, ckpt_every=1)
     if cluster:
         s.set_launch(cluster, 0)
-    expect_res = 1 if case == "resident" else 0
+    batched = case == "batched" and precision == "bf16x3"   # TF32 is never batched: per instance there
+    expect_res = 1 if case == "resident" or (case == "batched" and not batched) else 0
     assert s.option(SF_OPT_TC_RESIDENT) == expect_res
+    assert s.option(SF_OPT_TC_BATCH) == (4 if batched else 0)
     fresh = _solve(s, insts, 8, backward=True)
     assert (fresh["status"] == 0).all()
 

@@ -7,6 +7,7 @@ import torch
 
 import sfgen
 from paper_2510_09204_b300 import SF_NRES, SFSolver
+from paper_2510_09204_b300.sf import SF_OPT_TC_BATCH
 
 pytestmark = pytest.mark.gpu
 RHO = 0.3
@@ -42,12 +43,16 @@ class Step:
 
 
 @pytest.mark.parametrize("precision,proj,n_refine", [("fp32", "dense", 0), ("fp64", "structured", 0),
-                                                     ("bf16x3", "dense", 1)])
+                                                     ("bf16x3", "dense", 1), ("bf16x3+batched", "dense", 1)])
 def test_graph_replay_matches_eager(precision, proj, n_refine):
-    insts = uneven_batch()
+    batched = precision.endswith("+batched")
+    precision = precision.split("+")[0]
+    insts = sfgen.make_batch(2, B=8) if batched else uneven_batch()
     s = SFSolver(insts, 2, 11, rho=RHO, precision=precision, proj=proj, max_iters=ITERS, ckpt_every=10,
                  n_refine=n_refine)
     s.autotune(s.pack(insts), s.pack(insts)["xi"], ITERS, reps=1)
+    if batched:
+        assert s.option(SF_OPT_TC_BATCH) > 1
     data = s.pack(insts)
     st = Step(s, data)
     side = torch.cuda.Stream()
