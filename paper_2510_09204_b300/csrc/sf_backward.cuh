@@ -105,9 +105,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
         }
         cl.sync();
         for (int e = tid; e < NN; e += nt) {
-            T s = T(0);
-            for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, X.gb + q)[e];
-            xs[e] += s;
+            xs[e] += X.csum(cl, gme, e);
         }
     }
     for (int e = tid; e < NN; e += nt) {
@@ -239,9 +237,7 @@ __global__ void __launch_bounds__(MAXT) k_backward(BwdArgs<T> B)
             }
             cl.sync();
             for (int e = tid; e < NN; e += nt) {
-                T s = T(0);
-                for (int q = 0; q < C; ++q) s += cl.map_shared_rank(gme, X.gb + q)[e];
-                T x = xn[e] + s;
+                T x = xn[e] + X.csum(cl, gme, e);
                 if (fps) {   // and its share of z^l: - 2 w (z^{l+1} - z^l); z^l becomes the next z^{l+1}
                     x -= T(2) * wfp * (xq[e] - xl[e]);
                     ls[e] -= T(2) * wfp * (lq[e] - ll[e]);

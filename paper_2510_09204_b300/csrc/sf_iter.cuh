@@ -448,33 +448,44 @@ struct Cta {
         __syncthreads();
     }
 
-    // out[i][kl][ax] = sum_c W[k0 + kl][c] coeff[ax][i][c] (vector layout, one (ax, i, kl) per
-    // thread).  chk: also note in esc whether a value leaves its robot's inflated box.
+    // sum_c wr[c] xr[c] with three partial sums (the order every position is formed in)
+    __device__ __forceinline__ T wdot(const T *wr, const T *xr) const
+    {
+        T s0 = T(0), s1 = T(0), s2 = T(0);
+        int c = 0;
+        for (; c + 2 < nxi; c += 3) {
+            s0 += wr[c] * xr[c];
+            s1 += wr[c + 1] * xr[c + 1];
+            s2 += wr[c + 2] * xr[c + 2];
+        }
+        for (; c < nxi; ++c) s0 += wr[c] * xr[c];
+        return (s0 + s1) + s2;
+    }
+
+    // out[i][kl] = (sum_c W[k0 + kl][c] coeff[ax][i][c])_ax (vector layout, one (i, kl) per
+    // thread, every axis from one load of the basis row).  chk: also note in esc whether a
+    // value leaves its robot's inflated box.
     __device__ __forceinline__ void wvec(int k0, int hcc, const T *coeff, VP *out, bool chk = false)
     {
-        T *o = reinterpret_cast<T *>(out);
         const int S = seg_len(hcc), ns = nseg_of(hcc);
         FDiv fh, fS;
         fh.set(hcc);
         fS.set(S);
-        for (int e = tid; e < ND * n * hcc; e += nt) {
-            const int r = fh.q(e), kl = e - r * hcc, ax = fn.q(r), i = r - ax * n;
+        for (int e = tid; e < n * hcc; e += nt) {
+            const int i = fh.q(e), kl = e - i * hcc;
             const T *wr = W + (k0 + kl) * nxi;
-            const T *xr = coeff + r * nxi;
-            T s0 = T(0), s1 = T(0), s2 = T(0);
-            int c = 0;
-            for (; c + 2 < nxi; c += 3) {
-                s0 += wr[c] * xr[c];
-                s1 += wr[c + 1] * xr[c + 1];
-                s2 += wr[c + 2] * xr[c + 2];
-            }
-            for (; c < nxi; ++c) s0 += wr[c] * xr[c];
-            const T val = (s0 + s1) + s2;
-            o[(i * hcc + kl) * NDP<ND>::v + ax] = val;
+            VP p;
+#pragma unroll
+            for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = T(0);
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) p.v[ax] = wdot(wr, coeff + (ax * n + i) * nxi);
+            out[i * hcc + kl] = p;
             if (chk) {
                 const int sg = fS.q(kl);
-                if (!(val >= bbx[((2 * ax) * ns + sg) * NBX + i] && val <= bbx[((2 * ax + 1) * ns + sg) * NBX + i]))
-                    esc = true;
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax)
+                    if (!(p.v[ax] >= bbx[((2 * ax) * ns + sg) * NBX + i] && p.v[ax] <= bbx[((2 * ax + 1) * ns + sg) * NBX + i]))
+                        esc = true;
             }
         }
     }
@@ -484,37 +495,29 @@ struct Cta {
     // basis rows and the index arithmetic.  The same sums as two wvec calls.
     __device__ __forceinline__ void wvec2(int k0, int hcc, const T *c1, VP *out1, const T *c2, VP *out2, bool chk)
     {
-        T *o1 = reinterpret_cast<T *>(out1), *o2 = reinterpret_cast<T *>(out2);
         const int S = seg_len(hcc), ns = nseg_of(hcc);
         FDiv fh, fS;
         fh.set(hcc);
         fS.set(S);
-        for (int e = tid; e < ND * n * hcc; e += nt) {
-            const int r = fh.q(e), kl = e - r * hcc, ax = fn.q(r), i = r - ax * n;
+        for (int e = tid; e < n * hcc; e += nt) {
+            const int i = fh.q(e), kl = e - i * hcc;
             const T *wr = W + (k0 + kl) * nxi;
-            const T *xr = c1 + r * nxi, *yr = c2 + r * nxi;
-            T s0 = T(0), s1 = T(0), s2 = T(0), t0 = T(0), t1 = T(0), t2 = T(0);
-            int c = 0;
-            for (; c + 2 < nxi; c += 3) {
-                s0 += wr[c] * xr[c];
-                s1 += wr[c + 1] * xr[c + 1];
-                s2 += wr[c + 2] * xr[c + 2];
-                t0 += wr[c] * yr[c];
-                t1 += wr[c + 1] * yr[c + 1];
-                t2 += wr[c + 2] * yr[c + 2];
+            VP p, q;
+#pragma unroll
+            for (int ax = 0; ax < NDP<ND>::v; ++ax) p.v[ax] = q.v[ax] = T(0);
+#pragma unroll
+            for (int ax = 0; ax < ND; ++ax) {
+                p.v[ax] = wdot(wr, c1 + (ax * n + i) * nxi);
+                q.v[ax] = wdot(wr, c2 + (ax * n + i) * nxi);
             }
-            for (; c < nxi; ++c) {
-                s0 += wr[c] * xr[c];
-                t0 += wr[c] * yr[c];
-            }
-            const T val = (s0 + s1) + s2;
-            const int oi = (i * hcc + kl) * NDP<ND>::v + ax;
-            o1[oi] = val;
-            o2[oi] = (t0 + t1) + t2;
+            out1[i * hcc + kl] = p;
+            out2[i * hcc + kl] = q;
             if (chk) {
                 const int sg = fS.q(kl);
-                if (!(val >= bbx[((2 * ax) * ns + sg) * NBX + i] && val <= bbx[((2 * ax + 1) * ns + sg) * NBX + i]))
-                    esc = true;
+#pragma unroll
+                for (int ax = 0; ax < ND; ++ax)
+                    if (!(p.v[ax] >= bbx[((2 * ax) * ns + sg) * NBX + i] && p.v[ax] <= bbx[((2 * ax + 1) * ns + sg) * NBX + i]))
+                        esc = true;
             }
         }
     }
@@ -1562,6 +1565,22 @@ struct Cta {
         return update(cl, gme, corr_b, [] {});
     }
 
+    // Sum over this instance's C CTAs of buf[e] (their copies in distributed shared memory),
+    // in rank order: every remote load is issued before the first addition, so the C
+    // round trips overlap; the same bits in every CTA.
+    __device__ __forceinline__ T csum(cg::cluster_group &cl, const T *buf, int e) const
+    {
+        T x[kMaxCluster];
+#pragma unroll
+        for (int q = 0; q < kMaxCluster; ++q)
+            if (q < C) x[q] = cl.map_shared_rank(buf, gb + q)[e];
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < kMaxCluster; ++q)
+            if (q < C) s += x[q];
+        return s;
+    }
+
     // Per-warp partial statistics into gme[NN + 4 + 3 w + (0, 1, 2)]: sum of rp2, max of mx2,
     // sum of fp over the warp's lanes.
     __device__ __forceinline__ void warp_partials(T *gme, T rp2, T mx2, T fp) const
@@ -1617,8 +1636,7 @@ struct Cta {
     {
         T fp = T(0);
         for (int e = tid; e < NN; e += nt) {
-            T gg = T(0);
-            for (int q = 0; q < C; ++q) gg += cl.map_shared_rank(gme, gb + q)[e];
+            const T gg = csum(cl, gme, e);
             const T ln = lam[e] - rho * gg;
             const T dlam = ln - lam[e];
             fp += dlam * dlam;
