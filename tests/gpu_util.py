@@ -50,6 +50,22 @@ def ulp_perturbed(inst, seed, ulps=1.0):
 SENS_ULPS, SENS_DRAWS = 16, 3
 
 
+def check_positions_per_instance(err, sens, tol=1e-4, factor=10.0, max_excepted=0.15, what=""):
+    """Per-instance bound on FP32 positions against FP64 on the same input, with the
+    exception rule of check_adjoint_per_instance: an instance whose error exceeds tol is
+    excepted only when it stays within factor times that instance's FP64 sensitivity (the
+    largest position change of the FP64 solve over SENS_DRAWS draws of a SENS_ULPS-ulp
+    candidate perturbation), and at most max_excepted of the batch may be excepted."""
+    excepted = [(k, err[k], sens[k]) for k in range(len(err)) if err[k] > tol]
+    bad = [(k, e, s) for k, e, s in excepted if e > factor * s]
+    print("\n%s positions FP32 vs FP64 per instance: max %.2e m, median %.2e m; FP64 sensitivity median %.2e m; "
+          "instances above %.0e m (index, FP32 error, FP64 sensitivity): %s"
+          % (what, max(err), float(np.median(err)), float(np.median(sens)), tol,
+             [(k, "%.1e" % e, "%.1e" % s) for k, e, s in excepted]))
+    assert not bad, bad
+    assert len(excepted) <= max_excepted * len(err), excepted
+
+
 def check_adjoint_per_instance(g32, g64, g64p, tol=1e-3, factor=10.0, max_excepted=0.15, what=""):
     """Per-instance bound on the FP32 adjoint against the FP64 adjoint of the same input.
 

@@ -15,7 +15,8 @@ import torch
 
 import oracle
 import sfgen
-from gpu_util import SENS_DRAWS, SENS_ULPS, check_adjoint_per_instance, max_pos_err, rel, ulp_perturbed
+from gpu_util import (SENS_DRAWS, SENS_ULPS, check_adjoint_per_instance, check_positions_per_instance, max_pos_err,
+                      rel, ulp_perturbed)
 from paper_2510_09204_b300 import SFSolve, SFSolver
 
 pytestmark = pytest.mark.gpu
@@ -88,6 +89,35 @@ def test_uneven_64_instances_fp32_structured():
               % (k, inst["n"], inst["n_obs"], inst["H"], err))
         assert err <= 1e-4
         assert abs(r40[k, 1].item() - oracle.residual(inst, ref["xi"], rho=RHO)[1]) <= 1e-3
+
+
+def test_uneven_64_instances_fp32_against_fp64_per_instance():
+    """Every instance of the uneven batch (200 iterations, the benchmark's launch) against the
+    FP64 GPU solve of the same input as FP32 holds it (FP64 is pinned to the oracle
+    elsewhere), with the per-instance exception rule of check_positions_per_instance."""
+    insts = [rounded32(i) for i in sfgen.make_batch(3)]
+    iters = sfgen.CONFIGS[3].iters
+
+    def run(batch, prec):
+        s, d = tuned(batch, prec, "structured", iters)
+        xo, _, res = s.solve(d, d["xi"], iters)
+        torch.cuda.synchronize()
+        assert (s.status() == 0).all()
+        out = unpack_all(s, xo, len(batch)), res.cpu().numpy()
+        s.close()
+        return out
+
+    x32, r32 = run(insts, "fp32")
+    x64, r64 = run(insts, "fp64")
+    pert = [run([ulp_perturbed(i, 100 * s + k, SENS_ULPS) for k, i in enumerate(insts)], "fp64")[0]
+            for s in range(SENS_DRAWS)]
+    err, sens = [], []
+    for k, inst in enumerate(insts):
+        W = oracle.basis(inst["H"], 11)
+        err.append(max_pos_err(inst, x32[k], x64[k], W))
+        sens.append(max(max_pos_err(inst, p[k], x64[k], W) for p in pert))
+    check_positions_per_instance(err, sens, what="config 3")
+    assert np.abs(r32[:, 1] - r64[:, 1]).max() <= 1e-3
 
 
 def test_differentiable_128_instances_fp64_autograd():
