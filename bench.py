@@ -497,9 +497,20 @@ def _convergence(insts, nd, a, dev, stream, iters=4000, tol=1e-3):
     ms = e0.elapsed_time(e1)
     its = res[:, 3].cpu().numpy()
     ok = its >= 0
+    # the same with SF_OPT_EARLY_EXIT: converged instances stop and free their SMs; the batch
+    # still waits for the instances that never meet the tolerance
+    from paper_2510_09204_b300.sf import SF_OPT_EARLY_EXIT
+    s.set_option(SF_OPT_EARLY_EXIT, 1)
+    s.solve(d, d["xi"], iters, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.solve(d, d["xi"], iters, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms_early = e0.elapsed_time(e1)
     s.close()
     need = int(its[ok].max()) if ok.all() else None
-    return {"iterations": iters, "tol_m": tol, "ms": ms, "frac_converged": float(ok.mean()),
+    return {"iterations": iters, "tol_m": tol, "ms": ms, "ms_early_exit": ms_early, "frac_converged": float(ok.mean()),
             "iters_to_tol_median": float(np.median(its[ok])) if ok.any() else None,
             "iters_to_tol_max": int(its[ok].max()) if ok.any() else None,
             "ms_until_every_instance_converged": ms * need / iters if need is not None else None}

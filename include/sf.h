@@ -287,7 +287,7 @@ enum {
     SF_OPT_TC_RESIDENT = 3, /* read-only: 1 when the plan keeps each CTA's tensor-core
                          projector rows resident in shared memory (loaded once per solve),
                          0 when they stream through a two-stage ring every projection   */
-    SF_OPT_TC_BATCH = 4  /* the batched tensor-core projection of eq. batch_comp: 1 (default)
+    SF_OPT_TC_BATCH = 4, /* the batched tensor-core projection of eq. batch_comp: 1 (default)
                          lets the plan run G instances of one shape in one thread-block
                          cluster of G x (CTAs per instance) <= 16 CTAs, when the precision
                          is SF_BF16 or SF_BF16X3 with SF_PROJ_DENSE, every instance has the
@@ -297,6 +297,15 @@ enum {
                          right-hand sides of all G instances (G n_d <= 16 columns); 0 keeps
                          one instance per cluster.  sf_get_option gives G (0: not used).
                          Results agree with the per-instance product to rounding order   */
+    SF_OPT_EARLY_EXIT = 5 /* 1: an instance stops iterating after the iteration whose iterate
+                         first met max residual <= tol (SF_RES_ITERS); its outputs are the
+                         iterate that iteration produced, and the other instances run on,
+                         so a batch where some instances converge frees their SMs early.
+                         Handles without checkpoints only (SF_EUNSUPPORTED otherwise: the
+                         adjoint differentiates a fixed iteration count); not applied while
+                         instances share clusters (SF_OPT_TC_BATCH, whose instances share
+                         barriers: sf_get_option then reads 0).  0 (default): every
+                         instance runs `iters` iterations                                 */
 };
 
 /*

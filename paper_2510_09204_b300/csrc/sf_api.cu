@@ -84,6 +84,7 @@ struct sf_handle {
     int cull_req = 1;                  // culled row loops (sf_set_option SF_OPT_CULL)
     int tcb_req = 1;                   // batched tensor-core projection when eligible (SF_OPT_TC_BATCH)
     int test_timeout = 0;              // SF_OPT_TEST_TIMEOUT: zero polling budget
+    int early = 0;                     // SF_OPT_EARLY_EXIT
     int n_slots = 0;
     int64_t xi_total = 0;
     // launch configuration
@@ -614,6 +615,7 @@ static FwdArgs<T> fwd_args(const sf_handle *h, const void *bnd, const void *obs,
     a.tcb = h->plan.tcb;
     a.cost = h->d.cost;
     a.wait_budget = h->test_timeout ? 0u : kWaitLimit;
+    a.early = h->early && h->d.ckpt_every == 0 && !h->plan.tcb;
     a.cull = h->plan.cull;
     a.n_refine = h->tc_mode ? h->d.n_refine : 0;
     a.tcA = (const unsigned char *)h->tcA.p;
@@ -971,6 +973,12 @@ extern "C" int sf_set_option(sf_handle *h, int32_t option, int32_t value)
         if (rc) h->cull_req = keep;
         return rc;
     }
+    if (option == SF_OPT_EARLY_EXIT) {
+        if (value != 0 && value != 1) return SF_EINVAL;
+        if (value && h->d.ckpt_every > 0) return SF_EUNSUPPORTED;   // the adjoint needs every iteration
+        h->early = value;
+        return SF_OK;
+    }
     if (option == SF_OPT_TC_BATCH) {
         if (value != 0 && value != 1) return SF_EINVAL;
         const int keep = h->tcb_req;
@@ -999,6 +1007,10 @@ extern "C" int sf_get_option(const sf_handle *h, int32_t option, int32_t *value)
     }
     if (option == SF_OPT_TC_BATCH) {
         *value = h->plan.tcb;
+        return SF_OK;
+    }
+    if (option == SF_OPT_EARLY_EXIT) {
+        *value = h->early && !h->plan.tcb;
         return SF_OK;
     }
     return SF_EINVAL;

@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
     }
     X.boundary_gap();
 
+    __shared__ int s_stop;   // early exit: the instance met the tolerance (set by the statistics warp)
+    if (tid == 0) s_stop = 0;
     int its_tol = -1;
     T fp = T(0), fp_prev = T(0);
     double fp_sum = 0.0;   // sum over the iterations of ||z^{l+1} - z^l||^2
@@ -100,7 +102,10 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
                 if (!last) {
                     if (!isfinite(s_rp2)) bad = true;
                     const T mxr = sqrt(s_mx2);
-                    if (its_tol < 0 && (double)mxr <= A.tol) its_tol = it;
+                    if (its_tol < 0 && (double)mxr <= A.tol) {
+                        its_tol = it;
+                        if (A.early) s_stop = 1;   // every CTA of the instance takes the same decision
+                    }
                     if (A.hist && cr == 0) A.hist[(int64_t)ii * A.iters + it] = (float)mxr;
                 }
             }
@@ -110,6 +115,7 @@ __global__ void __launch_bounds__(MAXT) k_forward(FwdArgs<T> A)
             break;
         }
         fp = X.update(cl, gme, X.need_b && it == 0, stats);
+        if (s_stop) break;   // written before update()'s barrier; the output is the next iterate
     }
     const bool stat_thread = tid == nt - 32;   // lane 0 of the last warp holds the statistics
     if (cr == 0) {

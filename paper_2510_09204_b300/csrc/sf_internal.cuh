@@ -207,6 +207,7 @@ struct FwdArgs {
     int tc_mode;      // tensor-core projection: 0 none, 1 TF32, 2 BF16, 3 BF16 x3
     int tc_res;       // the CTA's projector chunks stay resident in shared memory
     int cull;         // row loops over per-chunk candidate lists (bounding-box culling)
+    int early;        // an instance stops after the iteration whose iterate met the tolerance
     int cost;         // SF_COST_PROJECTION or SF_COST_SMOOTHNESS (per-robot cost block Q1)
     uint32_t wait_budget;   // polls of the tensor-core pipeline's waits (0 only in tests)
     int n_refine;     // refinement passes of the tensor-core projection

@@ -31,7 +31,7 @@ EXPORTS = ("sf_create", "sf_destroy", "sf_layout", "sf_solve", "sf_solve_backwar
            "sf_shape_operator", "sf_profile", "sf_kernel_times", "sf_solve_noalloc", "sf_set_launch",
            "sf_get_launch", "sf_set_option", "sf_get_option", "sf_autotune", "sf_fit_positions", "sf_metrics",
            "sf_select", "sf_alu_peaks", "sf_strerror", "sf_version")
-SF_OPT_CULL, SF_OPT_TEST_TIMEOUT, SF_OPT_TC_RESIDENT, SF_OPT_TC_BATCH = 1, 2, 3, 4
+SF_OPT_CULL, SF_OPT_TEST_TIMEOUT, SF_OPT_TC_RESIDENT, SF_OPT_TC_BATCH, SF_OPT_EARLY_EXIT = 1, 2, 3, 4, 5
 SF_KT_FORWARD, SF_KT_RESIDUAL, SF_KT_BACKWARD, SF_NKT = range(4)
 
 

@@ -255,3 +255,45 @@ def test_zero_iterations_pass_the_input_through(precision, proj):
         r = oracle.residual(inst, s.unpack(d["xi"], k).double().cpu().numpy())
         np.testing.assert_allclose(res.cpu().numpy()[k, :2], r[:2], rtol=1e-9, atol=1e-12)
     s.close()
+
+
+def test_early_exit_stops_converged_instances_only():
+    """SF_OPT_EARLY_EXIT: an instance whose iterate l met the tolerance returns the iterate
+    of iteration l + 1, bit for bit the plain solve run for l + 1 iterations; instances that
+    never meet it return the full run's bits; a handle with checkpoints refuses the option."""
+    import torch
+    from paper_2510_09204_b300 import SFError, SFSolver
+    from paper_2510_09204_b300.sf import SF_OPT_EARLY_EXIT
+    # three small instances that meet the tolerance within 15 iterations, three of the
+    # 16-robot batch that do not meet it in 300
+    insts = [sfgen.custom_instance(n=4, n_obs=2, H=30, seed=s, extent=8.0, sigma=0.3) for s in range(3)]
+    insts += sfgen.make_batch(2, B=3)
+    iters = 300
+
+    def run(n_it, early):
+        s = SFSolver(insts, 2, 11, rho=RHO, precision="fp32", proj="structured", max_iters=iters, tol=1e-3)
+        if early:
+            s.set_option(SF_OPT_EARLY_EXIT, 1)
+            assert s.option(SF_OPT_EARLY_EXIT) == 1
+        d = s.pack(insts)
+        xo, _, res = s.solve(d, d["xi"], n_it)
+        torch.cuda.synchronize()
+        assert (s.status() == 0).all()
+        return [s.unpack(xo, k).cpu().numpy().copy() for k in range(len(insts))], res.cpu().numpy()
+
+    full, rf = run(iters, False)
+    early, re = run(iters, True)
+    its = rf[:, 3].astype(int)
+    assert (re[:, 3].astype(int) == its).all()
+    stopped = [k for k in range(len(insts)) if 0 <= its[k] < iters - 1]
+    assert stopped == [0, 1, 2], its
+    for k in range(len(insts)):
+        if k in stopped:
+            ref, _ = run(int(its[k]) + 1, False)
+            assert np.array_equal(early[k], ref[k]), k
+            assert re[k, 1] <= 1e-3 + 1e-6
+        else:
+            assert np.array_equal(early[k], full[k]), k
+    s = SFSolver(insts, 2, 11, rho=RHO, precision="fp32", max_iters=10, ckpt_every=1)
+    with pytest.raises(SFError):
+        s.set_option(SF_OPT_EARLY_EXIT, 1)
