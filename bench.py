@@ -59,6 +59,8 @@ def args_():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 and tensor-core comparison solves")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--cluster", type=int, default=0, help="CTAs per instance (with --threads: a fixed geometry, no autotune)")
+    p.add_argument("--threads", type=int, default=0)
     p.add_argument("--no-configs", action="store_true", help="skip the other workloads' summary (configs 3, 4, 5)")
     p.add_argument("--shard-batch", action="store_true",
                    help="under torchrun: split the one batch over the ranks (shard.balance) instead of one batch per rank")
@@ -713,7 +715,9 @@ def main():
     setup_ms = 1e3 * (time.perf_counter() - t_setup)
     data = solver.pack(insts, device=dev)
     tune = None
-    if not a.no_autotune:
+    if a.cluster:
+        solver.set_launch(a.cluster, a.threads)
+    elif not a.no_autotune:
         t0 = time.perf_counter()
         c, t, ms = solver.autotune(data, data["xi"], iters, reps=2, stream=stream)
         tune = {"cluster": c, "threads": t, "best_forward_ms": ms, "tuning_s": time.perf_counter() - t0}

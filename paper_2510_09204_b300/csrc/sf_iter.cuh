@@ -1224,22 +1224,25 @@ struct Cta {
             // stays inside it)
             constexpr int kU = 4;
             if ((N & 3) == 0) {   // four consecutive k of one axis per vector: 8-byte stores
-                const int NV = N >> 2, tot = G * ND * NV;
+                // a warp takes 8 columns x 4 vectors (the columns fastest: its stores fall in
+                // distinct banks but for a two-way overlap of the vectors 0 and 2)
+                const int NV = N >> 2, ncol = G * ND, cb = (ncol + 7) >> 3, qb = (NV + 3) >> 2, tot = 32 * cb * qb;
                 for (int b0 = tid; b0 < tot; b0 += nt * kU) {
                     float4 x4[kU];
 #pragma unroll
                     for (int u = 0; u < kU; ++u) {
-                        const int idx = b0 + u * nt;
-                        if (idx < tot) {
-                            const int g = idx / (ND * NV), r = idx - g * ND * NV;
-                            x4[u] = reinterpret_cast<const float4 *>(cl.map_shared_rank(src, g * C + cr))[r];
+                        const int t = b0 + u * nt, blk = t >> 5, gc = (blk % cb) * 8 + (t & 7),
+                                  q = (blk / cb) * 4 + ((t >> 3) & 3);
+                        if (t < tot && gc < ncol && q < NV) {
+                            const int g = gc / ND, ax = gc - g * ND;
+                            x4[u] = reinterpret_cast<const float4 *>(cl.map_shared_rank(src, g * C + cr))[ax * NV + q];
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < kU; ++u) {
-                        const int idx = b0 + u * nt;
-                        if (idx >= tot) continue;
-                        const int gc = idx / NV, q = idx - gc * NV, k0 = 4 * q;   // gc = g n_d + ax: the B column
+                        const int t = b0 + u * nt, blk = t >> 5, gc = (blk % cb) * 8 + (t & 7),
+                                  q = (blk / cb) * 4 + ((t >> 3) & 3), k0 = 4 * q;   // gc = g n_d + ax: the B column
+                        if (t >= tot || gc >= ncol || q >= NV) continue;
                         const int off = (gc >> 3) * SBO + (k0 >> 3) * 128 + (gc & 7) * 16 + (k0 & 7) * 2;
                         const __nv_bfloat162 h01 = __floats2bfloat162_rn(x4[u].x, x4[u].y);
                         const __nv_bfloat162 h23 = __floats2bfloat162_rn(x4[u].z, x4[u].w);
@@ -1305,11 +1308,11 @@ struct Cta {
                     for (int q = 0; q < 16; ++q) dv[q] += dl2[q];
                 }
             }
-            if (la == 2 && (wp == 2 || wp == 3))   // A's low parts' rows, tid - 64
-                for (int q = 0; q < 16; ++q) tb_stage[(tid - 64) * 16 + q] = dv[q];
+            if (la == 2 && (wp == 2 || wp == 3))   // A's low parts' rows, tid - 64; [column][row]
+                for (int q = 0; q < 16; ++q) tb_stage[q * 64 + tid - 64] = dv[q];
             __syncthreads();
             if (wp < 2 && tid < rows)
-                for (int q = 0; q < ncol; ++q) dl[q * Lb + tid] = (T)(dv[q] + (la == 2 ? tb_stage[tid * 16 + q] : 0.f));
+                for (int q = 0; q < ncol; ++q) dl[q * Lb + tid] = (T)(dv[q] + (la == 2 ? tb_stage[q * 64 + tid] : 0.f));
             tc::fence_before_sync();
             cl.sync();
         }
