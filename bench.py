@@ -703,10 +703,47 @@ def other_configs(dev, stream, flush, peaks):
     return out
 
 
+def batch_sweep(dev, stream, flush, peaks, sizes=(32, 128, 512)):
+    """The config-2 step (16 robots, 2-D, 200 iterations, forward + FP64 residual check +
+    adjoint, checkpoints every iteration) at growing batch sizes: config 2's 32 instances
+    leave SMs idle and its time is one instance's dependent chain, while larger batches
+    fill the GPU.  Per size: autotuned geometry, median of 3 steps with the L2 flushed,
+    throughput and the fraction of the measured FP32 peak over both step kernels."""
+    import torch
+
+    from paper_2510_09204_b300 import SFSolver
+    cfg = sfgen.CONFIGS[2]
+    out = []
+    for B in sizes:
+        insts = sfgen.make_batch(2, B=B)
+        pairs, _ = sfgen.batch_stats(insts)
+        s = SFSolver(insts, 2, 11, rho=RHO, precision="fp32", proj="structured", max_iters=cfg.iters, ckpt_every=1)
+        d = s.pack(insts, device=dev)
+        c, t, _ = s.autotune(d, d["xi"], cfg.iters, reps=1, stream=stream)
+        st = Step(s, d, cfg.iters, False, stream)
+        for _ in range(2):
+            st()
+        torch.cuda.synchronize()
+        times, _ = _time_steps(st, 3, stream, flush)
+        ms = statistics.median(times)
+        fl = algorithmic_flops(insts, cfg.iters, "structured", "k_forward")[0] + \
+            algorithmic_flops(insts, cfg.iters, "structured", "k_backward", 1)[0]
+        out.append({"instances": B, "cluster": c, "threads": t, "ms_per_step": ms,
+                    "pair_timestep_updates_per_s": pairs * cfg.iters / (ms * 1e-3),
+                    "frac_of_measured_fp32": fl / (ms * 1e-3) / 1e12 / peaks["fp32_tflops"],
+                    "status_ok": bool((s.status() == 0).all())})
+        s.close()
+    return out
+
+
 def summary_of(line, configs):
     """The few numbers a reader needs, last in the line: the chosen step against plain
     FP64 on the GPU, and per other workload its fastest run's time, error and fraction."""
     s = {"chosen_ms": line["ms_per_step"], "roofline_frac": line["roofline"]["frac"]}
+    if line.get("batch_sweep"):
+        s["batch_sweep"] = {str(b["instances"]): {"ms": round(b["ms_per_step"], 3),
+                                                  "frac": round(b["frac_of_measured_fp32"], 4)}
+                            for b in line["batch_sweep"]}
     f = line.get("fp64_gpu")
     if f:
         s.update(fp64_gpu_ms=f["ms_per_step"], chosen_speedup_vs_fp64=f["chosen_speedup"],
@@ -871,9 +908,11 @@ def main():
             v.pop("_pos"), v.pop("_res")
             variants.append(v)
 
-    configs = None
+    configs = sweep = None
     if not a.no_compare and not a.no_configs and rank == 0:
         configs = other_configs(dev, stream, flush, peaks)
+        if a.config == 2 and world == 1:
+            sweep = batch_sweep(dev, stream, flush, peaks)
 
     if rank == 0:
         peak_alu = peaks["fp32_tflops"]
@@ -939,6 +978,8 @@ def main():
             line["convergence"] = convergence
         if configs:
             line["configs"] = configs
+        if sweep:
+            line["batch_sweep"] = sweep
         if not a.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(insts, iters, a.forward_only)
         line["summary"] = summary_of(line, configs)   # last, so a truncated tail still shows it
