@@ -21,8 +21,10 @@ instead splits the one batch over the ranks with shard.balance (strong scaling).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -49,6 +51,7 @@ def args_():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", type=int, default=2)
+    p.add_argument("--batch", type=int, default=0, help="instances of the config's shape (0: the config's own count)")
     p.add_argument("--precision", default="fp32")
     p.add_argument("--proj", default="structured")
     p.add_argument("--n-refine", type=int, default=0)
@@ -71,15 +74,18 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def workload(cid, rank=0, world=1, shard_batch=False):
+def workload(cid, rank=0, world=1, shard_batch=False, batch=0):
     """The config's batch: one batch per rank (seeds offset by rank), or with shard_batch
-    this rank's share of the one batch (shard.balance by rows per iteration)."""
+    this rank's share of the one batch (shard.balance by rows per iteration).  batch > 0
+    replaces the config's instance count (the workload is then named for it)."""
     cfg = sfgen.CONFIGS[cid]
+    if batch and batch != cfg.B:
+        cfg = dataclasses.replace(cfg, B=batch, name=re.sub(r"b\d+", "b%d" % batch, cfg.name, count=1))
     if shard_batch:
         from paper_2510_09204_b300.shard import shard
-        _, insts = shard(sfgen.make_batch(cid), rank, world)
+        _, insts = shard(sfgen.make_batch(cid, B=cfg.B), rank, world)
     else:
-        insts = sfgen.make_batch(cid, start=rank * cfg.B)
+        insts = sfgen.make_batch(cid, B=cfg.B, start=rank * cfg.B)
     pairs, obs = sfgen.batch_stats(insts)
     return cfg, insts, pairs, obs
 
@@ -321,7 +327,7 @@ def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cfg, insts, _, _ = workload(a.config)
+    cfg, insts, _, _ = workload(a.config, batch=a.batch)
     iters = cfg.iters
     sample, seeds, pool, cores = _oracle_sample(insts, iters, a.forward_only, 4.0)   # ~4 s of host work per step
     pairs, _ = sfgen.batch_stats(sample)
@@ -777,9 +783,9 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg, insts, pairs, obs = workload(a.config, rank, world, a.shard_batch)
+    cfg, insts, pairs, obs = workload(a.config, rank, world, a.shard_batch, a.batch)
     # work of the whole job: every rank's batch, or the one batch split over the ranks
-    pairs_job = sfgen.batch_stats(sfgen.make_batch(a.config))[0] if a.shard_batch else pairs * world
+    pairs_job = sfgen.batch_stats(sfgen.make_batch(a.config, B=cfg.B))[0] if a.shard_batch else pairs * world
     peaks = alu_peaks(dev)   # before the timed region
     iters = cfg.iters
     nd = cfg.n_d
