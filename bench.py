@@ -804,7 +804,7 @@ def main():
     elif not a.no_autotune:
         t0 = time.perf_counter()
         c, t, ms = solver.autotune(data, data["xi"], iters, reps=2, stream=stream)
-        tune = {"cluster": c, "threads": t, "best_forward_ms": ms, "tuning_s": time.perf_counter() - t0}
+        tune = {"cluster": c, "threads": t, "best_step_ms": ms, "tuning_s": time.perf_counter() - t0}
     solver.profile(True)
     step = Step(solver, data, iters, a.forward_only, stream)
 
