@@ -329,7 +329,7 @@ def run_reference(a):
         return
     cfg, insts, _, _ = workload(a.config, batch=a.batch)
     iters = cfg.iters
-    sample, seeds, pool, cores = _oracle_sample(insts, iters, a.forward_only, 4.0)   # ~4 s of host work per step
+    sample, seeds, pool, cores = _oracle_sample(insts, iters, a.forward_only, 2.0)   # ~2 s of host work per step
     pairs, _ = sfgen.batch_stats(sample)
     for _ in range(a.warmup):
         _oracle_step(sample, iters, seeds, a.forward_only, pool)
